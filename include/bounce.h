@@ -1,0 +1,173 @@
+/*
+ * bounce.h -- C ABI of the GB300 BOUNCE velocity-jump MD library.
+ *
+ * Method: Monmarche, Weisman, Lagardere, Piquemal, "BOUNCE: a velocity-jump
+ * integrator for molecular dynamics" (arXiv 2002.07109).  The library runs
+ * the BJAOAJB splitting of Sec. III.C / Sec. IV.B (BOUNCE) and the BAOAB
+ * splitting it extends, for point-charge + Lennard-Jones systems with
+ * harmonic bonds and angles, on one CUDA device (sm_103a).
+ *
+ * Units: Angstrom, fs, kcal/mol, g/mol, elementary charge, K.
+ * Coulomb constant 332.063713 kcal A/(mol e^2); k_B = 0.0019872041
+ * kcal/(mol K); an acceleration of 1 kcal/mol/A per g/mol is 4.184e-4 A/fs^2.
+ *
+ * Conventions for every entry point:
+ *   - Return value: BOUNCE_OK (0) or a negative BOUNCE_ERR_* code.  Nothing
+ *     is thrown across the ABI.  bounce_last_error() returns a message for
+ *     the last failing call on that context.  The context stays usable after
+ *     an error unless the error is BOUNCE_ERR_CUDA from a sticky device fault.
+ *   - Arrays of 3-vectors are row-major (n, 3) doubles.
+ *   - Pointer arguments flagged by `where` are host memory (BOUNCE_HOST) or
+ *     device memory of the context's device (BOUNCE_DEVICE).  The caller owns
+ *     every array it passes; the library copies inputs into its own device
+ *     buffers and never keeps a caller pointer after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *     of a call is ordered on that stream.  Host-memory transfers through
+ *     `where = BOUNCE_HOST` synchronise the stream before returning.
+ *   - The F_i of the paper are GRADIENT terms of E_pot (Sec. II.A): the
+ *     "gradient" outputs below are dE/dq, not physical forces.
+ */
+#ifndef BOUNCE_H
+#define BOUNCE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BOUNCE_OK 0
+#define BOUNCE_ERR_INVALID_ARG (-1)
+#define BOUNCE_ERR_CUDA (-2)
+#define BOUNCE_ERR_NONFINITE (-3)
+#define BOUNCE_ERR_LIST_OVERFLOW (-4)
+#define BOUNCE_ERR_STATE (-5)
+#define BOUNCE_ERR_UNSUPPORTED (-6)
+
+#define BOUNCE_HOST 0
+#define BOUNCE_DEVICE 1
+
+/* Integrators (bounce_run). */
+#define BOUNCE_BAOAB 0  /* B A O A B (paper Sec. III.C without J)            */
+#define BOUNCE_BOUNCE 1 /* B J A O A J B (paper Sec. III.C and Sec. IV.B)    */
+
+/* Gradient parts (bounce_compute_gradient). */
+#define BOUNCE_GRAD_FULL 0  /* dE_pot/dq: all pairs within r_c + bonded     */
+#define BOUNCE_GRAD_SHORT 1 /* F_0: bonded + (1 - chi) W' of every pair     */
+#define BOUNCE_GRAD_LONG 2  /* sum_j F_ij = chi W' of every pair (Sec. IV.A) */
+
+#define BOUNCE_MAX_TYPES 4
+
+typedef struct bounce_ctx bounce_ctx;
+
+/* Run configuration; bounce_config_default() fills the defaults shown. */
+typedef struct bounce_config {
+    double dt_fs;          /* time step delta (1.0)                              */
+    double gamma_per_fs;   /* Langevin friction gamma (0.001 = 1/ps)             */
+    double temperature_K;  /* T (300); beta = 1/(k_B T)                          */
+    uint64_t seed;         /* Philox key of every random draw (0)                */
+    double r_on;           /* r' : chi = 0 below (4.0); Sec. IV.A                */
+    double r_off;          /* r'': chi = 1 above (5.0); r_on == r_off = step     */
+    double r_cut;          /* pair cutoff r_c (<= 0 or inf: none)                */
+    double skin;           /* Verlet skin; rows hold r < r_c + skin (1.0)        */
+    double ewald_beta;     /* 0: bare Coulomb; > 0: Ewald direct erfc (A^-1)     */
+    int32_t periodic;      /* 0: open droplet; 1: periodic box                   */
+    double box[3];         /* periodic box edges (A)                             */
+    int32_t max_neighbors; /* capacity of one candidate row (2048)               */
+    int32_t max_short;     /* capacity of one short-range row (256)              */
+    int32_t device;        /* CUDA device ordinal (0)                            */
+} bounce_config;
+
+/* Energies and counters (bounce_get_energies). */
+typedef struct bounce_energies {
+    double coulomb;     /* sum_{i<j, r<r_c} k q_i q_j / r (or erfc(b r)/r)        */
+    double lj;          /* sum_{i<j, r<r_c} 4 eps ((s/r)^12 - (s/r)^6)           */
+    double bond;        /* sum k (r - r0)^2                                       */
+    double angle;       /* sum k (theta - theta0)^2                               */
+    double kinetic;     /* sum m v^2 / 2                                          */
+    double potential;   /* coulomb + lj + bond + angle                            */
+    double temperature; /* 2 E_kin / (3 N k_B)                                    */
+    int64_t step;       /* steps completed since the state was set               */
+    int64_t proposals;  /* jump proposals since the last counter reset            */
+    int64_t accepts;    /* accepted jumps (reflections)                           */
+    int64_t near_ties;  /* proposals with |U - lambda/lambda*| < 1e-6             */
+    int64_t rebuilds;   /* candidate-row rebuilds                                 */
+    int64_t short_pairs;/* pair terms evaluated for F_0 (BOUNCE)                 */
+    int64_t full_pairs; /* pair terms evaluated for the full gradient (BAOAB)    */
+} bounce_energies;
+
+/* Fill *cfg with the defaults documented above. */
+void bounce_config_default(bounce_config* cfg);
+
+/* Create a context on cfg->device.  *out receives the context; the config
+ * is copied.  Errors: INVALID_ARG (bad config), CUDA. */
+int bounce_create(bounce_ctx** out, const bounce_config* cfg);
+
+/* Topology (host arrays, copied).  type[n] in [0, BOUNCE_MAX_TYPES), mass[n]
+ * (g/mol, > 0), charge[n] (e), molecule[n]: pairs within one molecule are
+ * excluded from all pair terms and from the jump candidates.  bond_ij[2 nb],
+ * bond_k_r0[2 nb]: E = k (r - r0)^2.  angle_ijk[3 na] (end, vertex, end),
+ * angle_k_t0[2 na]: E = k (theta - theta0)^2, theta0 in rad.
+ * Errors: INVALID_ARG, CUDA. */
+int bounce_set_topology(bounce_ctx* ctx, int32_t n_atoms, const int32_t* type, const double* mass,
+                        const double* charge, const int32_t* molecule, int32_t n_bonds, const int32_t* bond_ij,
+                        const double* bond_k_r0, int32_t n_angles, const int32_t* angle_ijk,
+                        const double* angle_k_t0);
+
+/* Lennard-Jones table (host, copied): sigma[T*T], eps[T*T] per type pair,
+ * E = 4 eps ((sigma/r)^12 - (sigma/r)^6); eps = 0 switches a pair off.
+ * Computes the jump bounds L_ab = sup_r |chi W'_ab| (Sec. IV.A) for the
+ * current topology and config.  Call after bounce_set_topology. */
+int bounce_set_lj(bounce_ctx* ctx, int32_t n_types, const double* sigma, const double* eps);
+
+/* Positions q[n,3] and velocities v[n,3] (A, A/fs); resets the step counter
+ * to `step` (the Philox step index of the next step) and forces a row
+ * rebuild.  Errors: INVALID_ARG, NONFINITE, STATE (no topology). */
+int bounce_set_state(bounce_ctx* ctx, const double* q, const double* v, int64_t step, int32_t where, void* stream);
+
+/* Copy the current state out (q, v may be NULL to skip). */
+int bounce_get_state(bounce_ctx* ctx, double* q, double* v, int32_t where, void* stream);
+
+/* Advance n_steps full steps of the integrator (BOUNCE_BAOAB or
+ * BOUNCE_BOUNCE); the returned state is after the last B half-kick.  All
+ * work stays on the device; the call does not synchronise `stream` except
+ * to report row overflows, which it checks once at the end.
+ * Errors: STATE, LIST_OVERFLOW (a row exceeded max_neighbors; the state is
+ * then invalid), CUDA. */
+int bounce_run(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, void* stream);
+
+/* Energies of the current state and the run counters (synchronises). */
+int bounce_get_energies(bounce_ctx* ctx, bounce_energies* out, void* stream);
+
+/* Zero the proposal / accept / tie / pair counters. */
+int bounce_reset_counters(bounce_ctx* ctx, void* stream);
+
+/* Jump bounds: L[T*T] (padded by 1e-6 relative) and row maxima Lstar[T]. */
+int bounce_get_bounds(bounce_ctx* ctx, double* L, double* Lstar);
+
+/* --- Component entry points (each runs the same kernels bounce_run uses). */
+
+/* Gradient part (BOUNCE_GRAD_*) at the current positions into grad[n,3]. */
+int bounce_compute_gradient(bounce_ctx* ctx, int32_t part, double* grad, int32_t where, void* stream);
+
+/* One jump half-step J(delta/2) (Sec. IV.B, step J) on the current
+ * velocities at the current positions, with the Philox counter of
+ * (step, stream_id).  If M and n_acc are not NULL they receive, per atom,
+ * the Poisson proposal count and the number of accepted reflections. */
+int bounce_jump_half(bounce_ctx* ctx, int64_t step, int32_t stream_id, int32_t* M, int32_t* n_acc, int32_t where,
+                     void* stream);
+
+/* Candidate rows at the current positions (rebuilt first if stale):
+ * counts[n] and rows[n * capacity] (ascending atom indices). */
+int bounce_get_rows(bounce_ctx* ctx, int32_t* counts, int32_t* rows, int32_t capacity);
+
+/* Message of the last error on ctx (never NULL). */
+const char* bounce_last_error(const bounce_ctx* ctx);
+
+/* Free all device and host memory of ctx. */
+void bounce_destroy(bounce_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOUNCE_H */

@@ -1,0 +1,222 @@
+"""BAOAB and BOUNCE (BJAOAJB) steps in FP64, following the paper.
+
+Paper Sec. III.C (splitting): one step of BOUNCE is
+    B(delta/2) J(delta/2) A(delta/2) O(delta) A(delta/2) J(delta/2) B(delta/2)
+and BAOAB is the same without the J steps.  Sec. IV.B spells the steps out:
+    B: p <- p - delta/2 F_0(q)
+    J: for each atom i independently (Sec. IV.A: given q, the V_i are
+       independent chains), draw M_i ~ Poisson(n_i beta ||v_i|| L delta/2),
+       then M_i times: J uniform over the n_i candidates, U uniform on [0,1];
+       if U < lambda_iJ / lambda*_iJ then v_i <- R_iJ(v_i)
+    A: q <- q + delta/2 M^-1 p
+    O: p <- e^{-gamma delta} p + sqrt(beta^-1 (1 - e^{-2 gamma delta}) M) G
+with lambda_ij = beta max(0, v_i . F_ij), lambda* = beta ||v_i|| L and
+R_ij(v) = v - 2 (v . F_ij)/||F_ij||^2 F_ij (Sec. IV.A).  So the acceptance
+test is U ||v_i|| L < v_i . F_ij (beta cancels).
+
+Readings of the paper used here (all listed in the design notes):
+  * F_0 = bonded + (1 - chi) part of every pair term; F_ij = chi W' d/r.
+  * friction coefficient is mass-independent: c1 = exp(-gamma delta).
+  * L is the per-type row maximum L*_{t_i} (oracle.bounds).
+  * Random numbers: Philox4x32-10 keyed by the run seed with counter
+    (slot, atom, step, stream); stream 1 for the J after the first B,
+    stream 2 for the J before the last B, stream 0 for O.  Proposal k
+    (1-based) uses slot k: J = floor(x0 n_i / 2^32), U = 53-bit from x1, x2.
+    O uses slot 0: Box-Muller on (x0, x1) and (x2, x3).
+  * Units: v in A/fs, gradients in kcal/mol/A; a kick is
+    v <- v - (h * 4.184e-4 / m) G.
+"""
+import math
+import numpy as np
+
+from . import philox, poisson
+from .forcefield import (ACCEL, KB, Params, bonded_gradients, pair_gradients,
+                         pair_gradient_one, kinetic_energy, pair_energies, bonded_energies)
+from .neighbors import rows as build_rows, needs_rebuild, to_pairs
+
+
+class Topology:
+    def __init__(self, typ, mass, charge, mol, bonds, bond_k_r0, angles, angle_k_t0):
+        self.type = np.asarray(typ, dtype=np.int64)
+        self.mass = np.asarray(mass, dtype=np.float64)
+        self.charge = np.asarray(charge, dtype=np.float64)
+        self.mol = np.asarray(mol, dtype=np.int64)
+        self.bonds = np.asarray(bonds, dtype=np.int64).reshape(-1, 2)
+        self.bond_k_r0 = np.asarray(bond_k_r0, dtype=np.float64).reshape(-1, 2)
+        self.angles = np.asarray(angles, dtype=np.int64).reshape(-1, 3)
+        self.angle_k_t0 = np.asarray(angle_k_t0, dtype=np.float64).reshape(-1, 2)
+
+
+def o_step(v, mass, temperature, gamma, dt, seed, step, atoms=None):
+    """O: v <- c1 v + sqrt((1 - c1^2) k_B T / m) G, c1 = exp(-gamma dt)."""
+    n = v.shape[0]
+    atoms = np.arange(n) if atoms is None else atoms
+    x = philox.draw(seed, 0, atoms, step, philox.STREAM_O)
+    ua, ub = philox.u24_open0(x[0]), philox.u24(x[1])
+    uc, ud = philox.u24_open0(x[2]), philox.u24(x[3])
+    r1 = np.sqrt(-2.0 * np.log(ua))
+    r2 = np.sqrt(-2.0 * np.log(uc))
+    g = np.stack([r1 * np.cos(2.0 * math.pi * ub), r1 * np.sin(2.0 * math.pi * ub), r2 * np.cos(2.0 * math.pi * ud)], 1)
+    c1 = math.exp(-gamma * dt)
+    sd = np.sqrt((1.0 - c1 * c1) * KB * temperature * ACCEL / mass)
+    return c1 * v + sd[:, None] * g
+
+
+def jump_half(q, v, row_list, topo, p, Lstar_row, beta, dt, seed, step, stream, record=False):
+    """The jump step J over a half step dt/2 for every atom (Sec. IV.B).
+
+    Returns the new velocities and, if record, a dict of per-proposal arrays
+    (atom, k, J, j, U, ratio = max(0, v.F)/(||v|| L*), accepted)."""
+    n = q.shape[0]
+    v = np.array(v, dtype=np.float64, copy=True)
+    nrow = np.array([len(r) for r in row_list], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(nrow)])
+    flat = np.concatenate(row_list) if n else np.zeros(0, np.int64)
+    s = np.sqrt((v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1]) + v[:, 2] * v[:, 2])
+    Ls = Lstar_row[topo.type]
+    mu = ((((beta * s) * Ls) * nrow) * dt) * 0.5
+    atoms = np.arange(n)
+    M = poisson.counts(mu, atoms, seed, step, stream)
+    rec = {k: [] for k in ('atom', 'k', 'J', 'j', 'U', 'ratio', 'accepted')} if record else None
+    kmax = int(M.max()) if n else 0
+    for k in range(1, kmax + 1):
+        act = np.nonzero(M >= k)[0]
+        x = philox.draw(seed, k, act, step, stream)
+        J = philox.index_below(x[0], nrow[act])
+        j = flat[offs[act] + J]
+        U = philox.u53(x[1], x[2])
+        ti, tj = topo.type[act], topo.type[j]
+        G = pair_gradient_one(q[act], q[j], topo.charge[act], topo.charge[j],
+                              p.lj_sigma[ti, tj], p.lj_eps[ti, tj], p, part="long")
+        va = v[act]
+        a = (va[:, 0] * G[:, 0] + va[:, 1] * G[:, 1]) + va[:, 2] * G[:, 2]
+        thr = (U * s[act]) * Ls[act]
+        acc = thr < a
+        if record:
+            with np.errstate(divide='ignore', invalid='ignore'):
+                ratio = np.where(s[act] > 0, np.maximum(a, 0.0) / (s[act] * Ls[act]), 0.0)
+            for key, val in (('atom', act), ('k', np.full(len(act), k)), ('J', J), ('j', j), ('U', U),
+                             ('ratio', ratio), ('accepted', acc)):
+                rec[key].append(val)
+        if np.any(acc):
+            ia = act[acc]
+            Ga = G[acc]
+            aa = a[acc]
+            ff = (Ga[:, 0] * Ga[:, 0] + Ga[:, 1] * Ga[:, 1]) + Ga[:, 2] * Ga[:, 2]
+            coef = (aa + aa) / ff
+            v[ia] = v[ia] - coef[:, None] * Ga
+    if record:
+        rec = {key: (np.concatenate(val) if val else np.zeros(0)) for key, val in rec.items()}
+        rec['M'] = M
+        rec['mu'] = mu
+    return v, rec
+
+
+class OracleMD:
+    """Plain FP64 BAOAB / BOUNCE integrator over one system."""
+
+    def __init__(self, q, v, topo, p, *, dt=1.0, gamma=0.001, temperature=300.0, seed=0, skin=1.0, step=0):
+        self.q = np.array(q, dtype=np.float64)
+        self.v = np.array(v, dtype=np.float64)
+        self.topo = topo
+        self.p = p
+        self.dt = float(dt)
+        self.gamma = float(gamma)
+        self.T = float(temperature)
+        self.beta = 1.0 / (KB * self.T)
+        self.seed = int(seed)
+        self.skin = float(skin)
+        self.step_index = int(step)
+        self.q_ref = None
+        self.row_list = None
+        self.rebuilds = 0
+        self.proposals = 0
+        self.accepts = 0
+        from .bounds import bound_table
+        T = int(max(topo.type.max() + 1, p.lj_sigma.shape[0]))
+        self.L, self.Lstar = bound_table(topo.charge, topo.type, T, p.lj_sigma, p.lj_eps, p)
+
+    @property
+    def r_list(self):
+        return self.p.r_cut + self.skin if math.isfinite(self.p.r_cut) else math.inf
+
+    def ensure_rows(self):
+        if self.row_list is None or (math.isfinite(self.r_list) and needs_rebuild(self.q, self.q_ref, self.skin)):
+            self.row_list = build_rows(self.q, self.topo.mol, self.r_list, self.p.box)
+            self.q_ref = self.q.copy()
+            self.rebuilds += 1
+
+    def pairs(self):
+        return to_pairs(self.row_list)
+
+    def grad_short(self):
+        """F_0: bonded + (1 - chi) pair part."""
+        ii, jj = self.pairs()
+        t = self.topo
+        return (pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "short")
+                + bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box))
+
+    def grad_full(self):
+        ii, jj = self.pairs()
+        t = self.topo
+        return (pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "full")
+                + bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box))
+
+    def grad_long(self):
+        ii, jj = self.pairs()
+        t = self.topo
+        return pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "long")
+
+    def kick(self, G, h):
+        self.v = self.v - ((h * ACCEL) / self.topo.mass)[:, None] * G
+
+    def drift(self, h):
+        self.q = self.q + h * self.v
+
+    def jump(self, stream, record=False):
+        self.v, rec = jump_half(self.q, self.v, self.row_list, self.topo, self.p, self.Lstar, self.beta,
+                                self.dt, self.seed, self.step_index, stream, record=True)
+        self.proposals += int(rec['M'].sum())
+        self.accepts += int(rec['accepted'].sum()) if len(rec['accepted']) else 0
+        return rec if record else None
+
+    def step_baoab(self):
+        h = 0.5 * self.dt
+        self.ensure_rows()
+        self.kick(self.grad_full(), h)
+        self.drift(h)
+        self.v = o_step(self.v, self.topo.mass, self.T, self.gamma, self.dt, self.seed, self.step_index)
+        self.drift(h)
+        self.ensure_rows()
+        self.kick(self.grad_full(), h)
+        self.step_index += 1
+
+    def step_bounce(self, record=False):
+        h = 0.5 * self.dt
+        self.ensure_rows()
+        self.kick(self.grad_short(), h)
+        r1 = self.jump(philox.STREAM_J1, record)
+        self.drift(h)
+        self.v = o_step(self.v, self.topo.mass, self.T, self.gamma, self.dt, self.seed, self.step_index)
+        self.drift(h)
+        self.ensure_rows()
+        r2 = self.jump(philox.STREAM_J2, record)
+        self.kick(self.grad_short(), h)
+        self.step_index += 1
+        return (r1, r2) if record else None
+
+    def run(self, n, integrator="bounce"):
+        for _ in range(n):
+            if integrator == "bounce":
+                self.step_bounce()
+            else:
+                self.step_baoab()
+
+    def energies(self):
+        self.ensure_rows()
+        ii, jj = self.pairs()
+        t = self.topo
+        ec, el = pair_energies(self.q, t.charge, t.type, ii, jj, self.p)
+        eb, ea = bonded_energies(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box)
+        ek = kinetic_energy(self.v, t.mass)
+        return dict(coul=ec, lj=el, bond=eb, angle=ea, kin=ek, pot=ec + el + eb + ea)

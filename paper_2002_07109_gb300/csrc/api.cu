@@ -1,0 +1,772 @@
+// C ABI of the BOUNCE library (declared in include/bounce.h): context
+// management, host-side set-up (topology tables, the jump bounds
+// L_ab = sup |chi W'_ab| of Sec. IV.A, the cell grid) and the run loop,
+// which replays CUDA graphs of captured chunks of steps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bounce.h"
+#include "common.cuh"
+
+void nlist_set_smem_limit(size_t bytes);
+
+namespace {
+
+constexpr int CHUNK = 32;  // steps per captured graph
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct bounce_ctx {
+    bounce_config cfg{};
+    std::string err;
+    int n = 0;
+    bool have_topo = false, have_lj = false, have_state = false;
+    // host copies
+    std::vector<int> type, mol;
+    std::vector<double> mass, charge;
+    std::vector<int> bt_off;
+    std::vector<int4> bt_idx;
+    std::vector<float2> bt_par;
+    int n_types = 0;
+    double L[BOUNCE_MAXT * BOUNCE_MAXT] = {0};
+    double Lstar[BOUNCE_MAXT] = {0};
+    long long step0 = 0;
+    // device
+    std::vector<Buf> bufs;
+    DevSys ds{};
+    Params pp{};
+    double* terms = nullptr;     // energy scratch [6 n]
+    long long* d_step = nullptr;
+    int* h_err = nullptr;        // pinned
+    unsigned long long* h_cnt = nullptr;
+    int bitmap_warps = 1;
+    size_t bitmap_bytes = 0;
+    int ncell_alloc = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+int fail(bounce_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(c, BOUNCE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int dalloc(bounce_ctx* c, T** out, size_t count) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(c, BOUNCE_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cudaMemset(p, 0, bytes);
+    c->bufs.push_back({p, bytes});
+    *out = (T*)p;
+    return BOUNCE_OK;
+}
+
+void drop_graphs(bounce_ctx* c) {
+    for (auto& g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+void free_all(bounce_ctx* c) {
+    drop_graphs(c);
+    for (auto& b : c->bufs) cudaFree(b.p);
+    c->bufs.clear();
+    c->ds = DevSys{};
+    c->terms = nullptr;
+    c->d_step = nullptr;
+}
+
+// ---------------------------------------------------------------- bounds
+double chi_host(double r, double on, double off) {
+    if (!(off > on)) return r >= off ? 1.0 : 0.0;
+    double s = std::min(std::max((r - on) / (off - on), 0.0), 1.0);
+    return s * s * s * (10.0 + s * (-15.0 + 6.0 * s));
+}
+
+double dW_host(double r, double qq, double sig, double eps, double beta) {
+    double w;
+    if (beta > 0) w = -KCOUL_D * qq * (std::erfc(beta * r) / (r * r) + 2.0 * beta / std::sqrt(M_PI) * std::exp(-beta * beta * r * r) / r);
+    else w = -KCOUL_D * qq / (r * r);
+    if (eps != 0.0) {
+        double sr6 = std::pow(sig / r, 6);
+        w += -24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r;
+    }
+    return w;
+}
+
+// sup over r in [r', r_c) of |chi(r) W'(r)|: grid scan, then golden-section
+// refinement of the best bracket.
+double sup_chi_dW(const bounce_config& cfg, double qq, double sig, double eps) {
+    const double lo = cfg.r_off > cfg.r_on ? cfg.r_on : cfg.r_off;
+    const bool cut = std::isfinite(cfg.r_cut) && cfg.r_cut > 0;
+    const double hi = cut ? cfg.r_cut : cfg.r_off + 60.0;
+    if (!(hi > lo)) return 0.0;
+    auto f = [&](double r) {
+        if (cut && !(r < cfg.r_cut)) return 0.0;
+        return std::fabs(chi_host(r, cfg.r_on, cfg.r_off) * dW_host(r, qq, sig, eps, cfg.ewald_beta));
+    };
+    const int N = 400000;
+    const double h = (hi - lo) / N;
+    int kbest = 0;
+    double best = -1.0;
+    for (int k = 0; k <= N; ++k) {
+        double v = f(lo + k * h);
+        if (v > best) {
+            best = v;
+            kbest = k;
+        }
+    }
+    double a = lo + std::max(kbest - 2, 0) * h, b = lo + std::min(kbest + 2, N) * h;
+    const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+    double x1 = b - g * (b - a), x2 = a + g * (b - a), f1 = f(x1), f2 = f(x2);
+    for (int it = 0; it < 200 && b - a > 1e-13; ++it) {
+        if (f1 > f2) {
+            b = x2;
+            x2 = x1;
+            f2 = f1;
+            x1 = b - g * (b - a);
+            f1 = f(x1);
+        } else {
+            a = x1;
+            x1 = x2;
+            f1 = f2;
+            x2 = a + g * (b - a);
+            f2 = f(x2);
+        }
+    }
+    return std::max(best, std::max(f1, f2));
+}
+
+void compute_bounds(bounce_ctx* c, const std::vector<double>& sig, const std::vector<double>& eps) {
+    const int T = c->n_types;
+    double qmin[BOUNCE_MAXT], qmax[BOUNCE_MAXT];
+    bool present[BOUNCE_MAXT] = {false};
+    for (int t = 0; t < T; ++t) qmin[t] = qmax[t] = 0.0;
+    for (int i = 0; i < c->n; ++i) {
+        int t = c->type[i];
+        double q = c->charge[i];
+        if (!present[t]) {
+            qmin[t] = qmax[t] = q;
+            present[t] = true;
+        } else {
+            qmin[t] = std::min(qmin[t], q);
+            qmax[t] = std::max(qmax[t], q);
+        }
+    }
+    for (int a = 0; a < BOUNCE_MAXT; ++a) c->Lstar[a] = 0.0;
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            double best = 0.0;
+            const double qa[2] = {qmin[a], qmax[a]}, qb[2] = {qmin[b], qmax[b]};
+            for (int x = 0; x < 2; ++x)
+                for (int y = 0; y < 2; ++y)
+                    best = std::max(best, sup_chi_dW(c->cfg, qa[x] * qb[y], sig[a * T + b], eps[a * T + b]));
+            c->L[a * T + b] = best * (1.0 + 1e-6);
+            c->Lstar[a] = std::max(c->Lstar[a], c->L[a * T + b]);
+        }
+}
+
+double r_list(const bounce_config& cfg) {
+    const bool cut = std::isfinite(cfg.r_cut) && cfg.r_cut > 0;
+    return cut ? cfg.r_cut + cfg.skin : INFINITY;
+}
+
+void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vector<double>& eps) {
+    Params& p = c->pp;
+    const bounce_config& g = c->cfg;
+    const int T = c->n_types;
+    for (int k = 0; k < BOUNCE_MAXT * BOUNCE_MAXT; ++k) p.c12[k] = p.c6[k] = 0.f;
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            double s6 = std::pow(sig[a * T + b], 6);
+            p.c12[a * BOUNCE_MAXT + b] = (float)(4.0 * eps[a * T + b] * s6 * s6);
+            p.c6[a * BOUNCE_MAXT + b] = (float)(4.0 * eps[a * T + b] * s6);
+        }
+    p.kcoul = (float)KCOUL_D;
+    const bool cut = std::isfinite(g.r_cut) && g.r_cut > 0;
+    const double rc2 = cut ? g.r_cut * g.r_cut : INFINITY;
+    p.rc2_lo = cut ? (float)(rc2 * (1.0 - 1e-5)) : INFINITY;
+    p.rc2_hi = cut ? (float)(rc2 * (1.0 + 1e-5)) : INFINITY;
+    p.rc2_d = rc2;
+    p.chi_step = g.r_off > g.r_on ? 0 : 1;
+    p.r_on = (float)g.r_on;
+    p.r_off = (float)g.r_off;
+    p.inv_span = g.r_off > g.r_on ? (float)(1.0 / (g.r_off - g.r_on)) : 0.f;
+    p.ebeta = (float)g.ewald_beta;
+    p.e2b_sqrtpi = (float)(2.0 * g.ewald_beta / std::sqrt(M_PI));
+    p.periodic = g.periodic;
+    for (int d = 0; d < 3; ++d) {
+        double Lb = g.periodic ? g.box[d] : 1.0;
+        p.Ld[d] = Lb;
+        p.Lhi[d] = (float)Lb;
+        p.Llo[d] = (float)(Lb - (double)p.Lhi[d]);
+        p.invL[d] = (float)(1.0 / Lb);
+    }
+    const double rl = r_list(g);
+    const double rl2 = rl * rl;
+    p.rlist2_d = rl2;
+    p.rlist2_lo = std::isfinite(rl2) ? (float)(rl2 * (1.0 - 1e-5)) : INFINITY;
+    p.rlist2_hi = std::isfinite(rl2) ? (float)(rl2 * (1.0 + 1e-5)) : INFINITY;
+    const double rs = g.r_off + g.skin;
+    p.rshort2 = (std::isfinite(rs) && rs < rl) ? (float)(rs * rs * (1.0 + 1e-4)) : INFINITY;
+    for (int a = 0; a < BOUNCE_MAXT; ++a) {
+        p.Lstar_d[a] = c->Lstar[a];
+        p.Lstar_f[a] = (float)c->Lstar[a];
+    }
+    p.beta = 1.0 / (KB_D * g.temperature_K);
+    p.dt = g.dt_fs;
+    p.c1 = std::exp(-g.gamma_per_fs * g.dt_fs);
+    p.skin_half2 = std::isfinite(rl) ? 0.25 * g.skin * g.skin : INFINITY;
+    p.key0 = (uint32_t)(g.seed & 0xFFFFFFFFull);
+    p.key1 = (uint32_t)(g.seed >> 32);
+}
+
+// Cell grid for the current host positions (edge > r_list).
+int setup_grid(bounce_ctx* c, const std::vector<double>& q) {
+    DevSys& s = c->ds;
+    const double rl = r_list(c->cfg);
+    const double edge_min = std::isfinite(rl) ? rl * (1.0 + 1e-5) + 1e-3 : INFINITY;
+    int nc[3] = {1, 1, 1};
+    float org[3] = {0.f, 0.f, 0.f}, ih[3] = {0.f, 0.f, 0.f};
+    for (int d = 0; d < 3; ++d) {
+        if (c->cfg.periodic) {
+            const double Lb = c->cfg.box[d];
+            nc[d] = std::isfinite(edge_min) ? std::max(1, (int)std::floor(Lb / edge_min)) : 1;
+            nc[d] = std::min(nc[d], 256);
+            ih[d] = (float)(nc[d] / Lb);
+        } else {
+            double lo = 1e300, hi = -1e300;
+            for (int i = 0; i < c->n; ++i) {
+                lo = std::min(lo, q[3 * i + d]);
+                hi = std::max(hi, q[3 * i + d]);
+            }
+            lo -= 5.0;
+            hi += 5.0;
+            const double ext = hi - lo;
+            if (std::isfinite(edge_min)) {
+                const double h = std::max(edge_min, ext / 128.0);
+                nc[d] = std::max(1, (int)std::floor(ext / h));
+                ih[d] = (float)(1.0 / h);
+            }
+            org[d] = (float)lo;
+        }
+    }
+    const int ncell = nc[0] * nc[1] * nc[2];
+    if (ncell > c->ncell_alloc) {
+        int r;
+        if ((r = dalloc(c, &s.cell_count, ncell)) || (r = dalloc(c, &s.cell_start, ncell + 1)) ||
+            (r = dalloc(c, &s.cell_fill, ncell)))
+            return r;
+        c->ncell_alloc = ncell;
+    }
+    s.ncx = nc[0];
+    s.ncy = nc[1];
+    s.ncz = nc[2];
+    s.ox = org[0];
+    s.oy = org[1];
+    s.oz = org[2];
+    s.ihx = ih[0];
+    s.ihy = ih[1];
+    s.ihz = ih[2];
+    return BOUNCE_OK;
+}
+
+// Launch the rebuild sequence (gated by the device flag unless forced).
+void rebuild(bounce_ctx* c, int step_off, bool force, cudaStream_t st) {
+    launch_rebuild(c->ds, c->pp, step_off, force, c->bitmap_warps, c->bitmap_bytes, st);
+}
+
+int check_err(bounce_ctx* c, cudaStream_t st) {
+    CU(cudaMemcpyAsync(c->h_err, c->ds.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (*c->h_err & BERR_RATE) {
+        cudaMemsetAsync(c->ds.err, 0, sizeof(int), st);
+        return fail(c, BOUNCE_ERR_NONFINITE, "a jump proposal mean was not finite or above 1e6 (the state blew up)");
+    }
+    if (*c->h_err & (BERR_LIST_OVERFLOW | BERR_SHORT_OVERFLOW)) {
+        const int e = *c->h_err;
+        cudaMemsetAsync(c->ds.err, 0, sizeof(int), st);
+        return fail(c, BOUNCE_ERR_LIST_OVERFLOW,
+                    (e & BERR_LIST_OVERFLOW) ? "a candidate row exceeded max_neighbors"
+                                             : "a short-range row exceeded max_short");
+    }
+    return BOUNCE_OK;
+}
+
+int ensure_graph(bounce_ctx* c, int integ) {
+    if (c->graph[integ]) return BOUNCE_OK;
+    cudaStream_t st = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < CHUNK; ++k) {
+        rebuild(c, k, false, st);
+        launch_step(c->ds, c->pp, integ, 1, k, st);
+    }
+    launch_advance_step(c->ds, CHUNK, st);
+    CU(cudaStreamEndCapture(st, &g));
+    cudaError_t e = cudaGraphInstantiate(&c->graph[integ], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, BOUNCE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return BOUNCE_OK;
+}
+
+bool finite_all(const std::vector<double>& x) {
+    for (double v : x)
+        if (!std::isfinite(v)) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bounce_config_default(bounce_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->dt_fs = 1.0;
+    cfg->gamma_per_fs = 0.001;
+    cfg->temperature_K = 300.0;
+    cfg->seed = 0;
+    cfg->r_on = 4.0;
+    cfg->r_off = 5.0;
+    cfg->r_cut = INFINITY;
+    cfg->skin = 1.0;
+    cfg->ewald_beta = 0.0;
+    cfg->periodic = 0;
+    cfg->max_neighbors = 2048;
+    cfg->max_short = 256;
+    cfg->device = 0;
+}
+
+int bounce_create(bounce_ctx** out, const bounce_config* cfg) {
+    bounce_ctx* c = nullptr;
+    if (!out || !cfg) return BOUNCE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!(cfg->dt_fs > 0) || !(cfg->temperature_K > 0) || cfg->gamma_per_fs < 0 || cfg->skin < 0 ||
+        cfg->max_neighbors < 1 || cfg->max_short < 1 || !(cfg->r_off >= cfg->r_on) || cfg->r_on < 0 ||
+        cfg->ewald_beta < 0)
+        return BOUNCE_ERR_INVALID_ARG;
+    if (cfg->periodic && !(cfg->box[0] > 0 && cfg->box[1] > 0 && cfg->box[2] > 0)) return BOUNCE_ERR_INVALID_ARG;
+    c = new bounce_ctx();
+    c->cfg = *cfg;
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return BOUNCE_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_cnt, CNT_N * sizeof(unsigned long long)) != cudaSuccess) {
+        delete c;
+        return BOUNCE_ERR_CUDA;
+    }
+    *out = c;
+    return BOUNCE_OK;
+}
+
+int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const double* mass, const double* charge,
+                        const int32_t* molecule, int32_t nb, const int32_t* bond_ij, const double* bond_k_r0,
+                        int32_t na, const int32_t* angle_ijk, const double* angle_k_t0) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (n < 1 || !type || !mass || !charge || !molecule || nb < 0 || na < 0 || (nb && (!bond_ij || !bond_k_r0)) ||
+        (na && (!angle_ijk || !angle_k_t0)))
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad topology arguments");
+    cudaSetDevice(c->cfg.device);
+    free_all(c);
+    c->ncell_alloc = 0;
+    c->have_topo = c->have_lj = c->have_state = false;
+    c->n = n;
+    c->type.assign(type, type + n);
+    c->mol.assign(molecule, molecule + n);
+    c->mass.assign(mass, mass + n);
+    c->charge.assign(charge, charge + n);
+    int maxt = 0;
+    for (int i = 0; i < n; ++i) {
+        if (type[i] < 0 || type[i] >= BOUNCE_MAXT) return fail(c, BOUNCE_ERR_INVALID_ARG, "atom type out of range");
+        if (!(mass[i] > 0) || !std::isfinite(charge[i])) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad mass or charge");
+        maxt = std::max(maxt, type[i] + 1);
+    }
+    c->n_types = maxt;
+    // bonded terms per atom
+    std::vector<std::vector<std::pair<int4, float2>>> per(n);
+    for (int b = 0; b < nb; ++b) {
+        int i = bond_ij[2 * b], j = bond_ij[2 * b + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad bond");
+        float2 kp = make_float2((float)bond_k_r0[2 * b], (float)bond_k_r0[2 * b + 1]);
+        per[i].push_back({make_int4(0, j, 0, 0), kp});
+        per[j].push_back({make_int4(0, i, 0, 0), kp});
+    }
+    for (int a = 0; a < na; ++a) {
+        int i = angle_ijk[3 * a], v = angle_ijk[3 * a + 1], k = angle_ijk[3 * a + 2];
+        if (i < 0 || v < 0 || k < 0 || i >= n || v >= n || k >= n || i == v || v == k || i == k)
+            return fail(c, BOUNCE_ERR_INVALID_ARG, "bad angle");
+        float2 kp = make_float2((float)angle_k_t0[2 * a], (float)angle_k_t0[2 * a + 1]);
+        per[i].push_back({make_int4(1, v, k, 0), kp});
+        per[k].push_back({make_int4(1, v, i, 0), kp});
+        per[v].push_back({make_int4(2, i, k, 0), kp});
+    }
+    c->bt_off.assign(n + 1, 0);
+    c->bt_idx.clear();
+    c->bt_par.clear();
+    for (int i = 0; i < n; ++i) {
+        c->bt_off[i + 1] = c->bt_off[i] + (int)per[i].size();
+        for (auto& t : per[i]) {
+            c->bt_idx.push_back(t.first);
+            c->bt_par.push_back(t.second);
+        }
+    }
+    // device buffers
+    DevSys& s = c->ds;
+    s.n = n;
+    int r;
+    for (int b = 0; b < 2; ++b) {
+        if ((r = dalloc(c, &s.qx[b], n)) || (r = dalloc(c, &s.qy[b], n)) || (r = dalloc(c, &s.qz[b], n)) ||
+            (r = dalloc(c, &s.phi[b], n)) || (r = dalloc(c, &s.plo[b], n)))
+            return r;
+    }
+    double *kick, *osd;
+    int *dtype, *dmol, *boff;
+    int4* bidx;
+    float2* bpar;
+    const double rl = r_list(c->cfg);
+    s.cap = std::isfinite(rl) ? c->cfg.max_neighbors : std::max(1, n - 1);
+    const double rs = c->cfg.r_off + c->cfg.skin;
+    s.caps = (std::isfinite(rs) && rs < rl) ? c->cfg.max_short : s.cap;
+    if ((r = dalloc(c, &s.vx, n)) || (r = dalloc(c, &s.vy, n)) || (r = dalloc(c, &s.vz, n)) ||
+        (r = dalloc(c, &kick, n)) || (r = dalloc(c, &osd, n)) || (r = dalloc(c, &dtype, n)) ||
+        (r = dalloc(c, &dmol, n)) || (r = dalloc(c, &boff, n + 1)) ||
+        (r = dalloc(c, &bidx, c->bt_idx.size())) || (r = dalloc(c, &bpar, c->bt_par.size())) ||
+        (r = dalloc(c, &s.nlong, n)) || (r = dalloc(c, &s.rows, (size_t)n * s.cap)) ||
+        (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, (size_t)n * s.caps)) ||
+        (r = dalloc(c, &s.refx, n)) || (r = dalloc(c, &s.refy, n)) || (r = dalloc(c, &s.refz, n)) ||
+        (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
+        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n)))
+        return r;
+    s.kick = kick;
+    s.osd = osd;
+    s.type = dtype;
+    s.mol = dmol;
+    s.bt_off = boff;
+    s.bt_idx = bidx;
+    s.bt_par = bpar;
+    s.step_base = c->d_step;
+    std::vector<double> hk(n), ho(n);
+    const double c1 = std::exp(-c->cfg.gamma_per_fs * c->cfg.dt_fs);
+    for (int i = 0; i < n; ++i) {
+        hk[i] = ACCEL_D / mass[i];
+        ho[i] = std::sqrt((1.0 - c1 * c1) * KB_D * c->cfg.temperature_K * ACCEL_D / mass[i]);
+    }
+    CU(cudaMemcpy(kick, hk.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(osd, ho.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dtype, type, n * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dmol, molecule, n * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(boff, c->bt_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    if (!c->bt_idx.empty()) {
+        CU(cudaMemcpy(bidx, c->bt_idx.data(), c->bt_idx.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(bpar, c->bt_par.data(), c->bt_par.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    // charge and type ride in the w slots of the split positions
+    std::vector<float4> hh(n), hl(n);
+    for (int i = 0; i < n; ++i) {
+        int t = type[i];
+        float tf;
+        std::memcpy(&tf, &t, 4);
+        hh[i] = make_float4(0.f, 0.f, 0.f, (float)charge[i]);
+        hl[i] = make_float4(0.f, 0.f, 0.f, tf);
+    }
+    for (int b = 0; b < 2; ++b) {
+        CU(cudaMemcpy(s.phi[b], hh.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(s.plo[b], hl.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    }
+    // bitmap shared memory of the row builder
+    int dev = c->cfg.device, optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t words = (size_t)(n + 31) / 32;
+    const size_t per_warp = words * 4;
+    if (per_warp > (size_t)optin) return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for the row builder bitmap");
+    c->bitmap_warps = (int)std::min<size_t>(8, (size_t)optin / per_warp);
+    c->bitmap_bytes = per_warp * c->bitmap_warps;
+    nlist_set_smem_limit(c->bitmap_bytes);
+    c->have_topo = true;
+    return BOUNCE_OK;
+}
+
+int bounce_set_lj(bounce_ctx* c, int32_t T, const double* sigma, const double* eps) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_topo) return fail(c, BOUNCE_ERR_STATE, "set the topology first");
+    if (T < c->n_types || T > BOUNCE_MAXT || !sigma || !eps) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad LJ table");
+    std::vector<double> sg(c->n_types * c->n_types), ep(c->n_types * c->n_types);
+    for (int a = 0; a < c->n_types; ++a)
+        for (int b = 0; b < c->n_types; ++b) {
+            sg[a * c->n_types + b] = sigma[a * T + b];
+            ep[a * c->n_types + b] = eps[a * T + b];
+        }
+    compute_bounds(c, sg, ep);
+    fill_params(c, sg, ep);
+    drop_graphs(c);
+    c->have_lj = true;
+    return BOUNCE_OK;
+}
+
+int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t step, int32_t where, void* stream) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_topo || !c->have_lj) return fail(c, BOUNCE_ERR_STATE, "set the topology and LJ table first");
+    if (!q || !v || (where != BOUNCE_HOST && where != BOUNCE_DEVICE) || step < 0)
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad state arguments");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = c->n;
+    std::vector<double> hq(3 * (size_t)n), hv(3 * (size_t)n);
+    if (where == BOUNCE_HOST) {
+        std::memcpy(hq.data(), q, hq.size() * sizeof(double));
+        std::memcpy(hv.data(), v, hv.size() * sizeof(double));
+    } else {
+        CU(cudaMemcpyAsync(hq.data(), q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(hv.data(), v, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    if (!finite_all(hq) || !finite_all(hv)) return fail(c, BOUNCE_ERR_NONFINITE, "non-finite position or velocity");
+    int r = setup_grid(c, hq);
+    if (r) return r;
+    drop_graphs(c);
+    const int cur = (int)(step & 1);
+    std::vector<double> cx(n), cy(n), cz(n), vx(n), vy(n), vz(n);
+    for (int i = 0; i < n; ++i) {
+        cx[i] = hq[3 * i];
+        cy[i] = hq[3 * i + 1];
+        cz[i] = hq[3 * i + 2];
+        vx[i] = hv[3 * i];
+        vy[i] = hv[3 * i + 1];
+        vz[i] = hv[3 * i + 2];
+    }
+    DevSys& s = c->ds;
+    CU(cudaMemcpyAsync(s.qx[cur], cx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s.qy[cur], cy.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s.qz[cur], cz.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s.vx, vx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s.vy, vy.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s.vz, vz.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    long long st0 = step;
+    CU(cudaMemcpyAsync(c->d_step, &st0, sizeof(long long), cudaMemcpyHostToDevice, st));
+    launch_pack_positions(s, c->pp, cur, st);
+    const int one = 1;
+    CU(cudaMemcpyAsync(s.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(s.err, 0, sizeof(int), st));
+    CU(cudaStreamSynchronize(st));
+    c->step0 = step;
+    c->have_state = true;
+    return BOUNCE_OK;
+}
+
+int bounce_get_state(bounce_ctx* c, double* q, double* v, int32_t where, void* stream) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    if (where != BOUNCE_HOST && where != BOUNCE_DEVICE) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad where");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = c->n;
+    long long step;
+    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const int cur = (int)(step & 1);
+    DevSys& s = c->ds;
+    const cudaMemcpyKind kind = where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    // strided copies interleave the SoA device arrays into (n, 3) rows
+    if (q) {
+        CU(cudaMemcpy2DAsync(q + 0, 3 * sizeof(double), s.qx[cur], sizeof(double), sizeof(double), n, kind, st));
+        CU(cudaMemcpy2DAsync(q + 1, 3 * sizeof(double), s.qy[cur], sizeof(double), sizeof(double), n, kind, st));
+        CU(cudaMemcpy2DAsync(q + 2, 3 * sizeof(double), s.qz[cur], sizeof(double), sizeof(double), n, kind, st));
+    }
+    if (v) {
+        CU(cudaMemcpy2DAsync(v + 0, 3 * sizeof(double), s.vx, sizeof(double), sizeof(double), n, kind, st));
+        CU(cudaMemcpy2DAsync(v + 1, 3 * sizeof(double), s.vy, sizeof(double), sizeof(double), n, kind, st));
+        CU(cudaMemcpy2DAsync(v + 2, 3 * sizeof(double), s.vz, sizeof(double), sizeof(double), n, kind, st));
+    }
+    if (where == BOUNCE_HOST) CU(cudaStreamSynchronize(st));
+    return BOUNCE_OK;
+}
+
+int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    if (n_steps < 0 || (integ != BOUNCE_BAOAB && integ != BOUNCE_BOUNCE))
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad run arguments");
+    if (n_steps == 0) return BOUNCE_OK;
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = ensure_graph(c, integ);
+    if (r) return r;
+    // head: B/2 [J] A O A at the current step
+    rebuild(c, 0, false, st);
+    launch_step(c->ds, c->pp, integ, 0, 0, st);
+    launch_advance_step(c->ds, 1, st);
+    int64_t rem = n_steps - 1;
+    while (rem >= CHUNK) {
+        CU(cudaGraphLaunch(c->graph[integ], st));
+        rem -= CHUNK;
+    }
+    for (int64_t k = 0; k < rem; ++k) {
+        rebuild(c, (int)k, false, st);
+        launch_step(c->ds, c->pp, integ, 1, (int)k, st);
+    }
+    if (rem) launch_advance_step(c->ds, rem, st);
+    // tail: [J] B/2
+    rebuild(c, 0, false, st);
+    launch_step(c->ds, c->pp, integ, 2, 0, st);
+    CU(cudaGetLastError());
+    return check_err(c, st);
+}
+
+int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
+    if (!c || !out) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    long long step;
+    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    rebuild(c, 0, false, st);
+    launch_energies(c->ds, c->pp, (int)(step & 1), c->terms, st);
+    double tot[5];
+    CU(cudaMemcpyAsync(tot, c->terms + 5 * (size_t)c->n, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(c->h_cnt, c->ds.cnt, CNT_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    int r = check_err(c, st);
+    if (r) return r;
+    out->coulomb = KCOUL_D / (double)c->pp.kcoul * tot[0];
+    out->lj = tot[1];
+    out->bond = tot[2];
+    out->angle = tot[3];
+    out->kinetic = tot[4];
+    out->potential = out->coulomb + out->lj + out->bond + out->angle;
+    out->temperature = 2.0 * tot[4] / (3.0 * c->n * KB_D);
+    out->step = step - c->step0;
+    out->proposals = (int64_t)c->h_cnt[CNT_PROPOSALS];
+    out->accepts = (int64_t)c->h_cnt[CNT_ACCEPTS];
+    out->near_ties = (int64_t)c->h_cnt[CNT_NEAR];
+    out->rebuilds = (int64_t)c->h_cnt[CNT_REBUILDS];
+    out->short_pairs = (int64_t)c->h_cnt[CNT_SHORT_PAIRS];
+    out->full_pairs = (int64_t)c->h_cnt[CNT_FULL_PAIRS];
+    return BOUNCE_OK;
+}
+
+int bounce_reset_counters(bounce_ctx* c, void* stream) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_topo) return fail(c, BOUNCE_ERR_STATE, "no topology");
+    cudaSetDevice(c->cfg.device);
+    CU(cudaMemsetAsync(c->ds.cnt, 0, CNT_N * sizeof(unsigned long long), (cudaStream_t)stream));
+    return BOUNCE_OK;
+}
+
+int bounce_get_bounds(bounce_ctx* c, double* L, double* Lstar) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_lj) return fail(c, BOUNCE_ERR_STATE, "no LJ table");
+    const int T = c->n_types;
+    if (L)
+        for (int k = 0; k < T * T; ++k) L[k] = c->L[k];
+    if (Lstar)
+        for (int k = 0; k < T; ++k) Lstar[k] = c->Lstar[k];
+    return BOUNCE_OK;
+}
+
+int bounce_compute_gradient(bounce_ctx* c, int32_t part, double* grad, int32_t where, void* stream) {
+    if (!c || !grad || part < 0 || part > 2 || (where != BOUNCE_HOST && where != BOUNCE_DEVICE))
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad gradient arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    long long step;
+    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    rebuild(c, 0, false, st);
+    double* out = c->terms;  // scratch of 6 n doubles >= 3 n
+    launch_gradient(c->ds, c->pp, part, (int)(step & 1), out, st);
+    CU(cudaMemcpyAsync(grad, out, 3 * (size_t)c->n * sizeof(double),
+                       where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return check_err(c, st);
+}
+
+int bounce_jump_half(bounce_ctx* c, int64_t step, int32_t stream_id, int32_t* M, int32_t* nacc, int32_t where,
+                     void* stream) {
+    if (!c || step < 0 || stream_id < 0 || stream_id > 255 || (where != BOUNCE_HOST && where != BOUNCE_DEVICE))
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad jump arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    long long cur_step;
+    CU(cudaMemcpyAsync(&cur_step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    rebuild(c, 0, false, st);
+    int* dM = nullptr;
+    int* dA = nullptr;
+    if (M || nacc) {
+        int* tmp = (int*)c->terms;  // 12 n ints of scratch
+        dM = tmp;
+        dA = tmp + c->n;
+    }
+    launch_jump_half(c->ds, c->pp, (int)(cur_step & 1), step, stream_id, dM, dA, st);
+    const cudaMemcpyKind kind = where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (M) CU(cudaMemcpyAsync(M, dM, c->n * sizeof(int), kind, st));
+    if (nacc) CU(cudaMemcpyAsync(nacc, dA, c->n * sizeof(int), kind, st));
+    CU(cudaStreamSynchronize(st));
+    return check_err(c, st);
+}
+
+int bounce_get_rows(bounce_ctx* c, int32_t* counts, int32_t* rows, int32_t capacity) {
+    if (!c || !counts || !rows || capacity < 1) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad row arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    cudaSetDevice(c->cfg.device);
+    rebuild(c, 0, false, nullptr);
+    CU(cudaDeviceSynchronize());
+    int r = check_err(c, nullptr);
+    if (r) return r;
+    const int n = c->n, cap = c->ds.cap;
+    std::vector<int> cnt(n), all((size_t)n * cap);
+    CU(cudaMemcpy(cnt.data(), c->ds.nlong, n * sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(all.data(), c->ds.rows, all.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) {
+        counts[i] = cnt[i];
+        for (int k = 0; k < std::min(cnt[i], capacity); ++k) rows[(size_t)i * capacity + k] = all[(size_t)i * cap + k];
+    }
+    return BOUNCE_OK;
+}
+
+const char* bounce_last_error(const bounce_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void bounce_destroy(bounce_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->cfg.device);
+    free_all(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    delete c;
+}
+
+}  // extern "C"

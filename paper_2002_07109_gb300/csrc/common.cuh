@@ -1,0 +1,322 @@
+// Shared device-side definitions of the BOUNCE library: the system view
+// passed to every kernel, the Philox4x32-10 generator, the FP32 exp(-x) and
+// Poisson inversion used by the jump step, and the FP32 pair terms.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define BOUNCE_MAXT 4
+#define BOUNCE_GROUP 32                // atoms per CTA in the fused step kernels
+#define BOUNCE_POISSON_SLOT 0x80000000u
+#define BOUNCE_STREAM_O 0u
+#define BOUNCE_STREAM_J1 1u
+#define BOUNCE_STREAM_J2 2u
+
+// Error bits set by kernels (ctx->err).
+#define BERR_LIST_OVERFLOW 1
+#define BERR_SHORT_OVERFLOW 2
+#define BERR_RATE 4               // a jump proposal mean was not finite or above 1e6
+
+// Counter slots (unsigned long long).
+enum { CNT_PROPOSALS = 0, CNT_ACCEPTS, CNT_NEAR, CNT_REBUILDS, CNT_SHORT_PAIRS, CNT_FULL_PAIRS, CNT_N };
+
+constexpr double KCOUL_D = 332.063713;
+constexpr double KB_D = 0.0019872041;
+constexpr double ACCEL_D = 4.184e-4;
+
+// Device pointers of one system (passed by value).
+struct DevSys {
+    int n;
+    double* qx[2];
+    double* qy[2];
+    double* qz[2];
+    float4* phi[2];  // (x, y, z) high FP32 part of the (wrapped) position, w = charge
+    float4* plo[2];  // (x, y, z) low FP32 part, w = type (bit pattern of an int)
+    double* vx;
+    double* vy;
+    double* vz;
+    const double* kick;  // 4.184e-4 / m
+    const double* osd;   // sqrt((1 - c1^2) k_B T 4.184e-4 / m)
+    const int* type;
+    const int* mol;
+    // bonded terms touching each atom: bt_off[n + 1], bt_idx (role, o1, o2, -), bt_par (k, x0)
+    const int* bt_off;
+    const int4* bt_idx;
+    const float2* bt_par;
+    // candidate rows (r < r_list) and short rows (r < r_off + skin)
+    int* nlong;
+    int* rows;
+    int cap;
+    int* nshort;
+    int* srows;
+    int caps;
+    double* refx;
+    double* refy;
+    double* refz;
+    // cell grid
+    int* cell_count;
+    int* cell_start;
+    int* cell_fill;
+    int* cell_atoms;
+    int ncx, ncy, ncz;
+    float ox, oy, oz;        // grid origin (droplets)
+    float ihx, ihy, ihz;     // inverse cell edges
+    // flags and counters
+    int* rebuild;            // 1 = rows must be rebuilt before the next evaluation
+    int* err;
+    unsigned long long* cnt;
+    const long long* step_base;
+};
+
+// Scalar parameters (passed by value; fits the kernel parameter space).
+struct Params {
+    float c12[BOUNCE_MAXT * BOUNCE_MAXT];  // 4 eps sigma^12
+    float c6[BOUNCE_MAXT * BOUNCE_MAXT];   // 4 eps sigma^6
+    float kcoul;
+    float rc2_lo, rc2_hi;  // FP32 screening band around r_c^2 (+inf = no cutoff)
+    double rc2_d;          // exact FP64 cutoff test r^2 < r_c^2
+    float r_on, inv_span;
+    int chi_step;        // 1: chi = indicator of [r_off, inf)
+    float r_off;
+    float ebeta, e2b_sqrtpi;  // Ewald beta and 2 beta / sqrt(pi); ebeta = 0: bare Coulomb
+    int periodic;
+    float Lhi[3], Llo[3], invL[3];
+    double Ld[3];
+    float rlist2_lo, rlist2_hi;  // FP32 screening band around r_list^2
+    double rlist2_d;             // exact FP64 threshold r_list^2 (+inf = all)
+    float rshort2;               // short-row threshold
+    float Lstar_f[BOUNCE_MAXT];
+    double Lstar_d[BOUNCE_MAXT];
+    double beta;
+    double dt;
+    double c1;
+    double skin_half2;
+    uint32_t key0, key1;
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64 multiplies with the round constants, key bumped by the Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Counter (slot, atom, step mod 2^32, stream << 24 | step >> 32 mod 2^24).
+__device__ __forceinline__ uint4 rng_draw(const Params& p, uint32_t slot, uint32_t atom, long long step,
+                                          uint32_t stream) {
+    uint4 c = make_uint4(slot, atom, (uint32_t)(step & 0xFFFFFFFFll),
+                         (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFll));
+    return philox4x32_10(c, p.key0, p.key1);
+}
+
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-08f; }
+__device__ __forceinline__ float u24_open0(uint32_t x) { return (float)((x >> 8) + 1u) * 5.9604644775390625e-08f; }
+__device__ __forceinline__ double u53(uint32_t x1, uint32_t x2) {
+    return __dmul_rn(__dadd_rn(__dmul_rn((double)(x1 >> 5), 67108864.0), (double)(x2 >> 6)),
+                     1.1102230246251565e-16);
+}
+
+// ------------------------------------------------------- FP32 exp(-x), Poisson
+// exp(-x) for x in [0, 32]: x = n ln2 + r with n = floor(x log2 e + 1/2)
+// (two-constant reduction), exp(-r) by its Taylor polynomial of degree 7
+// (coefficients (-1)^k / k!), scaled by 2^-n.  Every operation is an explicit
+// round-to-nearest FP32 operation so the result does not depend on
+// contraction choices.
+__device__ __forceinline__ float expneg_f32(float x) {
+    const float LOG2E = (float)(1.0 / 0.6931471805599453094);
+    const float LN2_HI = 0.693145751953125f;
+    const float LN2_LO = (float)(0.6931471805599453094 - 0.693145751953125);
+    const float C0 = 1.0f, C1 = -1.0f, C2 = (float)(1.0 / 2.0), C3 = (float)(-1.0 / 6.0),
+                C4 = (float)(1.0 / 24.0), C5 = (float)(-1.0 / 120.0), C6 = (float)(1.0 / 720.0),
+                C7 = (float)(-1.0 / 5040.0);
+    float t = __fmul_rn(x, LOG2E);
+    float n = floorf(__fadd_rn(t, 0.5f));
+    float r = __fsub_rn(__fsub_rn(x, __fmul_rn(n, LN2_HI)), __fmul_rn(n, LN2_LO));
+    float q = C7;
+    q = __fadd_rn(__fmul_rn(q, r), C6);
+    q = __fadd_rn(__fmul_rn(q, r), C5);
+    q = __fadd_rn(__fmul_rn(q, r), C4);
+    q = __fadd_rn(__fmul_rn(q, r), C3);
+    q = __fadd_rn(__fmul_rn(q, r), C2);
+    q = __fadd_rn(__fmul_rn(q, r), C1);
+    q = __fadd_rn(__fmul_rn(q, r), C0);
+    return __fmul_rn(q, ldexpf(1.0f, -(int)n));
+}
+
+// One Poisson(mu_c) count by sequential search of the CDF in FP32
+// (mu_c <= 16); stops when the CDF passes u, when adding a term no longer
+// changes it, or at k = 128.
+__device__ __forceinline__ int poisson_invert_f32(float u, float mu_c) {
+    float p = expneg_f32(mu_c);
+    float cdf = p;
+    int k = 0;
+    while (u > cdf && k < 128) {
+        ++k;
+        float pk = __fmul_rn(__fmul_rn(p, mu_c), __frcp_rn((float)k));
+        float cn = __fadd_rn(cdf, pk);
+        if (cn == cdf) break;
+        p = pk;
+        cdf = cn;
+    }
+    return k;
+}
+
+// ------------------------------------------------------------- pair terms
+// Displacement q_i - q_j from the split FP32 positions (hi + lo), minimum
+// image under periodic boundaries.
+__device__ __forceinline__ float3 pair_disp(const Params& p, float4 hi, float4 lo, float4 hj, float4 lj) {
+    float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
+    float ex = lo.x - lj.x, ey = lo.y - lj.y, ez = lo.z - lj.z;
+    if (p.periodic) {
+        float kx = rintf(dx * p.invL[0]), ky = rintf(dy * p.invL[1]), kz = rintf(dz * p.invL[2]);
+        dx = fmaf(-kx, p.Lhi[0], dx);
+        dy = fmaf(-ky, p.Lhi[1], dy);
+        dz = fmaf(-kz, p.Lhi[2], dz);
+        ex = fmaf(-kx, p.Llo[0], ex);
+        ey = fmaf(-ky, p.Llo[1], ey);
+        ez = fmaf(-kz, p.Llo[2], ez);
+    }
+    return make_float3(dx + ex, dy + ey, dz + ez);
+}
+
+// W'(r) / r of one pair (Coulomb or Ewald direct + LJ), r2 < rc2 assumed.
+__device__ __forceinline__ float pair_dW_over_r(const Params& p, float r2, float qq, int tp) {
+    float ir = rsqrtf(r2);
+    float ir2 = ir * ir;
+    float w;
+    if (p.ebeta > 0.f) {
+        float r = r2 * ir;
+        float br = p.ebeta * r;
+        w = -qq * (erfcf(br) * ir2 + p.e2b_sqrtpi * __expf(-br * br) * ir) * ir;
+    } else {
+        w = -qq * ir2 * ir;
+    }
+    float c12 = p.c12[tp];
+    if (c12 != 0.f) {
+        float ir6 = ir2 * ir2 * ir2;
+        w -= (12.f * c12 * ir6 - 6.f * p.c6[tp]) * ir6 * ir2;
+    }
+    return w;
+}
+
+// Switching function chi(r) (quintic smoothstep on [r', r'']).
+__device__ __forceinline__ float chi_of(const Params& p, float r) {
+    if (p.chi_step) return r >= p.r_off ? 1.f : 0.f;
+    float s = fminf(fmaxf((r - p.r_on) * p.inv_span, 0.f), 1.f);
+    return s * s * s * (10.f + s * (-15.f + 6.f * s));
+}
+
+// Pair energy W(r) components (Coulomb or erfc, LJ), r2 < rc2 assumed.
+__device__ __forceinline__ void pair_W(const Params& p, float r2, float qq, int tp, float& ec, float& el) {
+    float ir = rsqrtf(r2);
+    if (p.ebeta > 0.f) {
+        float r = r2 * ir;
+        ec = qq * erfcf(p.ebeta * r) * ir;
+    } else {
+        ec = qq * ir;
+    }
+    float c12 = p.c12[tp];
+    el = 0.f;
+    if (c12 != 0.f) {
+        float ir2 = ir * ir;
+        float ir6 = ir2 * ir2 * ir2;
+        el = (c12 * ir6 - p.c6[tp]) * ir6;
+    }
+}
+
+// Exact FP64 r_ij^2 with the minimum image d - L rint(d / L), evaluated as
+// (dx dx + dy dy) + dz dz with round-to-nearest and no contraction.
+__device__ __forceinline__ double exact_r2(const DevSys& s, const Params& p, int cur, int i, int j) {
+    double dx = __dsub_rn(s.qx[cur][i], s.qx[cur][j]);
+    double dy = __dsub_rn(s.qy[cur][i], s.qy[cur][j]);
+    double dz = __dsub_rn(s.qz[cur][i], s.qz[cur][j]);
+    if (p.periodic) {
+        dx = __dsub_rn(dx, __dmul_rn(p.Ld[0], rint(__ddiv_rn(dx, p.Ld[0]))));
+        dy = __dsub_rn(dy, __dmul_rn(p.Ld[1], rint(__ddiv_rn(dy, p.Ld[1]))));
+        dz = __dsub_rn(dz, __dmul_rn(p.Ld[2], rint(__ddiv_rn(dz, p.Ld[2]))));
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Pair cutoff test r^2 < r_c^2: decided in FP32 outside a narrow band around
+// r_c^2 and exactly in FP64 inside it.
+__device__ __forceinline__ bool inside_cut(const DevSys& s, const Params& p, int cur, int i, int j, float r2f) {
+    if (r2f < p.rc2_lo) return true;
+    if (!(r2f <= p.rc2_hi)) return false;
+    return exact_r2(s, p, cur, i, j) < p.rc2_d;
+}
+
+__device__ __forceinline__ int type_of(float4 lo) { return __float_as_int(lo.w); }
+
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ int warp_sum_i(int x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Gradient on atom i of the bonded terms listed for it (FP32 from split
+// positions).  role 0: bond to o1; role 1: angle end (vertex o1, other end
+// o2); role 2: angle vertex (ends o1, o2).
+__device__ __forceinline__ float3 bonded_grad(const Params& p, const DevSys& s, int cur, int i, int4 t, float2 kp) {
+    float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if (t.x == 0) {
+        float3 d = pair_disp(p, hi, lo, s.phi[cur][t.y], s.plo[cur][t.y]);
+        float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        float c = 2.f * kp.x * (r - kp.y) / r;
+        g = make_float3(c * d.x, c * d.y, c * d.z);
+    } else {
+        // angle a-b-c with b the vertex
+        int a, b, c;
+        if (t.x == 1) { a = i; b = t.y; c = t.z; } else { a = t.y; b = i; c = t.z; }
+        float4 hb = s.phi[cur][b], lb = s.plo[cur][b];
+        float3 u = pair_disp(p, s.phi[cur][a], s.plo[cur][a], hb, lb);
+        float3 w = pair_disp(p, s.phi[cur][c], s.plo[cur][c], hb, lb);
+        float nu2 = u.x * u.x + u.y * u.y + u.z * u.z, nw2 = w.x * w.x + w.y * w.y + w.z * w.z;
+        float inuw = rsqrtf(nu2 * nw2);
+        float cs = (u.x * w.x + u.y * w.y + u.z * w.z) * inuw;
+        cs = fminf(fmaxf(cs, -1.f), 1.f);
+        float th = acosf(cs);
+        float sn = sqrtf(fmaxf(1.f - cs * cs, 1e-12f));
+        float dE = 2.f * kp.x * (th - kp.y);
+        // d theta / d a = -(w/(|u||w|) - cos u/|u|^2) / sin ; same for c with u <-> w
+        float fa = -dE / sn;
+        float3 ga = make_float3(fa * (w.x * inuw - cs * u.x / nu2), fa * (w.y * inuw - cs * u.y / nu2),
+                                fa * (w.z * inuw - cs * u.z / nu2));
+        if (t.x == 1) {
+            g = ga;
+        } else {
+            float3 gc = make_float3(fa * (u.x * inuw - cs * w.x / nw2), fa * (u.y * inuw - cs * w.y / nw2),
+                                    fa * (u.z * inuw - cs * w.z / nw2));
+            g = make_float3(-(ga.x + gc.x), -(ga.y + gc.y), -(ga.z + gc.z));
+        }
+    }
+    return g;
+}
+
+// Launchers implemented in the .cu files.
+void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
+                    cudaStream_t st);
+void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, cudaStream_t st);
+void launch_gradient(const DevSys& s, const Params& p, int part, int cur, double* out, cudaStream_t st);
+void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,
+                      cudaStream_t st);
+void launch_energies(const DevSys& s, const Params& p, int cur, double* terms, cudaStream_t st);
+void launch_advance_step(const DevSys& s, long long by, cudaStream_t st);
+void launch_pack_positions(const DevSys& s, const Params& p, int cur, cudaStream_t st);

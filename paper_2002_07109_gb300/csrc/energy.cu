@@ -1,0 +1,121 @@
+// Energies of the current state (unsplit W, paper Sec. IV.A / V) and the
+// position packing used after a state upload.
+//
+// Pair energies: one warp per atom sums W over the members j > i of its row
+// with r < r_c (FP32 per pair, FP32 per lane, FP64 across lanes); bonded and
+// kinetic terms per atom in FP64.  The per-atom terms are then summed by one
+// CTA in a fixed order, so totals are deterministic.
+#include "common.cuh"
+
+namespace {
+
+// terms layout: [5][n] = coulomb, lj, bond, angle, kinetic per atom
+__global__ void k_atom_energies(DevSys s, Params p, int cur, double* terms) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= s.n) return;
+    const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
+    const int ti = type_of(lo);
+    const int n = s.nlong[i];
+    const int* row = s.rows + (size_t)i * s.cap;
+    float ec = 0.f, el = 0.f;
+    for (int k = lane; k < n; k += 32) {
+        const int j = row[k];
+        if (j <= i) continue;
+        const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
+        const float3 d = pair_disp(p, hi, lo, hj, lj);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        if (inside_cut(s, p, cur, i, j, r2)) {
+            float a, b;
+            pair_W(p, r2, p.kcoul * hi.w * hj.w, ti * BOUNCE_MAXT + type_of(lj), a, b);
+            ec += a;
+            el += b;
+        }
+    }
+    double dc = ec, dl = el;
+    for (int o = 16; o > 0; o >>= 1) {
+        dc += __shfl_xor_sync(0xffffffffu, dc, o);
+        dl += __shfl_xor_sync(0xffffffffu, dl, o);
+    }
+    // bonded terms owned by atom i: bonds with i < partner, angles at their vertex
+    double eb = 0.0, ea = 0.0;
+    for (int t = s.bt_off[i] + lane; t < s.bt_off[i + 1]; t += 32) {
+        const int4 b = s.bt_idx[t];
+        const float2 kp = s.bt_par[t];
+        if (b.x == 0 && i < b.y) {
+            const float3 d = pair_disp(p, hi, lo, s.phi[cur][b.y], s.plo[cur][b.y]);
+            const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+            eb += (double)(kp.x * (r - kp.y) * (r - kp.y));
+        } else if (b.x == 2) {
+            const float4 ha = s.phi[cur][b.y], la = s.plo[cur][b.y], hc = s.phi[cur][b.z], lc = s.plo[cur][b.z];
+            const float3 u = pair_disp(p, ha, la, hi, lo);
+            const float3 w = pair_disp(p, hc, lc, hi, lo);
+            float cs = (u.x * w.x + u.y * w.y + u.z * w.z) *
+                       rsqrtf((u.x * u.x + u.y * u.y + u.z * u.z) * (w.x * w.x + w.y * w.y + w.z * w.z));
+            cs = fminf(fmaxf(cs, -1.f), 1.f);
+            const float th = acosf(cs) - kp.y;
+            ea += (double)(kp.x * th * th);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        eb += __shfl_xor_sync(0xffffffffu, eb, o);
+        ea += __shfl_xor_sync(0xffffffffu, ea, o);
+    }
+    if (lane == 0) {
+        const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
+        terms[0 * (size_t)s.n + i] = dc;
+        terms[1 * (size_t)s.n + i] = dl;
+        terms[2 * (size_t)s.n + i] = eb;
+        terms[3 * (size_t)s.n + i] = ea;
+        // 1/2 m v^2 with m = 4.184e-4 / kick, in kcal/mol: 1/2 v^2 / kick
+        terms[4 * (size_t)s.n + i] = 0.5 * (vx * vx + vy * vy + vz * vz) / s.kick[i];
+    }
+}
+
+// Fixed-order sum of the 5 per-atom term arrays into out[5] by one CTA.
+__global__ void k_sum_terms(int n, const double* terms, double* out) {
+    __shared__ double part[5][256];
+    for (int t = 0; t < 5; ++t) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) acc += terms[(size_t)t * n + i];
+        part[t][threadIdx.x] = acc;
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int t = 0; t < 5; ++t) part[t][threadIdx.x] += part[t][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = part[threadIdx.x][0];
+}
+
+// Split FP32 copies (hi + lo) of the FP64 positions of buffer `cur`;
+// positions are wrapped into the box for periodic systems.
+__global__ void k_pack(DevSys s, Params p, int cur) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        double x = s.qx[cur][i], y = s.qy[cur][i], z = s.qz[cur][i];
+        if (p.periodic) {
+            x -= p.Ld[0] * floor(x / p.Ld[0]);
+            y -= p.Ld[1] * floor(y / p.Ld[1]);
+            z -= p.Ld[2] * floor(z / p.Ld[2]);
+        }
+        const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
+        const float4 oh = s.phi[cur][i];
+        const float4 ol = s.plo[cur][i];
+        s.phi[cur][i] = make_float4(hx, hy, hz, oh.w);
+        s.plo[cur][i] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
+                                    __double2float_rn(z - (double)hz), ol.w);
+    }
+}
+
+}  // namespace
+
+void launch_energies(const DevSys& s, const Params& p, int cur, double* terms, cudaStream_t st) {
+    const int wpb = 8;
+    k_atom_energies<<<(s.n + wpb - 1) / wpb, wpb * 32, 0, st>>>(s, p, cur, terms);
+    k_sum_terms<<<1, 256, 0, st>>>(s.n, terms, terms + 5 * (size_t)s.n);
+}
+
+void launch_pack_positions(const DevSys& s, const Params& p, int cur, cudaStream_t st) {
+    k_pack<<<(s.n + 255) / 256, 256, 0, st>>>(s, p, cur);
+}

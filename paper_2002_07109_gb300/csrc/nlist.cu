@@ -1,0 +1,235 @@
+// Candidate rows of the jump step and the pair sums (paper Sec. V, first
+// paragraph: the partner J of atom i is drawn uniformly among the particles
+// interacting with i).  Row of atom i: every atom j of another molecule with
+// r_ij^2 < r_list^2 (FP64, minimum image), in ascending j.
+//
+// GPU design: a cell grid of edge > r_list (counting sort: count, scan,
+// scatter), then one warp per atom scans the 27 neighbour cells, screens each
+// candidate in FP32 from the split positions and settles the few candidates
+// near r_list exactly in FP64.  Accepted candidates set a bit in a per-warp
+// bitmap over all atom indices in shared memory; reading the bitmap back in
+// word order yields the row already in ascending order (no sort), and
+// duplicate visits of a cell (grids narrower than 3 cells) are harmless.
+// Every kernel returns at once unless a rebuild is pending (the step kernel
+// raises the flag when an atom has moved more than skin/2 since the last
+// build), so the sequence can sit in a captured CUDA graph.
+#include "common.cuh"
+
+namespace {
+
+__device__ __forceinline__ bool pending(const DevSys& s, int force) { return force || *s.rebuild; }
+
+__device__ __forceinline__ void cell_of(const DevSys& s, const Params& p, float4 hi, int& cx, int& cy, int& cz) {
+    if (p.periodic) {
+        cx = min(max((int)(hi.x * s.ihx), 0), s.ncx - 1);
+        cy = min(max((int)(hi.y * s.ihy), 0), s.ncy - 1);
+        cz = min(max((int)(hi.z * s.ihz), 0), s.ncz - 1);
+    } else {
+        cx = min(max((int)floorf((hi.x - s.ox) * s.ihx), 0), s.ncx - 1);
+        cy = min(max((int)floorf((hi.y - s.oy) * s.ihy), 0), s.ncy - 1);
+        cz = min(max((int)floorf((hi.z - s.oz) * s.ihz), 0), s.ncz - 1);
+    }
+}
+
+__global__ void k_cells_count(DevSys s, Params p, int step_off, int force) {
+    if (!pending(s, force)) return;
+    int cur = (int)((*s.step_base + step_off) & 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        int cx, cy, cz;
+        cell_of(s, p, s.phi[cur][i], cx, cy, cz);
+        atomicAdd(&s.cell_count[(cz * s.ncy + cy) * s.ncx + cx], 1);
+    }
+}
+
+// Exclusive scan of the cell counts by one CTA; resets the counts to zero
+// for the next rebuild.
+__global__ void k_cells_scan(DevSys s, int force) {
+    if (!pending(s, force)) return;
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    int nc = s.ncx * s.ncy * s.ncz;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nc; base += blockDim.x) {
+        int c = base + threadIdx.x;
+        int v = c < nc ? s.cell_count[c] : 0;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        int excl = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+        if (c < nc) {
+            s.cell_start[c] = excl;
+            s.cell_fill[c] = excl;
+            s.cell_count[c] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s.cell_start[nc] = carry;
+}
+
+__global__ void k_cells_scatter(DevSys s, Params p, int step_off, int force) {
+    if (!pending(s, force)) return;
+    int cur = (int)((*s.step_base + step_off) & 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        int cx, cy, cz;
+        cell_of(s, p, s.phi[cur][i], cx, cy, cz);
+        int pos = atomicAdd(&s.cell_fill[(cz * s.ncy + cy) * s.ncx + cx], 1);
+        s.cell_atoms[pos] = i;
+    }
+}
+
+__device__ __forceinline__ bool in_list_fp64(const DevSys& s, const Params& p, int cur, int i, int j) {
+    return exact_r2(s, p, cur, i, j) < p.rlist2_d;
+}
+
+// An FP32 minimum-image choice can differ from the FP64 one only when a
+// component sits near half a box edge.
+__device__ __forceinline__ bool image_ambiguous(const Params& p, float4 hi, float4 hj) {
+    if (!p.periodic) return false;
+    float fx = fabsf((hi.x - hj.x) * p.invL[0]), fy = fabsf((hi.y - hj.y) * p.invL[1]),
+          fz = fabsf((hi.z - hj.z) * p.invL[2]);
+    fx -= floorf(fx);
+    fy -= floorf(fy);
+    fz -= floorf(fz);
+    return fabsf(fx - 0.5f) < 1e-4f || fabsf(fy - 0.5f) < 1e-4f || fabsf(fz - 0.5f) < 1e-4f;
+}
+
+__global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_per_warp) {
+    if (!pending(s, force)) return;
+    extern __shared__ uint32_t smem_bm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int nwords = (s.n + 31) >> 5;
+    uint32_t* bm = smem_bm + (size_t)warp * words_per_warp;
+    const int cur = (int)((*s.step_base + step_off) & 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
+    for (int i = blockIdx.x * wpb + warp; i < s.n; i += gridDim.x * wpb) {
+        for (int w = lane; w < nwords; w += 32) bm[w] = 0u;
+        __syncwarp();
+        const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
+        const int mi = s.mol[i];
+        int cx, cy, cz;
+        cell_of(s, p, hi, cx, cy, cz);
+        for (int dz = -1; dz <= 1; ++dz) {
+            int zz = cz + dz;
+            if (p.periodic) zz = (zz + s.ncz) % s.ncz;
+            else if (zz < 0 || zz >= s.ncz) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = cy + dy;
+                if (p.periodic) yy = (yy + s.ncy) % s.ncy;
+                else if (yy < 0 || yy >= s.ncy) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = cx + dx;
+                    if (p.periodic) xx = (xx + s.ncx) % s.ncx;
+                    else if (xx < 0 || xx >= s.ncx) continue;
+                    const int c = (zz * s.ncy + yy) * s.ncx + xx;
+                    const int b = s.cell_start[c], e = s.cell_start[c + 1];
+                    for (int k = b + lane; k < e; k += 32) {
+                        const int j = s.cell_atoms[k];
+                        if (j == i || s.mol[j] == mi) continue;
+                        const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
+                        const float3 d = pair_disp(p, hi, lo, hj, lj);
+                        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+                        bool in;
+                        if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
+                        else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
+                        else in = in_list_fp64(s, p, cur, i, j);
+                        if (in) atomicOr(&bm[j >> 5], 1u << (j & 31));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // bitmap -> ascending row
+        int total = 0;
+        int* row = s.rows + (size_t)i * s.cap;
+        for (int w0 = 0; w0 < nwords; w0 += 32) {
+            const int w = w0 + lane;
+            uint32_t bits = w < nwords ? bm[w] : 0u;
+            const int c = __popc(bits);
+            int x = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            int pos = total + x - c;
+            while (bits) {
+                const int t = __ffs(bits) - 1;
+                if (pos < s.cap) row[pos] = (w << 5) + t;
+                ++pos;
+                bits &= bits - 1u;
+            }
+            total += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) {
+            s.nlong[i] = min(total, s.cap);
+            if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
+        }
+        __syncwarp();
+        // short rows: the members of the (ascending) row with r < r_off + skin
+        const int nl = min(total, s.cap);
+        int ns = 0;
+        int* srow = s.srows + (size_t)i * s.caps;
+        for (int k0 = 0; k0 < nl; k0 += 32) {
+            const int k = k0 + lane;
+            bool keep = false;
+            int j = 0;
+            if (k < nl) {
+                j = row[k];
+                const float3 d = pair_disp(p, hi, lo, s.phi[cur][j], s.plo[cur][j]);
+                keep = (d.x * d.x + d.y * d.y + d.z * d.z) < p.rshort2;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = ns + __popc(m & ((1u << lane) - 1u));
+                if (pos < s.caps) srow[pos] = j;
+            }
+            ns += __popc(m);
+        }
+        if (lane == 0) {
+            s.nshort[i] = min(ns, s.caps);
+            if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
+            s.refx[i] = s.qx[cur][i];
+            s.refy[i] = s.qy[cur][i];
+            s.refz[i] = s.qz[cur][i];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_rebuild_clear(DevSys s) { *s.rebuild = 0; }
+
+}  // namespace
+
+void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
+                    cudaStream_t st) {
+    const int f = force ? 1 : 0;
+    const int tb = 256;
+    const int gb = (s.n + tb - 1) / tb;
+    k_cells_count<<<gb, tb, 0, st>>>(s, p, step_off, f);
+    k_cells_scan<<<1, 1024, 0, st>>>(s, f);
+    k_cells_scatter<<<gb, tb, 0, st>>>(s, p, step_off, f);
+    const int words = (int)(bitmap_bytes / 4 / bitmap_warps);
+    const int blocks = (s.n + bitmap_warps - 1) / bitmap_warps;
+    k_rows<<<blocks, bitmap_warps * 32, bitmap_bytes, st>>>(s, p, step_off, f, words);
+    k_rebuild_clear<<<1, 1, 0, st>>>(s);
+}
+
+void nlist_set_smem_limit(size_t bytes) {
+    cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}

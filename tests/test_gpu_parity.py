@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA library against the FP64 oracle on the same seeded
+inputs (all calls go through the C ABI via the ctypes binding).
+
+Tolerances: per-atom gradients and post-jump velocities within 1e-5
+relative (||d_i|| / max(||ref_i||, 1e-3 rms)); candidate rows and Poisson
+counts bit-exact; thinning decisions identical except where the oracle's
+|U - lambda/lambda*| < 1e-6 (counted); energies within 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import philox
+from oracle.forcefield import Params
+from oracle.integrate import OracleMD, Topology, jump_half
+from oracle.neighbors import rows as oracle_rows
+from paper_2002_07109_gb300.water import water_box, water_droplet, water_droplet_molecules
+
+bounce = pytest.importorskip("paper_2002_07109_gb300.bounce")
+
+TOL = 1e-5
+
+
+def _topo(s):
+    return Topology(s.type, s.mass, s.charge, s.molecule, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0)
+
+
+def _rel_err(a, ref):
+    scale = np.maximum(np.linalg.norm(ref, axis=1), 1e-3 * math.sqrt((ref ** 2).sum(1).mean()))
+    return np.linalg.norm(a - ref, axis=1) / scale
+
+
+CASES = {
+    # name: (system builder, config)
+    "droplet_all_pairs": (lambda: water_droplet(4, seed=0), dict(r_on=4.0, r_off=5.0, r_cut=math.inf)),
+    "droplet_cutoff": (lambda: water_droplet_molecules(300, seed=2), dict(r_on=4.0, r_off=5.0, r_cut=9.0, skin=1.0)),
+    "box_ewald": (lambda: water_box(6, seed=3), dict(r_on=4.0, r_off=5.0, r_cut=8.0, skin=1.0, ewald_beta=0.35)),
+}
+
+
+def _setup(name, seed=11, perturb=0.0):
+    build, cfg = CASES[name]
+    s = build()
+    rng = np.random.default_rng(99)
+    q = s.q + (rng.normal(scale=perturb, size=s.q.shape) if perturb else 0.0)
+    ctx = bounce.from_system(s, seed=seed, **cfg)
+    ctx.set_state(q, s.v, step=7)
+    p = Params(r_on=cfg["r_on"], r_off=cfg["r_off"], r_cut=cfg["r_cut"], ewald_beta=cfg.get("ewald_beta", 0.0),
+               box=s.box, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps)
+    md = OracleMD(q, s.v, _topo(s), p, seed=seed, skin=cfg.get("skin", 1.0), step=7)
+    md.ensure_rows()
+    return s, ctx, md
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rows_bit_exact(name):
+    s, ctx, md = _setup(name, perturb=0.05)
+    got = ctx.rows()
+    assert len(got) == len(md.row_list)
+    for i, (a, b) in enumerate(zip(got, md.row_list)):
+        assert np.array_equal(a, b), i
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_bounds_match(name):
+    s, ctx, md = _setup(name)
+    L, Ls = ctx.bounds()
+    assert np.allclose(L, md.L, rtol=1e-9, atol=0)
+    assert np.allclose(Ls, md.Lstar, rtol=1e-9, atol=0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("part", ["full", "short", "long"])
+def test_gradients(name, part):
+    s, ctx, md = _setup(name, perturb=0.05)
+    code = {"full": bounce.GRAD_FULL, "short": bounce.GRAD_SHORT, "long": bounce.GRAD_LONG}[part]
+    g = ctx.gradient(code)
+    ref = {"full": md.grad_full, "short": md.grad_short, "long": md.grad_long}[part]()
+    err = _rel_err(g, ref)
+    assert err.max() < TOL, (part, err.max(), int(err.argmax()))
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_energies(name):
+    s, ctx, md = _setup(name, perturb=0.05)
+    e = ctx.energies()
+    ref = md.energies()
+    for k_gpu, k_ref in (("coulomb", "coul"), ("lj", "lj"), ("bond", "bond"), ("angle", "angle"), ("kinetic", "kin")):
+        scale = max(abs(ref[k_ref]), 1e-3 * abs(ref["kin"]))
+        assert abs(e[k_gpu] - ref[k_ref]) < 1e-6 * scale + 1e-9, (k_gpu, e[k_gpu], ref[k_ref])
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("stream_id", [1, 2])
+def test_jump_half(name, stream_id):
+    s, ctx, md = _setup(name, perturb=0.05)
+    step = 12345
+    M, A = ctx.jump_half(step, stream_id)
+    _, v = ctx.get_state()
+    v_ref, rec = jump_half(md.q, md.v, md.row_list, md.topo, md.p, md.Lstar, md.beta, md.dt, md.seed, step,
+                           stream_id, record=True)
+    # Poisson counts: bit-exact
+    assert np.array_equal(M, rec["M"])
+    assert M.sum() > 100
+    # decisions: identical except at atoms with a near tie in the oracle
+    tie = np.zeros(len(M), bool)
+    close = np.abs(rec["U"] - rec["ratio"]) < 1e-6
+    tie[rec["atom"][close]] = True
+    acc_ref = np.bincount(rec["atom"][rec["accepted"].astype(bool)], minlength=len(M))
+    assert np.array_equal(A[~tie], acc_ref[~tie])
+    assert A.sum() > 10
+    err = _rel_err(v, v_ref)
+    assert err[~tie].max() < TOL, err[~tie].max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("integrator", ["baoab", "bounce"])
+def test_one_step(name, integrator):
+    s, ctx, md = _setup(name)
+    q0 = md.q.copy()
+    code = bounce.BOUNCE if integrator == "bounce" else bounce.BAOAB
+    ctx.run(1, code)
+    if integrator == "bounce":
+        r1, r2 = md.step_bounce(record=True)
+        tie = np.zeros(s.n_atoms, bool)
+        for r in (r1, r2):
+            tie[r["atom"][np.abs(r["U"] - r["ratio"]) < 1e-6]] = True
+    else:
+        md.step_baoab()
+        tie = np.zeros(s.n_atoms, bool)
+    q, v = ctx.get_state()
+    dq = np.linalg.norm(q - md.q, axis=1) / np.maximum(np.linalg.norm(md.q - q0, axis=1), 1e-6)
+    assert dq[~tie].max() < TOL, dq[~tie].max()
+    assert _rel_err(v, md.v)[~tie].max() < TOL
+    ctx.close()
+
+
+def test_run_is_deterministic():
+    s, ctx, md = _setup("droplet_cutoff")
+    ctx.run(40, bounce.BOUNCE)
+    q1, v1 = ctx.get_state()
+    ctx.set_state(md.q, md.v, step=7)
+    ctx.run(40, bounce.BOUNCE)
+    q2, v2 = ctx.get_state()
+    assert np.array_equal(q1, q2) and np.array_equal(v1, v2)
+    ctx.close()
+
+
+def test_chunked_runs_equal_one_run():
+    """Graph-replayed chunks, direct launches and split runs give the same bits."""
+    s, ctx, md = _setup("droplet_cutoff")
+    ctx.run(70, bounce.BAOAB)
+    q1, v1 = ctx.get_state()
+    ctx.set_state(md.q, md.v, step=7)
+    for n in (1, 33, 36):
+        ctx.run(n, bounce.BAOAB)
+    q2, v2 = ctx.get_state()
+    assert np.array_equal(q1, q2) and np.array_equal(v1, v2)
+    ctx.close()
+
+
+def test_no_long_range_bounce_is_baoab():
+    s = water_droplet(3, seed=4)
+    cfg = dict(r_on=math.inf, r_off=math.inf, r_cut=math.inf)
+    outs = []
+    for integ in (bounce.BAOAB, bounce.BOUNCE):
+        ctx = bounce.from_system(s, seed=3, **cfg)
+        ctx.set_state(s.q, s.v)
+        ctx.run(10, integ)
+        outs.append(ctx.get_state())
+        e = ctx.energies()
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_multi_step_trajectory_tracks_oracle():
+    """20 BOUNCE steps: GPU and oracle stay together until a near tie flips a
+    decision (then they may separate); the counted proposals agree."""
+    s, ctx, md = _setup("droplet_all_pairs", seed=21)
+    for k in range(20):
+        ctx.run(1, bounce.BOUNCE)
+        r1, r2 = md.step_bounce(record=True)
+        ties = sum(int((np.abs(r["U"] - r["ratio"]) < 1e-6).sum()) for r in (r1, r2))
+        q, v = ctx.get_state()
+        if ties:
+            break
+        assert _rel_err(v, md.v).max() < 1e-4, k
+    e = ctx.energies()
+    assert e["proposals"] > 0
+    ctx.close()
+
+
+def test_full_size_droplet_sampled():
+    """4096-molecule droplet with a 12 A cutoff (the benchmark workload):
+    rows, gradients and a jump half-step on a sample of atoms."""
+    s = water_droplet(16, seed=0)
+    cfg = dict(r_on=4.0, r_off=5.0, r_cut=12.0, skin=1.0)
+    ctx = bounce.from_system(s, seed=1, **cfg)
+    ctx.set_state(s.q, s.v, step=3)
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(s.n_atoms, 150, replace=False))
+    p = Params(r_on=4.0, r_off=5.0, r_cut=12.0, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps)
+    ref_rows = oracle_rows(s.q, s.molecule, 13.0, None, atoms=sample)
+    got_rows = ctx.rows()
+    for a, i in enumerate(sample):
+        assert np.array_equal(got_rows[i], ref_rows[a])
+    from oracle.forcefield import pair_gradients, bonded_gradients
+    from oracle.neighbors import to_pairs
+    g = ctx.gradient(bounce.GRAD_FULL)
+    ii, jj = to_pairs(ref_rows, sample)
+    ref = pair_gradients(s.q, s.charge, s.type, ii, jj, p, "full") + bonded_gradients(
+        s.q, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0)
+    err = _rel_err(g[sample], ref[sample])
+    assert err.max() < TOL
+    ctx.close()
