@@ -161,6 +161,18 @@ int bounce_jump_half(bounce_ctx* ctx, int64_t step, int32_t stream_id, int32_t* 
  * counts[n] and rows[n * capacity] (ascending atom indices). */
 int bounce_get_rows(bounce_ctx* ctx, int32_t* counts, int32_t* rows, int32_t capacity);
 
+/* Profiling: advance n_steps exactly as bounce_run does, but with direct
+ * launches (no graph) and CUDA events around every launch of the fused step
+ * kernel; *kernel_ms receives the summed step-kernel time and *launches
+ * the number of step-kernel launches.  Synchronises `stream`. */
+int bounce_profile_steps(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, void* stream, double* kernel_ms,
+                         int64_t* launches);
+
+/* Number of kernel launches bounce_run issues for n_steps (for launch
+ * accounting: head and tail launches, gated row-rebuild launches, graph
+ * chunks and step-counter updates). */
+int64_t bounce_run_launch_count(int64_t n_steps);
+
 /* Message of the last error on ctx (never NULL). */
 const char* bounce_last_error(const bounce_ctx* ctx);
 

@@ -143,6 +143,24 @@ def pair_gradients(q, charge, typ, ii, jj, p, part="full"):
     return g
 
 
+def pair_gradient_magnitudes(q, charge, typ, ii, jj, p, part="full"):
+    """Per-atom sum over the directed pairs of the magnitude of each pair's
+    gradient term: the scale of the rounding error of any floating-point
+    evaluation of the sum (forward error bound of summation)."""
+    n = q.shape[0]
+    m = np.zeros(n)
+    if len(ii) == 0:
+        return m
+    d, r, qa, qb, sig, eps = pair_terms(q, charge, typ, ii, jj, p)
+    w = np.where(inside_cut(r2_of(d), p), pair_dW(r, qa, qb, sig, eps, _uncut(p)), 0.0)
+    if part == "short":
+        w = w * (1.0 - chi(r, p.r_on, p.r_off))
+    elif part == "long":
+        w = w * chi(r, p.r_on, p.r_off)
+    np.add.at(m, ii, np.abs(w))
+    return m
+
+
 def pair_gradient_one(qi, qj, qa, qb, sig, eps, p, part="long"):
     """Gradient of one pair with respect to q_i (vectorised over rows)."""
     d = displacement(qi, qj, p.box)
@@ -193,6 +211,35 @@ def bonded_gradients(q, bonds, bond_k_r0, angles, angle_k_t0, box=None):
     return g
 
 
+def bonded_gradient_magnitudes(q, bonds, bond_k_r0, angles, angle_k_t0, box=None):
+    """Per-atom sum of the magnitudes of the bonded gradient terms."""
+    m = np.zeros(q.shape[0])
+    if len(bonds):
+        a, b = bonds[:, 0], bonds[:, 1]
+        d = displacement(q[a], q[b], box)
+        r = np.sqrt((d * d).sum(1))
+        c = np.abs(2.0 * bond_k_r0[:, 0] * (r - bond_k_r0[:, 1]))
+        np.add.at(m, a, c)
+        np.add.at(m, b, c)
+    if len(angles):
+        a, b, c = angles[:, 0], angles[:, 1], angles[:, 2]
+        u = displacement(q[a], q[b], box)
+        w = displacement(q[c], q[b], box)
+        nu = np.sqrt((u * u).sum(1))
+        nw = np.sqrt((w * w).sum(1))
+        cos = np.clip((u * w).sum(1) / (nu * nw), -1.0, 1.0)
+        sin = np.sqrt(1.0 - cos * cos)
+        dE = 2.0 * angle_k_t0[:, 0] * (np.arccos(cos) - angle_k_t0[:, 1])
+        du = -(w / (nu * nw)[:, None] - (cos / (nu * nu))[:, None] * u) / sin[:, None]
+        dw = -(u / (nu * nw)[:, None] - (cos / (nw * nw))[:, None] * w) / sin[:, None]
+        ga = dE[:, None] * du
+        gc = dE[:, None] * dw
+        np.add.at(m, a, np.linalg.norm(ga, axis=1))
+        np.add.at(m, c, np.linalg.norm(gc, axis=1))
+        np.add.at(m, b, np.linalg.norm(ga + gc, axis=1))
+    return m
+
+
 def bonded_energies(q, bonds, bond_k_r0, angles, angle_k_t0, box=None):
     eb = 0.0
     ea = 0.0
@@ -224,6 +271,23 @@ def pair_energies(q, charge, typ, ii, jj, p):
     sr6 = np.where(eps != 0, (sig / r) ** 6, 0.0)
     lj = 4.0 * eps * (sr6 * sr6 - sr6)
     return float(np.where(inside, coul, 0.0).sum()), float(np.where(inside, lj, 0.0).sum())
+
+
+def pair_energy_magnitudes(q, charge, typ, ii, jj, p):
+    """(sum |Coulomb term|, sum |LJ term|) over the unordered pairs i < j."""
+    keep = ii < jj
+    ii, jj = ii[keep], jj[keep]
+    if len(ii) == 0:
+        return 0.0, 0.0
+    d, r, qa, qb, sig, eps = pair_terms(q, charge, typ, ii, jj, p)
+    inside = inside_cut(r2_of(d), p)
+    if p.ewald_beta > 0:
+        coul = K_COUL * qa * qb * erfc(p.ewald_beta * r) / r
+    else:
+        coul = K_COUL * qa * qb / r
+    sr6 = np.where(eps != 0, (sig / r) ** 6, 0.0)
+    lj = 4.0 * eps * (sr6 * sr6 - sr6)
+    return float(np.abs(np.where(inside, coul, 0.0)).sum()), float(np.abs(np.where(inside, lj, 0.0)).sum())
 
 
 def kinetic_energy(v, mass):

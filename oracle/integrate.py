@@ -30,8 +30,9 @@ import math
 import numpy as np
 
 from . import philox, poisson
-from .forcefield import (ACCEL, KB, Params, bonded_gradients, pair_gradients,
-                         pair_gradient_one, kinetic_energy, pair_energies, bonded_energies)
+from .forcefield import (ACCEL, KB, Params, bonded_gradients, pair_gradients, pair_gradient_magnitudes,
+                         bonded_gradient_magnitudes, pair_gradient_one, kinetic_energy, pair_energies,
+                         pair_energy_magnitudes, bonded_energies)
 from .neighbors import rows as build_rows, needs_rebuild, to_pairs
 
 
@@ -166,6 +167,21 @@ class OracleMD:
         ii, jj = self.pairs()
         t = self.topo
         return pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "long")
+
+    def grad_scale(self, part):
+        """Per-atom sum of the magnitudes of the terms of the gradient part
+        (the forward error scale of a floating-point evaluation)."""
+        ii, jj = self.pairs()
+        t = self.topo
+        m = pair_gradient_magnitudes(self.q, t.charge, t.type, ii, jj, self.p, part)
+        if part != "long":
+            m = m + bonded_gradient_magnitudes(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box)
+        return m
+
+    def energy_scale(self):
+        ii, jj = self.pairs()
+        t = self.topo
+        return pair_energy_magnitudes(self.q, t.charge, t.type, ii, jj, self.p)
 
     def kick(self, G, h):
         self.v = self.v - ((h * ACCEL) / self.topo.mass)[:, None] * G

@@ -60,6 +60,8 @@ _sig = {
     "bounce_compute_gradient": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
     "bounce_jump_half": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, C.c_int32, _P]),
     "bounce_get_rows": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "bounce_profile_steps": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "bounce_run_launch_count": (C.c_int64, [C.c_int64]),
     "bounce_last_error": (C.c_char_p, [_P]),
     "bounce_destroy": (None, [_P]),
 }
@@ -162,6 +164,14 @@ class Context:
     # ---- run / read
     def run(self, n_steps, integrator=BOUNCE, stream=None):
         self._check(bounce_run(self.h, int(n_steps), int(integrator), stream), "run")
+
+    def profile_steps(self, n_steps, integrator=BOUNCE, stream=None):
+        """(summed step-kernel ms, step-kernel launches) over n_steps."""
+        ms = C.c_double()
+        nl = C.c_int64()
+        self._check(bounce_profile_steps(self.h, int(n_steps), int(integrator), stream, C.byref(ms), C.byref(nl)),
+                    "profile_steps")
+        return ms.value, nl.value
 
     def get_state(self, q_out=None, v_out=None, stream=None):
         if q_out is not None and hasattr(q_out, "data_ptr"):

@@ -639,6 +639,52 @@ int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
     return check_err(c, st);
 }
 
+int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream, double* kernel_ms,
+                         int64_t* launches) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    if (n_steps < 1 || (integ != BOUNCE_BAOAB && integ != BOUNCE_BOUNCE) || !kernel_ms)
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad profile arguments");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev(2 * (size_t)(n_steps + 1));
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    auto timed = [&](int k, int variant, int off) {
+        cudaEventRecord(ev[2 * k], st);
+        launch_step(c->ds, c->pp, integ, variant, off, st);
+        cudaEventRecord(ev[2 * k + 1], st);
+    };
+    rebuild(c, 0, false, st);
+    timed(0, 0, 0);
+    launch_advance_step(c->ds, 1, st);
+    for (int64_t k = 0; k < n_steps - 1; ++k) {
+        rebuild(c, (int)k, false, st);
+        timed((int)k + 1, 1, (int)k);
+    }
+    if (n_steps > 1) launch_advance_step(c->ds, n_steps - 1, st);
+    rebuild(c, 0, false, st);
+    timed((int)n_steps, 2, 0);
+    CU(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (int64_t k = 0; k <= n_steps; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+        tot += ms;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    *kernel_ms = tot;
+    if (launches) *launches = n_steps + 1;
+    return check_err(c, st);
+}
+
+int64_t bounce_run_launch_count(int64_t n) {
+    if (n <= 0) return 0;
+    const int64_t per_step = 6;  // 5 gated row-rebuild kernels + the fused step kernel
+    const int64_t rem_all = n - 1;
+    const int64_t chunks = rem_all / CHUNK, rem = rem_all % CHUNK;
+    return per_step + 1 + chunks * (CHUNK * per_step + 1) + rem * per_step + (rem ? 1 : 0) + per_step;
+}
+
 int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     if (!c || !out) return BOUNCE_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");

@@ -190,9 +190,15 @@ __device__ __forceinline__ float3 pair_disp(const Params& p, float4 hi, float4 l
     return make_float3(dx + ex, dy + ey, dz + ez);
 }
 
+// 1/sqrt(r2) to about 1 ulp: the hardware estimate refined by one Newton step.
+__device__ __forceinline__ float rsqrt_nr(float r2) {
+    const float y = rsqrtf(r2);
+    return y * fmaf(-0.5f * r2 * y, y, 1.5f);
+}
+
 // W'(r) / r of one pair (Coulomb or Ewald direct + LJ), r2 < rc2 assumed.
 __device__ __forceinline__ float pair_dW_over_r(const Params& p, float r2, float qq, int tp) {
-    float ir = rsqrtf(r2);
+    float ir = rsqrt_nr(r2);
     float ir2 = ir * ir;
     float w;
     if (p.ebeta > 0.f) {
@@ -219,7 +225,7 @@ __device__ __forceinline__ float chi_of(const Params& p, float r) {
 
 // Pair energy W(r) components (Coulomb or erfc, LJ), r2 < rc2 assumed.
 __device__ __forceinline__ void pair_W(const Params& p, float r2, float qq, int tp, float& ec, float& el) {
-    float ir = rsqrtf(r2);
+    float ir = rsqrt_nr(r2);
     if (p.ebeta > 0.f) {
         float r = r2 * ir;
         ec = qq * erfcf(p.ebeta * r) * ir;
@@ -289,7 +295,7 @@ __device__ __forceinline__ float3 bonded_grad(const Params& p, const DevSys& s, 
         float3 u = pair_disp(p, s.phi[cur][a], s.plo[cur][a], hb, lb);
         float3 w = pair_disp(p, s.phi[cur][c], s.plo[cur][c], hb, lb);
         float nu2 = u.x * u.x + u.y * u.y + u.z * u.z, nw2 = w.x * w.x + w.y * w.y + w.z * w.z;
-        float inuw = rsqrtf(nu2 * nw2);
+        float inuw = rsqrt_nr(nu2 * nw2);
         float cs = (u.x * w.x + u.y * w.y + u.z * w.z) * inuw;
         cs = fminf(fmaxf(cs, -1.f), 1.f);
         float th = acosf(cs);

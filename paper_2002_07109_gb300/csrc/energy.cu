@@ -51,7 +51,7 @@ __global__ void k_atom_energies(DevSys s, Params p, int cur, double* terms) {
             const float3 u = pair_disp(p, ha, la, hi, lo);
             const float3 w = pair_disp(p, hc, lc, hi, lo);
             float cs = (u.x * w.x + u.y * w.y + u.z * w.z) *
-                       rsqrtf((u.x * u.x + u.y * u.y + u.z * u.z) * (w.x * w.x + w.y * w.y + w.z * w.z));
+                       rsqrt_nr((u.x * u.x + u.y * u.y + u.z * u.z) * (w.x * w.x + w.y * w.y + w.z * w.z));
             cs = fminf(fmaxf(cs, -1.f), 1.f);
             const float th = acosf(cs) - kp.y;
             ea += (double)(kp.x * th * th);
