@@ -161,6 +161,23 @@ int bounce_jump_half(bounce_ctx* ctx, int64_t step, int32_t stream_id, int32_t* 
  * counts[n] and rows[n * capacity] (ascending atom indices). */
 int bounce_get_rows(bounce_ctx* ctx, int32_t* counts, int32_t* rows, int32_t capacity);
 
+/* Observables (paper Sec. VI). */
+
+/* Counts of unordered pairs (different molecules) of the type pair
+ * {type_a, type_b} by distance, n_bins bins of width r_max / n_bins over
+ * [0, r_max) (bin k: (k w)^2 <= r^2 < ((k+1) w)^2 in FP64); hist[n_bins]
+ * (host) receives the counts.  Needs r_max <= r_c when a cutoff is set.
+ * Synchronises `stream`. */
+int bounce_pair_histogram(bounce_ctx* ctx, int32_t type_a, int32_t type_b, double r_max, int32_t n_bins,
+                          int64_t* hist, void* stream);
+
+/* Take the current (unwrapped) positions as the reference of bounce_msd. */
+int bounce_set_msd_reference(bounce_ctx* ctx, void* stream);
+
+/* Mean over atoms of `type` of |q_i - q_i(ref)|^2 (A^2), FP64, into *out.
+ * Synchronises `stream`. */
+int bounce_msd(bounce_ctx* ctx, int32_t type, double* out, void* stream);
+
 /* Profiling: advance n_steps exactly as bounce_run does, but with direct
  * launches (no graph) and CUDA events around every launch of the fused step
  * kernel; *kernel_ms receives the summed step-kernel time and *launches

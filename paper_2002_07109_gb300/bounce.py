@@ -60,6 +60,9 @@ _sig = {
     "bounce_compute_gradient": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
     "bounce_jump_half": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, C.c_int32, _P]),
     "bounce_get_rows": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "bounce_pair_histogram": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_double, C.c_int32, _P, _P]),
+    "bounce_set_msd_reference": (C.c_int, [_P, _P]),
+    "bounce_msd": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), _P]),
     "bounce_profile_steps": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "bounce_run_launch_count": (C.c_int64, [C.c_int64]),
     "bounce_last_error": (C.c_char_p, [_P]),
@@ -164,6 +167,20 @@ class Context:
     # ---- run / read
     def run(self, n_steps, integrator=BOUNCE, stream=None):
         self._check(bounce_run(self.h, int(n_steps), int(integrator), stream), "run")
+
+    def pair_histogram(self, type_a, type_b, r_max, n_bins, stream=None):
+        h = np.zeros(int(n_bins), np.int64)
+        self._check(bounce_pair_histogram(self.h, int(type_a), int(type_b), float(r_max), int(n_bins), _ptr(h),
+                                          stream), "pair_histogram")
+        return h
+
+    def set_msd_reference(self, stream=None):
+        self._check(bounce_set_msd_reference(self.h, stream), "set_msd_reference")
+
+    def msd(self, type, stream=None):
+        out = C.c_double()
+        self._check(bounce_msd(self.h, int(type), C.byref(out), stream), "msd")
+        return out.value
 
     def profile_steps(self, n_steps, integrator=BOUNCE, stream=None):
         """(summed step-kernel ms, step-kernel launches) over n_steps."""

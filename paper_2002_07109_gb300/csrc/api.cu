@@ -13,6 +13,10 @@
 #include "common.cuh"
 
 void nlist_set_smem_limit(size_t bytes);
+void launch_pair_hist(const DevSys& s, const Params& p, int cur, int ta, int tb, double r_max, int n_bins,
+                      unsigned long long* hist, cudaStream_t st);
+void launch_msd(const DevSys& s, const double* rx, const double* ry, const double* rz, int cur, int t,
+                double* terms, cudaStream_t st);
 
 namespace {
 
@@ -40,11 +44,15 @@ struct bounce_ctx {
     double L[BOUNCE_MAXT * BOUNCE_MAXT] = {0};
     double Lstar[BOUNCE_MAXT] = {0};
     long long step0 = 0;
+    bool have_msd_ref = false;
     // device
     std::vector<Buf> bufs;
     DevSys ds{};
     Params pp{};
     double* terms = nullptr;     // energy scratch [6 n]
+    double* msd_ref = nullptr;   // [3 n] reference positions of bounce_msd
+    unsigned long long* hist = nullptr;
+    int hist_alloc = 0;
     long long* d_step = nullptr;
     int* h_err = nullptr;        // pinned
     unsigned long long* h_cnt = nullptr;
@@ -96,6 +104,10 @@ void free_all(bounce_ctx* c) {
     c->ds = DevSys{};
     c->terms = nullptr;
     c->d_step = nullptr;
+    c->msd_ref = nullptr;
+    c->hist = nullptr;
+    c->hist_alloc = 0;
+    c->have_msd_ref = false;
 }
 
 // ---------------------------------------------------------------- bounds
@@ -548,9 +560,15 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
         CU(cudaStreamSynchronize(st));
     }
     if (!finite_all(hq) || !finite_all(hv)) return fail(c, BOUNCE_ERR_NONFINITE, "non-finite position or velocity");
+    const DevSys before = c->ds;
     int r = setup_grid(c, hq);
     if (r) return r;
-    drop_graphs(c);
+    // captured graphs hold the system view by value: recapture only if the grid changed
+    const DevSys& g = c->ds;
+    if (g.ncx != before.ncx || g.ncy != before.ncy || g.ncz != before.ncz || g.ox != before.ox || g.oy != before.oy ||
+        g.oz != before.oz || g.ihx != before.ihx || g.ihy != before.ihy || g.ihz != before.ihz ||
+        g.cell_count != before.cell_count || g.cell_start != before.cell_start || g.cell_fill != before.cell_fill)
+        drop_graphs(c);
     const int cur = (int)(step & 1);
     std::vector<double> cx(n), cy(n), cz(n), vx(n), vy(n), vz(n);
     for (int i = 0; i < n; ++i) {
@@ -715,6 +733,70 @@ int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     out->rebuilds = (int64_t)c->h_cnt[CNT_REBUILDS];
     out->short_pairs = (int64_t)c->h_cnt[CNT_SHORT_PAIRS];
     out->full_pairs = (int64_t)c->h_cnt[CNT_FULL_PAIRS];
+    return BOUNCE_OK;
+}
+
+int bounce_pair_histogram(bounce_ctx* c, int32_t ta, int32_t tb, double r_max, int32_t n_bins, int64_t* hist,
+                          void* stream) {
+    if (!c || !hist || n_bins < 1 || !(r_max > 0) || ta < 0 || tb < 0 || ta >= BOUNCE_MAXT || tb >= BOUNCE_MAXT)
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad histogram arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    const bool cut = std::isfinite(c->cfg.r_cut) && c->cfg.r_cut > 0;
+    if (cut && r_max > c->cfg.r_cut) return fail(c, BOUNCE_ERR_INVALID_ARG, "r_max exceeds the cutoff");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_bins > c->hist_alloc) {
+        int r = dalloc(c, &c->hist, n_bins);
+        if (r) return r;
+        c->hist_alloc = n_bins;
+    }
+    long long step;
+    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    rebuild(c, 0, false, st);
+    CU(cudaMemsetAsync(c->hist, 0, n_bins * sizeof(unsigned long long), st));
+    launch_pair_hist(c->ds, c->pp, (int)(step & 1), ta, tb, r_max, n_bins, c->hist, st);
+    CU(cudaMemcpyAsync(hist, c->hist, n_bins * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return check_err(c, st);
+}
+
+int bounce_set_msd_reference(bounce_ctx* c, void* stream) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->msd_ref) {
+        int r = dalloc(c, &c->msd_ref, 3 * (size_t)c->n);
+        if (r) return r;
+    }
+    long long step;
+    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const int cur = (int)(step & 1);
+    const size_t b = c->n * sizeof(double);
+    CU(cudaMemcpyAsync(c->msd_ref, c->ds.qx[cur], b, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(c->msd_ref + c->n, c->ds.qy[cur], b, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(c->msd_ref + 2 * (size_t)c->n, c->ds.qz[cur], b, cudaMemcpyDeviceToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    c->have_msd_ref = true;
+    return BOUNCE_OK;
+}
+
+int bounce_msd(bounce_ctx* c, int32_t type, double* out, void* stream) {
+    if (!c || !out || type < 0 || type >= BOUNCE_MAXT) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad msd arguments");
+    if (!c->have_msd_ref) return fail(c, BOUNCE_ERR_STATE, "no msd reference");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    long long step;
+    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    launch_msd(c->ds, c->msd_ref, c->msd_ref + c->n, c->msd_ref + 2 * (size_t)c->n, (int)(step & 1), type, c->terms,
+               st);
+    double tot[2];
+    CU(cudaMemcpyAsync(tot, c->terms + 2 * (size_t)c->n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    *out = tot[1] > 0 ? tot[0] / tot[1] : 0.0;
     return BOUNCE_OK;
 }
 

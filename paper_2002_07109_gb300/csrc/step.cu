@@ -71,6 +71,17 @@ __device__ __forceinline__ void jump_prep(const DevSys& s, const Params& p, Jump
     js.nch[a] = nch;
 }
 
+// Exact FP64 decision U ||v|| L* < v . F for the inputs of one proposal (the
+// FP32 screen could not decide it).  Kept out of line so the compiler does
+// not hoist its FP64 work into the common path.
+__device__ __noinline__ int exact_decision(float vx, float vy, float vz, float gx, float gy, float gz, uint32_t x1,
+                                           uint32_t x2, double sp, double Ls) {
+    const double ad = __dadd_rn(__dadd_rn(__dmul_rn((double)vx, (double)gx), __dmul_rn((double)vy, (double)gy)),
+                                __dmul_rn((double)vz, (double)gz));
+    const double td = __dmul_rn(__dmul_rn(u53(x1, x2), sp), Ls);
+    return td < ad ? 1 : 0;
+}
+
 // Warp-cooperative jump chain of atom `a` (one half step).
 __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int cur, int a, int i, long long step,
                            uint32_t stream) {
@@ -125,12 +136,7 @@ __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int c
                 int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
                 const bool live = act && lane >= start;
                 if (__any_sync(0xffffffffu, live && dec == 2)) {
-                    if (live && dec == 2) {
-                        const double ad = __dadd_rn(__dadd_rn(__dmul_rn((double)vx, (double)gx), __dmul_rn((double)vy, (double)gy)),
-                                                    __dmul_rn((double)vz, (double)gz));
-                        const double td = __dmul_rn(__dmul_rn(u53(x1, x2), sp), Ls);
-                        dec = td < ad ? 1 : 0;
-                    }
+                    if (live && dec == 2) dec = exact_decision(vx, vy, vz, gx, gy, gz, x1, x2, sp, Ls);
                 }
                 const uint32_t acc = __ballot_sync(0xffffffffu, live && dec == 1);
                 const int f = acc ? __ffs(acc) - 1 : 32;
