@@ -57,6 +57,7 @@ extern "C" {
 #define BOUNCE_GRAD_LONG 2  /* sum_j F_ij = chi W' of every pair (Sec. IV.A) */
 
 #define BOUNCE_MAX_TYPES 4
+#define BOUNCE_NOALLOC_MAX_ATOMS 16384
 
 typedef struct bounce_ctx bounce_ctx;
 
@@ -189,6 +190,28 @@ int bounce_profile_steps(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, v
  * accounting: head and tail launches, gated row-rebuild launches, graph
  * chunks and step-counter updates). */
 int64_t bounce_run_launch_count(int64_t n_steps);
+
+/* Allocation-free pair energies.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code running
+ * while another framework captures a CUDA graph (cudaMalloc is illegal during
+ * capture), code that must live inside a caching allocator that owns the
+ * device pool, and hosts that forbid allocation after start-up.
+ * It returns out[0] = sum_{i<j} k q_i q_j / r (or erfc(beta r)/r with
+ * ewald_beta > 0) and out[1] = sum_{i<j} 4 eps ((sigma/r)^12 - (sigma/r)^6)
+ * over all pairs of different molecules with r < r_cut (r_cut <= 0 or inf:
+ * no cutoff; box = NULL: open boundaries, else 3 host doubles for a periodic
+ * box), the same totals as bounce_get_energies' coulomb and lj.
+ * Inputs are caller-owned DEVICE arrays: q[n,3], charge[n], type[n],
+ * molecule[n]; sigma and eps are host T*T tables; out is a DEVICE array of 2
+ * doubles written on `stream`.  The call allocates nothing: its scratch is a
+ * static device array of BOUNCE_NOALLOC_MAX_ATOMS atoms (786,432 bytes) that
+ * every GPU loading this library holds until exit.  n > BOUNCE_NOALLOC_MAX_ATOMS
+ * returns BOUNCE_ERR_INVALID_ARG.  The first call on a device looks up the
+ * scratch address on that device (make it before any stream capture).
+ * Calls share the scratch: calls whose GPU work overlaps race. */
+int bounce_pair_energy_noalloc(int32_t n, const double* q, const double* charge, const int32_t* type,
+                               const int32_t* molecule, int32_t n_types, const double* sigma, const double* eps,
+                               double r_cut, double ewald_beta, const double* box, double* out, void* stream);
 
 /* Message of the last error on ctx (never NULL). */
 const char* bounce_last_error(const bounce_ctx* ctx);

@@ -65,6 +65,8 @@ _sig = {
     "bounce_msd": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), _P]),
     "bounce_profile_steps": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "bounce_run_launch_count": (C.c_int64, [C.c_int64]),
+    "bounce_pair_energy_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, C.c_double, C.c_double,
+                                             _P, _P, _P]),
     "bounce_last_error": (C.c_char_p, [_P]),
     "bounce_destroy": (None, [_P]),
 }
@@ -233,6 +235,24 @@ class Context:
         rows = np.zeros((self.n, cap), np.int32)
         self._check(bounce_get_rows(self.h, _ptr(cnt), _ptr(rows), cap), "get_rows")
         return [rows[i, :min(cnt[i], cap)].astype(np.int64) for i in range(self.n)]
+
+
+NOALLOC_MAX_ATOMS = 16384
+
+
+def pair_energy_noalloc(q, charge, type, molecule, sigma, eps, r_cut=math.inf, ewald_beta=0.0, box=None, out=None,
+                        stream=None):
+    """Coulomb and LJ pair-energy totals of a device-resident state without any
+    device allocation by the library (for callers that cannot allocate, e.g.
+    inside another framework's graph capture).  q, charge, type, molecule and
+    out are CUDA tensors owned by the caller; returns the library's status
+    code (0 = ok)."""
+    s = _host(sigma, np.float64)
+    e = _host(eps, np.float64)
+    bx = None if box is None else _host(box, np.float64)
+    return bounce_pair_energy_noalloc(int(q.shape[0]), _ptr(q), _ptr(charge), _ptr(type), _ptr(molecule),
+                                      int(s.shape[0]), _ptr(s), _ptr(e), float(r_cut), float(ewald_beta),
+                                      None if bx is None else _ptr(bx), _ptr(out), stream)
 
 
 def from_system(sys, **kw):
