@@ -9,11 +9,11 @@ Protocol (our arm):
   * the droplet is pre-equilibrated on the GPU with BAOAB (friction 0.05/fs,
     1,500 steps) from the seeded lattice, so every timed window starts from
     a 300 K liquid droplet;
-  * W warm-up steps, then the K timed steps run in windows of at most 25
+  * W warm-up steps, then the K timed steps run in windows of at most 5
     steps, each window restarting from the equilibrated state (the state is
-    restored outside the timed region): BOUNCE with bare-Coulomb jumps at
-    1 fs heats flexible water over longer windows (see the design notes), so
-    each window measures steps from an equilibrated 300 K state;
+    restored outside the timed region): BOUNCE with this split (bare-Coulomb
+    jumps beyond 4-5 A) heats flexible water by ~15 % per 1 fs step (see the
+    design notes), so each window measures steps of a droplet near 300 K;
   * L2 is flushed (a 256 MB write) before each timed window;
   * device time by CUDA events on the launch stream; nvidia-smi clocks are
     sampled during the timed windows;
@@ -40,7 +40,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WINDOW = 25
+WINDOW = 5
 N_SIDE = 16                  # 16^3 = 4096 molecules
 R_CUT, R_ON, R_OFF, SKIN = 12.0, 4.0, 5.0, 1.0
 DT = 1.0

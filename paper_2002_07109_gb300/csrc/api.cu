@@ -255,18 +255,23 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     p.key1 = (uint32_t)(g.seed >> 32);
 }
 
-// Cell grid for the current host positions (edge > r_list).
+// Cell grid for the current host positions: cells of edge >= r_list / 3
+// (the row builder scans, for each (y, z) cell row within reach, only the
+// x-span of cells the r_list sphere can touch).
 int setup_grid(bounce_ctx* c, const std::vector<double>& q) {
     DevSys& s = c->ds;
     const double rl = r_list(c->cfg);
-    const double edge_min = std::isfinite(rl) ? rl * (1.0 + 1e-5) + 1e-3 : INFINITY;
-    int nc[3] = {1, 1, 1};
-    float org[3] = {0.f, 0.f, 0.f}, ih[3] = {0.f, 0.f, 0.f};
+    const double reach = std::isfinite(rl) ? rl * (1.0 + 1e-5) + 1e-3 : INFINITY;
+    const double edge_min = reach / 3.0;
+    int nc[3] = {1, 1, 1}, m[3] = {0, 0, 0};
+    float org[3] = {0.f, 0.f, 0.f}, ih[3] = {0.f, 0.f, 0.f}, hh[3] = {1.f, 1.f, 1.f};
     for (int d = 0; d < 3; ++d) {
+        double h = 1.0;
         if (c->cfg.periodic) {
             const double Lb = c->cfg.box[d];
             nc[d] = std::isfinite(edge_min) ? std::max(1, (int)std::floor(Lb / edge_min)) : 1;
-            nc[d] = std::min(nc[d], 256);
+            nc[d] = std::min(nc[d], 512);
+            h = Lb / nc[d];
             ih[d] = (float)(nc[d] / Lb);
         } else {
             double lo = 1e300, hi = -1e300;
@@ -278,12 +283,14 @@ int setup_grid(bounce_ctx* c, const std::vector<double>& q) {
             hi += 5.0;
             const double ext = hi - lo;
             if (std::isfinite(edge_min)) {
-                const double h = std::max(edge_min, ext / 128.0);
+                h = std::max(edge_min, ext / 256.0);
                 nc[d] = std::max(1, (int)std::floor(ext / h));
                 ih[d] = (float)(1.0 / h);
             }
             org[d] = (float)lo;
         }
+        hh[d] = (float)h;
+        m[d] = std::isfinite(reach) ? (int)std::ceil(reach / h) : 0;
     }
     const int ncell = nc[0] * nc[1] * nc[2];
     if (ncell > c->ncell_alloc) {
@@ -302,6 +309,13 @@ int setup_grid(bounce_ctx* c, const std::vector<double>& q) {
     s.ihx = ih[0];
     s.ihy = ih[1];
     s.ihz = ih[2];
+    s.hx = hh[0];
+    s.hy = hh[1];
+    s.hz = hh[2];
+    s.mx = m[0];
+    s.my = m[1];
+    s.mz = m[2];
+    c->pp.rcull = std::isfinite(reach) ? (float)(reach + 1e-3) : INFINITY;
     return BOUNCE_OK;
 }
 
@@ -474,7 +488,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
         (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, (size_t)n * s.caps)) ||
         (r = dalloc(c, &s.refx, n)) || (r = dalloc(c, &s.refy, n)) || (r = dalloc(c, &s.refz, n)) ||
         (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
-        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n)))
+        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 1024)))
         return r;
     s.kick = kick;
     s.osd = osd;
@@ -567,6 +581,7 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
     const DevSys& g = c->ds;
     if (g.ncx != before.ncx || g.ncy != before.ncy || g.ncz != before.ncz || g.ox != before.ox || g.oy != before.oy ||
         g.oz != before.oz || g.ihx != before.ihx || g.ihy != before.ihy || g.ihz != before.ihz ||
+        g.mx != before.mx || g.my != before.my || g.mz != before.mz ||
         g.cell_count != before.cell_count || g.cell_start != before.cell_start || g.cell_fill != before.cell_fill)
         drop_graphs(c);
     const int cur = (int)(step & 1);

@@ -61,6 +61,8 @@ struct DevSys {
     int ncx, ncy, ncz;
     float ox, oy, oz;        // grid origin (droplets)
     float ihx, ihy, ihz;     // inverse cell edges
+    float hx, hy, hz;        // cell edges
+    int mx, my, mz;          // search reach in cells (ceil(r_list / edge))
     // flags and counters
     int* rebuild;            // 1 = rows must be rebuilt before the next evaluation
     int* err;
@@ -85,6 +87,7 @@ struct Params {
     float rlist2_lo, rlist2_hi;  // FP32 screening band around r_list^2
     double rlist2_d;             // exact FP64 threshold r_list^2 (+inf = all)
     float rshort2;               // short-row threshold
+    float rcull;                 // r_list with a safety margin for cell culling (+inf = all)
     float Lstar_f[BOUNCE_MAXT];
     double Lstar_d[BOUNCE_MAXT];
     double beta;

@@ -72,21 +72,41 @@ __global__ void k_atom_energies(DevSys s, Params p, int cur, double* terms) {
     }
 }
 
-// Fixed-order sum of the 5 per-atom term arrays into out[5] by one CTA.
-__global__ void k_sum_terms(int n, const double* terms, double* out) {
-    __shared__ double part[5][256];
-    for (int t = 0; t < 5; ++t) {
+// Fixed-order sum of T per-atom term arrays: each of the first-pass CTAs
+// sums a fixed slice of every array, then one CTA adds the per-CTA partials
+// in CTA order, so totals do not depend on scheduling.
+constexpr int SUM_CTAS = 128;
+
+template <int T>
+__global__ void k_sum_pass1(int n, const double* terms, double* partial) {
+    __shared__ double part[T][256];
+    const int per = (n + SUM_CTAS - 1) / SUM_CTAS;
+    const int b = blockIdx.x * per, e = min(n, b + per);
+    for (int t = 0; t < T; ++t) {
         double acc = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) acc += terms[(size_t)t * n + i];
+        for (int i = b + threadIdx.x; i < e; i += blockDim.x) acc += terms[(size_t)t * n + i];
         part[t][threadIdx.x] = acc;
     }
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w)
-            for (int t = 0; t < 5; ++t) part[t][threadIdx.x] += part[t][threadIdx.x + w];
+            for (int t = 0; t < T; ++t) part[t][threadIdx.x] += part[t][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x < 5) out[threadIdx.x] = part[threadIdx.x][0];
+    if (threadIdx.x < T) partial[threadIdx.x * SUM_CTAS + blockIdx.x] = part[threadIdx.x][0];
+}
+
+template <int T>
+__global__ void k_sum_pass2(const double* partial, double* out) {
+    __shared__ double part[T][SUM_CTAS];
+    for (int t = 0; t < T; ++t) part[t][threadIdx.x] = partial[t * SUM_CTAS + threadIdx.x];
+    __syncthreads();
+    for (int w = SUM_CTAS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int t = 0; t < T; ++t) part[t][threadIdx.x] += part[t][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < T) out[threadIdx.x] = part[threadIdx.x][0];
 }
 
 // Split FP32 copies (hi + lo) of the FP64 positions of buffer `cur`;
@@ -113,7 +133,11 @@ __global__ void k_pack(DevSys s, Params p, int cur) {
 void launch_energies(const DevSys& s, const Params& p, int cur, double* terms, cudaStream_t st) {
     const int wpb = 8;
     k_atom_energies<<<(s.n + wpb - 1) / wpb, wpb * 32, 0, st>>>(s, p, cur, terms);
-    k_sum_terms<<<1, 256, 0, st>>>(s.n, terms, terms + 5 * (size_t)s.n);
+    // terms holds 6 n doubles: 5 n per-atom terms, then 5 * SUM_CTAS partials (n >= 640) or
+    // fewer atoms: the partials go after the totals slot in any case
+    double* partial = terms + 5 * (size_t)s.n + 8;
+    k_sum_pass1<5><<<SUM_CTAS, 256, 0, st>>>(s.n, terms, partial);
+    k_sum_pass2<5><<<1, SUM_CTAS, 0, st>>>(partial, terms + 5 * (size_t)s.n);
 }
 
 void launch_pack_positions(const DevSys& s, const Params& p, int cur, cudaStream_t st) {

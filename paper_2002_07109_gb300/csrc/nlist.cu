@@ -123,28 +123,81 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
         __syncwarp();
         const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
         const int mi = s.mol[i];
+        // unclamped cell coordinates of atom i
+        const float fx = p.periodic ? hi.x * s.ihx : (hi.x - s.ox) * s.ihx;
+        const float fy = p.periodic ? hi.y * s.ihy : (hi.y - s.oy) * s.ihy;
+        const float fz = p.periodic ? hi.z * s.ihz : (hi.z - s.oz) * s.ihz;
         int cx, cy, cz;
         cell_of(s, p, hi, cx, cy, cz);
-        for (int dz = -1; dz <= 1; ++dz) {
-            int zz = cz + dz;
-            if (p.periodic) zz = (zz + s.ncz) % s.ncz;
-            else if (zz < 0 || zz >= s.ncz) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                int yy = cy + dy;
-                if (p.periodic) yy = (yy + s.ncy) % s.ncy;
-                else if (yy < 0 || yy >= s.ncy) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int xx = cx + dx;
-                    if (p.periodic) xx = (xx + s.ncx) % s.ncx;
-                    else if (xx < 0 || xx >= s.ncx) continue;
-                    const int c = (zz * s.ncy + yy) * s.ncx + xx;
-                    const int b = s.cell_start[c], e = s.cell_start[c + 1];
+        // geometric culling is valid unless atom i sits outside a droplet grid
+        const bool cull = p.periodic || (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)s.ncx &&
+                                         fy < (float)s.ncy && fz < (float)s.ncz);
+        const float rc2 = p.rcull * p.rcull;
+        // axes narrower than the stencil are scanned once, without culling or wrap
+        const bool fullz = s.ncz <= 2 * s.mz + 1, fully = s.ncy <= 2 * s.my + 1, fullx = s.ncx <= 2 * s.mx + 1;
+        const int z0 = fullz ? 0 : cz - s.mz, z1 = fullz ? s.ncz - 1 : cz + s.mz;
+        const int y0 = fully ? 0 : cy - s.my, y1 = fully ? s.ncy - 1 : cy + s.my;
+        for (int zu = z0; zu <= z1; ++zu) {
+            int zz = zu;
+            if (!fullz) {
+                if (p.periodic) zz = (zu % s.ncz + s.ncz) % s.ncz;
+                else if (zu < 0 || zu >= s.ncz) continue;
+            }
+            float gz = 0.f;
+            if (cull && !fullz) gz = fmaxf(fmaxf((float)zu - fz, fz - (float)(zu + 1)), 0.f) * s.hz;
+            if (gz * gz > rc2) continue;
+            for (int yu = y0; yu <= y1; ++yu) {
+                int yy = yu;
+                if (!fully) {
+                    if (p.periodic) yy = (yu % s.ncy + s.ncy) % s.ncy;
+                    else if (yu < 0 || yu >= s.ncy) continue;
+                }
+                float gy = 0.f;
+                if (cull && !fully) gy = fmaxf(fmaxf((float)yu - fy, fy - (float)(yu + 1)), 0.f) * s.hy;
+                const float g2 = gz * gz + gy * gy;
+                if (g2 > rc2) continue;
+                // x-span of cells the sphere can reach in this row
+                int xa, xb;
+                if (fullx) {
+                    xa = 0;
+                    xb = s.ncx - 1;
+                } else if (cull) {
+                    const float hw = sqrtf(rc2 - g2) * s.ihx;
+                    xa = max((int)floorf(fx - hw), cx - s.mx);
+                    xb = min((int)floorf(fx + hw), cx + s.mx);
+                } else {
+                    xa = cx - s.mx;
+                    xb = cx + s.mx;
+                }
+                // up to two contiguous ranges of cells (periodic wrap), each a
+                // contiguous range of atoms in the cell-sorted array
+                int ra[2], rb[2], nr = 0;
+                if (fullx) {
+                    ra[0] = xa; rb[0] = xb; nr = 1;
+                } else if (p.periodic) {
+                    if (xa < 0) { ra[nr] = xa + s.ncx; rb[nr] = s.ncx - 1; ++nr; xa = 0; }
+                    if (xb >= s.ncx) { ra[nr] = 0; rb[nr] = xb - s.ncx; ++nr; xb = s.ncx - 1; }
+                    if (xa <= xb) { ra[nr] = xa; rb[nr] = xb; ++nr; }
+                } else {
+                    xa = max(xa, 0);
+                    xb = min(xb, s.ncx - 1);
+                    if (xa <= xb) { ra[0] = xa; rb[0] = xb; nr = 1; }
+                }
+                const int rowc = (zz * s.ncy + yy) * s.ncx;
+                for (int t = 0; t < nr; ++t) {
+                    const int b = s.cell_start[rowc + ra[t]], e = s.cell_start[rowc + rb[t] + 1];
                     for (int k = b + lane; k < e; k += 32) {
                         const int j = s.cell_atoms[k];
                         if (j == i || s.mol[j] == mi) continue;
-                        const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
-                        const float3 d = pair_disp(p, hi, lo, hj, lj);
-                        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+                        // screen with the high FP32 parts; the band covers their error
+                        const float4 hj = s.phi[cur][j];
+                        float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
+                        if (p.periodic) {
+                            dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
+                            dy -= rintf(dy * p.invL[1]) * p.Lhi[1];
+                            dz -= rintf(dz * p.invL[2]) * p.Lhi[2];
+                        }
+                        const float r2 = dx * dx + dy * dy + dz * dz;
                         bool in;
                         if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
                         else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;

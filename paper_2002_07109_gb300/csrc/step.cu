@@ -214,7 +214,7 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
 
 // variant: 0 head (B/2 [J1] A O A), 1 body ([J2] B [J1] A O A), 2 tail ([J2] B/2)
 template <int BOUNCE>
-__global__ void __launch_bounds__(NW * 32) k_step(DevSys s, Params p, int variant, int step_off) {
+__global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int variant, int step_off) {
     __shared__ float sG[BOUNCE_GROUP][3];
     __shared__ double sV[BOUNCE_GROUP][3];
     __shared__ JumpSmem js;

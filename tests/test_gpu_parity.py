@@ -61,8 +61,13 @@ def _setup(name, seed=11, perturb=0.0):
     return s, ctx, md
 
 
-@pytest.mark.parametrize("name", list(CASES))
+CASES_ROWS = dict(CASES, box_large=(lambda: water_box(10, seed=4),
+                                     dict(r_on=4.0, r_off=5.0, r_cut=8.0, skin=1.0, ewald_beta=0.35)))
+
+
+@pytest.mark.parametrize("name", list(CASES_ROWS))
 def test_rows_bit_exact(name):
+    CASES.setdefault(name, CASES_ROWS[name])
     s, ctx, md = _setup(name, perturb=0.05)
     got = ctx.rows()
     assert len(got) == len(md.row_list)
