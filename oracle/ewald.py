@@ -112,12 +112,21 @@ def bspline_deriv(x, n):
 
 
 def _bmod2(K, n):
-    """|b(m)|^2 = 1 / |sum_{k=0}^{n-2} M_n(k+1) exp(2 pi i m k / K)|^2."""
+    """|b(m)|^2 = 1 / |sum_{k=0}^{n-2} M_n(k+1) exp(2 pi i m k / K)|^2.
+
+    For odd n the sum vanishes at the Nyquist index m = K/2; there |b|^2 is
+    taken as the mean of its two neighbours (this project's reading; C(m)
+    is negligible at that frequency for any usable grid)."""
     m = np.arange(K)
     k = np.arange(n - 1)
     w = bspline(k + 1.0, n)
-    s = (w[None, :] * np.exp(2j * math.pi * np.outer(m, k) / K)).sum(1)
-    return 1.0 / np.abs(s) ** 2
+    s = np.abs((w[None, :] * np.exp(2j * math.pi * np.outer(m, k) / K)).sum(1)) ** 2
+    out = np.empty(K)
+    ok = s > 1e-7
+    out[ok] = 1.0 / s[ok]
+    for j in np.nonzero(~ok)[0]:
+        out[j] = 0.5 * (1.0 / s[(j - 1) % K] + 1.0 / s[(j + 1) % K])
+    return out
 
 
 def spme_influence(box, beta, grid, order):

@@ -40,6 +40,8 @@ class Params:
     box: np.ndarray = None     # periodic edges (3,), None = open
     lj_sigma: np.ndarray = None
     lj_eps: np.ndarray = None
+    pme_grid: tuple = None     # SPME grid (K1, K2, K3) for periodic Ewald, None = no reciprocal part
+    pme_order: int = 5         # B-spline order
 
 
 def chi(r, r_on, r_off):
@@ -94,7 +96,7 @@ def displacement(qi, qj, box):
 def _uncut(p):
     """The same parameters without the cutoff (callers apply inside_cut)."""
     return Params(r_on=p.r_on, r_off=p.r_off, r_cut=math.inf, ewald_beta=p.ewald_beta, box=p.box,
-                  lj_sigma=p.lj_sigma, lj_eps=p.lj_eps)
+                  lj_sigma=p.lj_sigma, lj_eps=p.lj_eps, pme_grid=p.pme_grid, pme_order=p.pme_order)
 
 
 def all_pairs(mol):

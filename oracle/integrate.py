@@ -25,6 +25,11 @@ Readings of the paper used here (all listed in the design notes):
     O uses slot 0: Box-Muller on (x0, x1) and (x2, x3).
   * Units: v in A/fs, gradients in kcal/mol/A; a kick is
     v <- v - (h * 4.184e-4 / m) G.
+  * Periodic Ewald (Sec. V): the reciprocal part (SPME) plus the removal of
+    excluded (same-molecule) pairs from it is one gradient term G_recip.
+    BAOAB adds it to the full gradient; basic BOUNCE adds it to F_0 (every
+    step); BOUNCE-RESPA kicks with it over Delta/2 = m delta/2 before and
+    after every block of m BJAOAJB steps (the outer splitting of Sec. V).
 """
 import math
 import numpy as np
@@ -34,6 +39,7 @@ from .forcefield import (ACCEL, KB, Params, bonded_gradients, pair_gradients, pa
                          bonded_gradient_magnitudes, pair_gradient_one, kinetic_energy, pair_energies,
                          pair_energy_magnitudes, bonded_energies)
 from .neighbors import rows as build_rows, needs_rebuild, to_pairs
+from . import ewald
 
 
 class Topology:
@@ -163,6 +169,20 @@ class OracleMD:
         return (pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "full")
                 + bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box))
 
+    def has_recip(self):
+        return self.p.box is not None and self.p.ewald_beta > 0 and self.p.pme_grid is not None
+
+    def recip(self):
+        """(E_recip + E_self + E_excl, gradient of E_recip + E_excl)."""
+        if not self.has_recip():
+            return 0.0, np.zeros_like(self.q)
+        t = self.topo
+        er, gr = ewald.spme_recip(self.q, t.charge, self.p.box, self.p.ewald_beta, self.p.pme_grid, self.p.pme_order)
+        if not hasattr(self, "_excl"):
+            self._excl = ewald.molecule_pairs(t.mol)
+        ex, gx = ewald.exclusion(self.q, t.charge, self._excl, self.p.ewald_beta, self.p.box)
+        return er + ex + ewald.self_energy(t.charge, self.p.ewald_beta), gr + gx
+
     def grad_long(self):
         ii, jj = self.pairs()
         t = self.topo
@@ -199,29 +219,45 @@ class OracleMD:
     def step_baoab(self):
         h = 0.5 * self.dt
         self.ensure_rows()
-        self.kick(self.grad_full(), h)
+        self.kick(self.grad_full() + self.recip()[1], h)
         self.drift(h)
         self.v = o_step(self.v, self.topo.mass, self.T, self.gamma, self.dt, self.seed, self.step_index)
         self.drift(h)
         self.ensure_rows()
-        self.kick(self.grad_full(), h)
+        self.kick(self.grad_full() + self.recip()[1], h)
         self.step_index += 1
 
-    def step_bounce(self, record=False):
+    def step_bounce(self, record=False, with_recip=True):
+        """One BJAOAJB step; F_0 includes G_recip unless with_recip is False
+        (BOUNCE-RESPA moves it to the outer kicks)."""
         h = 0.5 * self.dt
         self.ensure_rows()
-        self.kick(self.grad_short(), h)
+        self.kick(self.grad_short() + (self.recip()[1] if with_recip else 0.0), h)
         r1 = self.jump(philox.STREAM_J1, record)
         self.drift(h)
         self.v = o_step(self.v, self.topo.mass, self.T, self.gamma, self.dt, self.seed, self.step_index)
         self.drift(h)
         self.ensure_rows()
         r2 = self.jump(philox.STREAM_J2, record)
-        self.kick(self.grad_short(), h)
+        self.kick(self.grad_short() + (self.recip()[1] if with_recip else 0.0), h)
         self.step_index += 1
         return (r1, r2) if record else None
 
-    def run(self, n, integrator="bounce"):
+    def block_bounce_respa(self, m=2):
+        """One outer step Delta = m delta of BOUNCE-RESPA: kick with G_recip
+        over Delta/2, m BJAOAJB steps without it, kick again over Delta/2."""
+        H = 0.5 * m * self.dt
+        self.kick(self.recip()[1], H)
+        for _ in range(m):
+            self.step_bounce(with_recip=False)
+        self.kick(self.recip()[1], H)
+
+    def run(self, n, integrator="bounce", respa_m=2):
+        if integrator == "bounce_respa":
+            assert n % respa_m == 0
+            for _ in range(n // respa_m):
+                self.block_bounce_respa(respa_m)
+            return
         for _ in range(n):
             if integrator == "bounce":
                 self.step_bounce()
@@ -235,4 +271,5 @@ class OracleMD:
         ec, el = pair_energies(self.q, t.charge, t.type, ii, jj, self.p)
         eb, ea = bonded_energies(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box)
         ek = kinetic_energy(self.v, t.mass)
-        return dict(coul=ec, lj=el, bond=eb, angle=ea, kin=ek, pot=ec + el + eb + ea)
+        er = self.recip()[0]
+        return dict(coul=ec, lj=el, bond=eb, angle=ea, recip=er, kin=ek, pot=ec + el + eb + ea + er)

@@ -17,6 +17,8 @@
 
 namespace {
 
+constexpr int RANGE_MAX = 128;  // cell-row runs per atom (<= 2 (2*3+1)^2 = 98)
+
 __device__ __forceinline__ bool pending(const DevSys& s, int force) { return force || *s.rebuild; }
 
 __device__ __forceinline__ void cell_of(const DevSys& s, const Params& p, float4 hi, int& cx, int& cy, int& cz) {
@@ -137,75 +139,127 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
         const bool fullz = s.ncz <= 2 * s.mz + 1, fully = s.ncy <= 2 * s.my + 1, fullx = s.ncx <= 2 * s.mx + 1;
         const int z0 = fullz ? 0 : cz - s.mz, z1 = fullz ? s.ncz - 1 : cz + s.mz;
         const int y0 = fully ? 0 : cy - s.my, y1 = fully ? s.ncy - 1 : cy + s.my;
-        for (int zu = z0; zu <= z1; ++zu) {
-            int zz = zu;
-            if (!fullz) {
-                if (p.periodic) zz = (zu % s.ncz + s.ncz) % s.ncz;
-                else if (zu < 0 || zu >= s.ncz) continue;
-            }
-            float gz = 0.f;
-            if (cull && !fullz) gz = fmaxf(fmaxf((float)zu - fz, fz - (float)(zu + 1)), 0.f) * s.hz;
-            if (gz * gz > rc2) continue;
-            for (int yu = y0; yu <= y1; ++yu) {
-                int yy = yu;
+        // 1) lanes compute the candidate ranges of all (z, y) cell rows in
+        //    parallel: up to two contiguous runs of cells per row (periodic
+        //    wrap), each a contiguous run of atoms in the cell-sorted array
+        int* rb = (int*)(bm + words_per_warp - 3 * RANGE_MAX);
+        int* rl = rb + RANGE_MAX;
+        int* rp = rl + RANGE_MAX;
+        const int nzr = z1 - z0 + 1, nyr = y1 - y0 + 1, nrows = nzr * nyr;
+        int nr_tot = 0;
+        for (int r0 = 0; r0 < nrows; r0 += 32) {
+            const int r = r0 + lane;
+            int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
+            if (r < nrows) {
+                const int zu = z0 + r / nyr, yu = y0 + r % nyr;
+                int zz = zu, yy = yu;
+                bool ok = true;
+                if (!fullz) {
+                    if (p.periodic) zz = (zu % s.ncz + s.ncz) % s.ncz;
+                    else ok = zu >= 0 && zu < s.ncz;
+                }
                 if (!fully) {
                     if (p.periodic) yy = (yu % s.ncy + s.ncy) % s.ncy;
-                    else if (yu < 0 || yu >= s.ncy) continue;
+                    else ok = ok && yu >= 0 && yu < s.ncy;
                 }
-                float gy = 0.f;
+                float gz = 0.f, gy = 0.f;
+                if (cull && !fullz) gz = fmaxf(fmaxf((float)zu - fz, fz - (float)(zu + 1)), 0.f) * s.hz;
                 if (cull && !fully) gy = fmaxf(fmaxf((float)yu - fy, fy - (float)(yu + 1)), 0.f) * s.hy;
                 const float g2 = gz * gz + gy * gy;
-                if (g2 > rc2) continue;
-                // x-span of cells the sphere can reach in this row
-                int xa, xb;
-                if (fullx) {
-                    xa = 0;
-                    xb = s.ncx - 1;
-                } else if (cull) {
-                    const float hw = sqrtf(rc2 - g2) * s.ihx;
-                    xa = max((int)floorf(fx - hw), cx - s.mx);
-                    xb = min((int)floorf(fx + hw), cx + s.mx);
-                } else {
-                    xa = cx - s.mx;
-                    xb = cx + s.mx;
-                }
-                // up to two contiguous ranges of cells (periodic wrap), each a
-                // contiguous range of atoms in the cell-sorted array
-                int ra[2], rb[2], nr = 0;
-                if (fullx) {
-                    ra[0] = xa; rb[0] = xb; nr = 1;
-                } else if (p.periodic) {
-                    if (xa < 0) { ra[nr] = xa + s.ncx; rb[nr] = s.ncx - 1; ++nr; xa = 0; }
-                    if (xb >= s.ncx) { ra[nr] = 0; rb[nr] = xb - s.ncx; ++nr; xb = s.ncx - 1; }
-                    if (xa <= xb) { ra[nr] = xa; rb[nr] = xb; ++nr; }
-                } else {
-                    xa = max(xa, 0);
-                    xb = min(xb, s.ncx - 1);
-                    if (xa <= xb) { ra[0] = xa; rb[0] = xb; nr = 1; }
-                }
-                const int rowc = (zz * s.ncy + yy) * s.ncx;
-                for (int t = 0; t < nr; ++t) {
-                    const int b = s.cell_start[rowc + ra[t]], e = s.cell_start[rowc + rb[t] + 1];
-                    for (int k = b + lane; k < e; k += 32) {
-                        const int j = s.cell_atoms[k];
-                        if (j == i || s.mol[j] == mi) continue;
-                        // screen with the high FP32 parts; the band covers their error
-                        const float4 hj = s.phi[cur][j];
-                        float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
-                        if (p.periodic) {
-                            dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
-                            dy -= rintf(dy * p.invL[1]) * p.Lhi[1];
-                            dz -= rintf(dz * p.invL[2]) * p.Lhi[2];
-                        }
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        bool in;
-                        if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
-                        else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
-                        else in = in_list_fp64(s, p, cur, i, j);
-                        if (in) atomicOr(&bm[j >> 5], 1u << (j & 31));
+                if (ok && g2 <= rc2) {
+                    int xa, xb;
+                    if (fullx) {
+                        xa = 0;
+                        xb = s.ncx - 1;
+                    } else if (cull) {
+                        const float hw = sqrtf(rc2 - g2) * s.ihx;
+                        xa = max((int)floorf(fx - hw), cx - s.mx);
+                        xb = min((int)floorf(fx + hw), cx + s.mx);
+                    } else {
+                        xa = cx - s.mx;
+                        xb = cx + s.mx;
+                    }
+                    const int rowc = (zz * s.ncy + yy) * s.ncx;
+                    int ca[3], cb[3], nrr = 0;
+                    if (fullx) {
+                        ca[0] = xa; cb[0] = xb; nrr = 1;
+                    } else if (p.periodic) {
+                        if (xa < 0) { ca[nrr] = xa + s.ncx; cb[nrr] = s.ncx - 1; ++nrr; xa = 0; }
+                        if (xb >= s.ncx) { ca[nrr] = 0; cb[nrr] = xb - s.ncx; ++nrr; xb = s.ncx - 1; }
+                        if (xa <= xb) { ca[nrr] = xa; cb[nrr] = xb; ++nrr; }
+                    } else {
+                        xa = max(xa, 0);
+                        xb = min(xb, s.ncx - 1);
+                        if (xa <= xb) { ca[0] = xa; cb[0] = xb; nrr = 1; }
+                    }
+                    if (nrr > 0) {
+                        b0 = s.cell_start[rowc + ca[0]];
+                        l0 = s.cell_start[rowc + cb[0] + 1] - b0;
+                    }
+                    if (nrr > 1) {
+                        b1 = s.cell_start[rowc + ca[1]];
+                        l1 = s.cell_start[rowc + cb[1] + 1] - b1;
+                    }
+                    if (nrr > 2) {  // both wraps: the span covers the whole row
+                        b0 = s.cell_start[rowc];
+                        l0 = s.cell_start[rowc + s.ncx] - b0;
+                        l1 = 0;
                     }
                 }
             }
+            // compact non-empty runs into the per-warp list, in row order
+            const bool h0 = l0 > 0, h1 = l1 > 0;
+            const int cnt = (int)h0 + (int)h1;
+            int x = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            int pos = nr_tot + x - cnt;
+            if (h0 && pos < RANGE_MAX) { rb[pos] = b0; rl[pos] = l0; ++pos; }
+            if (h1 && pos < RANGE_MAX) { rb[pos] = b1; rl[pos] = l1; }
+            nr_tot += __shfl_sync(0xffffffffu, x, 31);
+        }
+        nr_tot = min(nr_tot, RANGE_MAX);
+        __syncwarp();
+        // 2) exclusive prefix of the run lengths
+        int total_c = 0;
+        for (int r0 = 0; r0 < nr_tot; r0 += 32) {
+            const int r = r0 + lane;
+            const int len = r < nr_tot ? rl[r] : 0;
+            int x = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (r < nr_tot) rp[r] = total_c + x - len;
+            total_c += __shfl_sync(0xffffffffu, x, 31);
+        }
+        __syncwarp();
+        // 3) all lanes stride over the concatenated candidates
+        for (int t = lane; t < total_c; t += 32) {
+            int lo_r = 0, hi_r = nr_tot - 1;
+            while (lo_r < hi_r) {  // last run with prefix <= t
+                const int mid = (lo_r + hi_r + 1) >> 1;
+                if (rp[mid] <= t) lo_r = mid;
+                else hi_r = mid - 1;
+            }
+            const int j = s.cell_atoms[rb[lo_r] + (t - rp[lo_r])];
+            if (j == i || s.mol[j] == mi) continue;
+            // screen with the high FP32 parts; the band covers their error
+            const float4 hj = s.phi[cur][j];
+            float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
+            if (p.periodic) {
+                dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
+                dy -= rintf(dy * p.invL[1]) * p.Lhi[1];
+                dz -= rintf(dz * p.invL[2]) * p.Lhi[2];
+            }
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            bool in;
+            if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
+            else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
+            else in = in_list_fp64(s, p, cur, i, j);
+            if (in) atomicOr(&bm[j >> 5], 1u << (j & 31));
         }
         __syncwarp();
         // bitmap -> ascending row
