@@ -175,6 +175,7 @@ def our_arm(args):
         torch.cuda.synchronize()
         ctx.reset_counters(stream=sh)
         ms = 0.0
+        launches = 0
         t_end = []
         with Clocks(local) as clk:
             _barrier(ws)
@@ -182,6 +183,7 @@ def our_arm(args):
             torch.cuda.nvtx.range_push(name + "_timed")
             for k, w in enumerate(windows):
                 ctx.set_state(q0, v0, step=100000 * (k + 1))
+                launches += ctx.run_launch_count(w, integ)
                 flush.fill_(float(k))
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
@@ -211,7 +213,7 @@ def our_arm(args):
         ep = ctx.energies(stream=sh)
         res[name] = dict(ms=ms, clocks=clk.summary(), energies=e, t_end=t_end, e2e_s=t_e2e, kernel_ms=kms,
                          kernel_launches=nl, prof=ep,
-                         launches=sum(int(bounce.bounce_run_launch_count(w)) for w in windows))
+                         launches=launches)
         ctx.close()
     steps = args.steps
     out = {}

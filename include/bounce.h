@@ -50,11 +50,14 @@ extern "C" {
 /* Integrators (bounce_run). */
 #define BOUNCE_BAOAB 0  /* B A O A B (paper Sec. III.C without J)            */
 #define BOUNCE_BOUNCE 1 /* B J A O A J B (paper Sec. III.C and Sec. IV.B)    */
+#define BOUNCE_BOUNCE_RESPA 2 /* reciprocal-space kick over Delta/2 = m delta/2
+                               * around every block of m BJAOAJB steps (Sec. V) */
 
 /* Gradient parts (bounce_compute_gradient). */
 #define BOUNCE_GRAD_FULL 0  /* dE_pot/dq: all pairs within r_c + bonded     */
 #define BOUNCE_GRAD_SHORT 1 /* F_0: bonded + (1 - chi) W' of every pair     */
 #define BOUNCE_GRAD_LONG 2  /* sum_j F_ij = chi W' of every pair (Sec. IV.A) */
+#define BOUNCE_GRAD_RECIP 3 /* SPME reciprocal Ewald + same-molecule removal */
 
 #define BOUNCE_MAX_TYPES 4
 #define BOUNCE_NOALLOC_MAX_ATOMS 16384
@@ -77,6 +80,9 @@ typedef struct bounce_config {
     int32_t max_neighbors; /* capacity of one candidate row (2048)               */
     int32_t max_short;     /* capacity of one short-range row (256)              */
     int32_t device;        /* CUDA device ordinal (0)                            */
+    int32_t pme_grid[3];   /* SPME grid K1 K2 K3; 0 = no reciprocal part (0)     */
+    int32_t pme_order;     /* SPME B-spline order, 3..8 (5)                      */
+    int32_t respa_m;       /* inner steps per BOUNCE-RESPA outer step (2)        */
 } bounce_config;
 
 /* Energies and counters (bounce_get_energies). */
@@ -95,6 +101,7 @@ typedef struct bounce_energies {
     int64_t rebuilds;   /* candidate-row rebuilds                                 */
     int64_t short_pairs;/* pair terms evaluated for F_0 (BOUNCE)                 */
     int64_t full_pairs; /* pair terms evaluated for the full gradient (BAOAB)    */
+    double recip;       /* E_recip + E_self + E_exclusion of periodic Ewald (0)   */
 } bounce_energies;
 
 /* Fill *cfg with the defaults documented above. */
@@ -129,8 +136,12 @@ int bounce_set_state(bounce_ctx* ctx, const double* q, const double* v, int64_t 
 /* Copy the current state out (q, v may be NULL to skip). */
 int bounce_get_state(bounce_ctx* ctx, double* q, double* v, int32_t where, void* stream);
 
-/* Advance n_steps full steps of the integrator (BOUNCE_BAOAB or
- * BOUNCE_BOUNCE); the returned state is after the last B half-kick.  All
+/* Advance n_steps full steps of the integrator (BOUNCE_BAOAB,
+ * BOUNCE_BOUNCE or BOUNCE_BOUNCE_RESPA); the returned state is after the
+ * last B half-kick.  With an SPME grid set, the reciprocal gradient is part
+ * of the full gradient (BAOAB) or of F_0 (BOUNCE, Sec. V basic BOUNCE);
+ * BOUNCE_BOUNCE_RESPA needs the grid, a step counter and n_steps that are
+ * multiples of respa_m (else INVALID_ARG).  All
  * work stays on the device; the call does not synchronise `stream` except
  * to report row overflows, which it checks once at the end.
  * Errors: STATE, LIST_OVERFLOW (a row exceeded max_neighbors; the state is
@@ -186,10 +197,10 @@ int bounce_msd(bounce_ctx* ctx, int32_t type, double* out, void* stream);
 int bounce_profile_steps(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, void* stream, double* kernel_ms,
                          int64_t* launches);
 
-/* Number of kernel launches bounce_run issues for n_steps (for launch
- * accounting: head and tail launches, gated row-rebuild launches, graph
- * chunks and step-counter updates). */
-int64_t bounce_run_launch_count(int64_t n_steps);
+/* Number of kernel launches a bounce_run of n_steps of `integrator` would
+ * issue from the current state (launch accounting: gated row-rebuild
+ * launches, step kernels, SPME launches, step-counter updates). */
+int64_t bounce_run_launch_count(const bounce_ctx* ctx, int64_t n_steps, int32_t integrator);
 
 /* Allocation-free pair energies.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code running

@@ -25,8 +25,8 @@ _lib = C.CDLL(LIB_PATH)
 OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "NONFINITE", -4: "LIST_OVERFLOW", -5: "STATE", -6: "UNSUPPORTED"}
 HOST, DEVICE = 0, 1
-BAOAB, BOUNCE = 0, 1
-GRAD_FULL, GRAD_SHORT, GRAD_LONG = 0, 1, 2
+BAOAB, BOUNCE, BOUNCE_RESPA = 0, 1, 2
+GRAD_FULL, GRAD_SHORT, GRAD_LONG, GRAD_RECIP = 0, 1, 2, 3
 MAX_TYPES = 4
 
 
@@ -35,14 +35,16 @@ class bounce_config(C.Structure):
                 ("seed", C.c_uint64), ("r_on", C.c_double), ("r_off", C.c_double), ("r_cut", C.c_double),
                 ("skin", C.c_double), ("ewald_beta", C.c_double), ("periodic", C.c_int32),
                 ("box", C.c_double * 3), ("max_neighbors", C.c_int32), ("max_short", C.c_int32),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("pme_grid", C.c_int32 * 3), ("pme_order", C.c_int32),
+                ("respa_m", C.c_int32)]
 
 
 class bounce_energies(C.Structure):
     _fields_ = [("coulomb", C.c_double), ("lj", C.c_double), ("bond", C.c_double), ("angle", C.c_double),
                 ("kinetic", C.c_double), ("potential", C.c_double), ("temperature", C.c_double),
                 ("step", C.c_int64), ("proposals", C.c_int64), ("accepts", C.c_int64), ("near_ties", C.c_int64),
-                ("rebuilds", C.c_int64), ("short_pairs", C.c_int64), ("full_pairs", C.c_int64)]
+                ("rebuilds", C.c_int64), ("short_pairs", C.c_int64), ("full_pairs", C.c_int64),
+                ("recip", C.c_double)]
 
 
 _P = C.c_void_p
@@ -64,7 +66,7 @@ _sig = {
     "bounce_set_msd_reference": (C.c_int, [_P, _P]),
     "bounce_msd": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), _P]),
     "bounce_profile_steps": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
-    "bounce_run_launch_count": (C.c_int64, [C.c_int64]),
+    "bounce_run_launch_count": (C.c_int64, [_P, C.c_int64, C.c_int32]),
     "bounce_pair_energy_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, C.c_double, C.c_double,
                                              _P, _P, _P]),
     "bounce_last_error": (C.c_char_p, [_P]),
@@ -102,7 +104,8 @@ class Context:
     """One system on one GPU."""
 
     def __init__(self, *, dt=1.0, gamma=0.001, temperature=300.0, seed=0, r_on=4.0, r_off=5.0, r_cut=math.inf,
-                 skin=1.0, ewald_beta=0.0, box=None, max_neighbors=2048, max_short=256, device=0):
+                 skin=1.0, ewald_beta=0.0, box=None, max_neighbors=2048, max_short=256, device=0, pme_grid=None,
+                 pme_order=5, respa_m=2):
         cfg = bounce_config()
         bounce_config_default(C.byref(cfg))
         cfg.dt_fs, cfg.gamma_per_fs, cfg.temperature_K, cfg.seed = dt, gamma, temperature, seed
@@ -111,6 +114,9 @@ class Context:
         if box is not None:
             cfg.box[0], cfg.box[1], cfg.box[2] = [float(x) for x in box]
         cfg.max_neighbors, cfg.max_short, cfg.device = max_neighbors, max_short, device
+        if pme_grid is not None:
+            cfg.pme_grid[0], cfg.pme_grid[1], cfg.pme_grid[2] = [int(k) for k in pme_grid]
+        cfg.pme_order, cfg.respa_m = pme_order, respa_m
         self.cfg = cfg
         h = C.c_void_p()
         r = bounce_create(C.byref(h), C.byref(cfg))
@@ -191,6 +197,9 @@ class Context:
         self._check(bounce_profile_steps(self.h, int(n_steps), int(integrator), stream, C.byref(ms), C.byref(nl)),
                     "profile_steps")
         return ms.value, nl.value
+
+    def run_launch_count(self, n_steps, integrator=BOUNCE):
+        return int(bounce_run_launch_count(self.h, int(n_steps), int(integrator)))
 
     def get_state(self, q_out=None, v_out=None, stream=None):
         if q_out is not None and hasattr(q_out, "data_ptr"):

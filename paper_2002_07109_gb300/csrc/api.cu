@@ -60,7 +60,11 @@ struct bounce_ctx {
     size_t bitmap_bytes = 0;
     int ncell_alloc = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[3][8] = {};   // [integrator][RESPA phase of the chunk's first step]
+    long long cur_step = 0;              // host mirror of the device step counter
+    bool has_pme = false;
+    DevPme pme{};
+    double e_self = 0.0;
 };
 
 namespace {
@@ -90,11 +94,12 @@ int dalloc(bounce_ctx* c, T** out, size_t count) {
 }
 
 void drop_graphs(bounce_ctx* c) {
-    for (auto& g : c->graph)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (auto& row : c->graph)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
 }
 
 void free_all(bounce_ctx* c) {
@@ -108,6 +113,8 @@ void free_all(bounce_ctx* c) {
     c->hist = nullptr;
     c->hist_alloc = 0;
     c->have_msd_ref = false;
+    c->has_pme = false;
+    c->pme = DevPme{};
 }
 
 // ---------------------------------------------------------------- bounds
@@ -203,6 +210,99 @@ void compute_bounds(bounce_ctx* c, const std::vector<double>& sig, const std::ve
 double r_list(const bounce_config& cfg) {
     const bool cut = std::isfinite(cfg.r_cut) && cfg.r_cut > 0;
     return cut ? cfg.r_cut + cfg.skin : INFINITY;
+}
+
+// ------------------------------------------------------------- SPME set-up
+double bspline_host(double x, int n) {
+    if (n == 2) return (x >= 0.0 && x <= 2.0) ? 1.0 - std::fabs(x - 1.0) : 0.0;
+    return (x * bspline_host(x, n - 1) + (n - x) * bspline_host(x - 1.0, n - 1)) / (n - 1);
+}
+
+// |b(m)|^2 of the Euler exponential spline; at the zero of odd orders
+// (m = K/2) the mean of the two neighbours.
+std::vector<double> bmod2_host(int K, int n) {
+    std::vector<double> s(K), out(K);
+    for (int m = 0; m < K; ++m) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k <= n - 2; ++k) {
+            const double w = bspline_host(k + 1.0, n), a = 2.0 * M_PI * m * k / K;
+            re += w * std::cos(a);
+            im += w * std::sin(a);
+        }
+        s[m] = re * re + im * im;
+    }
+    for (int m = 0; m < K; ++m)
+        out[m] = s[m] > 1e-7 ? 1.0 / s[m] : 0.5 * (1.0 / s[(m - 1 + K) % K] + 1.0 / s[(m + 1) % K]);
+    return out;
+}
+
+int setup_pme(bounce_ctx* c) {
+    const bounce_config& g = c->cfg;
+    c->has_pme = false;
+    if (!(g.periodic && g.ewald_beta > 0 && g.pme_grid[0] > 0 && g.pme_grid[1] > 0 && g.pme_grid[2] > 0)) return BOUNCE_OK;
+    if (g.pme_order < 3 || g.pme_order > 8 || g.pme_grid[0] > 512 || g.pme_grid[1] > 512 || g.pme_grid[2] > 512 ||
+        g.respa_m < 1 || g.respa_m > 8)
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad SPME or RESPA parameters");
+    DevPme& m = c->pme;
+    for (int d = 0; d < 3; ++d) {
+        m.K[d] = g.pme_grid[d];
+        m.L[d] = g.box[d];
+        if (m.K[d] < g.pme_order) return fail(c, BOUNCE_ERR_INVALID_ARG, "SPME grid smaller than the order");
+    }
+    m.order = g.pme_order;
+    m.beta = (float)g.ewald_beta;
+    m.two_b_sqrtpi = (float)(2.0 * g.ewald_beta / std::sqrt(M_PI));
+    const size_t N = (size_t)m.K[0] * m.K[1] * m.K[2];
+    // influence function B(m) C(m), C = exp(-pi^2 m^2/beta^2)/(pi V m^2), in FP64
+    const double V = g.box[0] * g.box[1] * g.box[2];
+    std::vector<double> b[3];
+    for (int d = 0; d < 3; ++d) b[d] = bmod2_host(m.K[d], m.order);
+    std::vector<float> bc(N);
+    for (int i = 0; i < m.K[0]; ++i) {
+        const double fx = (i <= m.K[0] / 2 ? i : i - m.K[0]) / g.box[0];
+        for (int j = 0; j < m.K[1]; ++j) {
+            const double fy = (j <= m.K[1] / 2 ? j : j - m.K[1]) / g.box[1];
+            for (int k = 0; k < m.K[2]; ++k) {
+                const double fz = (k <= m.K[2] / 2 ? k : k - m.K[2]) / g.box[2];
+                const double m2 = fx * fx + fy * fy + fz * fz;
+                const double C = m2 > 0 ? std::exp(-M_PI * M_PI * m2 / (g.ewald_beta * g.ewald_beta)) / (M_PI * V * m2) : 0.0;
+                bc[((size_t)i * m.K[1] + j) * m.K[2] + k] = (float)(b[0][i] * b[1][j] * b[2][k] * C);
+            }
+        }
+    }
+    // same-molecule partners of every atom
+    std::vector<int> off(c->n + 1, 0), idx;
+    {
+        std::vector<std::vector<int>> bym;
+        int maxm = 0;
+        for (int i = 0; i < c->n; ++i) maxm = std::max(maxm, c->mol[i] + 1);
+        bym.resize(maxm);
+        for (int i = 0; i < c->n; ++i) bym[c->mol[i]].push_back(i);
+        for (int i = 0; i < c->n; ++i) {
+            for (int j : bym[c->mol[i]])
+                if (j != i) idx.push_back(j);
+            off[i + 1] = (int)idx.size();
+        }
+    }
+    float* dbc;
+    int *doff, *didx;
+    int r;
+    if ((r = dalloc(c, &m.qgrid, N)) || (r = dalloc(c, &m.cgrid, N)) || (r = dalloc(c, &dbc, N)) ||
+        (r = dalloc(c, &m.grad, 3 * (size_t)c->n)) || (r = dalloc(c, &m.eexcl, c->n)) || (r = dalloc(c, &m.eterm, 256)) ||
+        (r = dalloc(c, &doff, c->n + 1)) || (r = dalloc(c, &didx, std::max<size_t>(idx.size(), 1))))
+        return r;
+    CU(cudaMemcpy(dbc, bc.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(doff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!idx.empty()) CU(cudaMemcpy(didx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    m.bc = dbc;
+    m.ex_off = doff;
+    m.ex_idx = didx;
+    c->ds.grecip = m.grad;
+    double q2 = 0.0;
+    for (int i = 0; i < c->n; ++i) q2 += c->charge[i] * c->charge[i];
+    c->e_self = -KCOUL_D * g.ewald_beta / std::sqrt(M_PI) * q2;
+    c->has_pme = true;
+    return BOUNCE_OK;
 }
 
 void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vector<double>& eps) {
@@ -341,20 +441,60 @@ int check_err(bounce_ctx* c, cudaStream_t st) {
     return BOUNCE_OK;
 }
 
-int ensure_graph(bounce_ctx* c, int integ) {
-    if (c->graph[integ]) return BOUNCE_OK;
+// What happens at one step boundary: whether the reciprocal gradient is
+// evaluated there and the time hr it kicks over (see k_step).
+void plan(const bounce_ctx* c, int integ, int variant, long long step, bool& pme, double& hr) {
+    const double dt = c->cfg.dt_fs;
+    const double hk = variant == 1 ? dt : 0.5 * dt;
+    pme = false;
+    hr = 0.0;
+    if (!c->has_pme) return;
+    if (integ != BOUNCE_BOUNCE_RESPA) {
+        pme = true;
+        hr = hk;
+        return;
+    }
+    const int m = c->cfg.respa_m;
+    if (step % m == 0) {
+        pme = true;
+        hr = (variant == 1 ? 1.0 : 0.5) * m * dt;
+    }
+}
+
+void boundary(bounce_ctx* c, int integ, int variant, int off, long long step, cudaStream_t st) {
+    bool pme;
+    double hr;
+    plan(c, integ, variant, step, pme, hr);
+    rebuild(c, off, false, st);
+    if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
+    launch_step(c->ds, c->pp, integ, variant, off, hr, st);
+}
+
+// Graph of CHUNK body steps whose first step index is congruent to `phase`
+// modulo respa_m (the RESPA block boundaries inside a chunk depend on it).
+int ensure_graph(bounce_ctx* c, int integ, int phase) {
+    if (c->graph[integ][phase]) return BOUNCE_OK;
     cudaStream_t st = c->cap_stream;
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < CHUNK; ++k) {
-        rebuild(c, k, false, st);
-        launch_step(c->ds, c->pp, integ, 1, k, st);
-    }
+    for (int k = 0; k < CHUNK; ++k) boundary(c, integ, 1, k, (long long)phase + k, st);
     launch_advance_step(c->ds, CHUNK, st);
     CU(cudaStreamEndCapture(st, &g));
-    cudaError_t e = cudaGraphInstantiate(&c->graph[integ], g, 0);
+    cudaError_t e = cudaGraphInstantiate(&c->graph[integ][phase], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(c, BOUNCE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return BOUNCE_OK;
+}
+
+int check_run_args(bounce_ctx* c, int64_t n_steps, int32_t integ) {
+    if (n_steps < 0 || (integ != BOUNCE_BAOAB && integ != BOUNCE_BOUNCE && integ != BOUNCE_BOUNCE_RESPA))
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad run arguments");
+    if (integ == BOUNCE_BOUNCE_RESPA) {
+        const int m = c->cfg.respa_m;
+        if (!c->has_pme) return fail(c, BOUNCE_ERR_INVALID_ARG, "BOUNCE-RESPA needs an SPME grid");
+        if (n_steps % m != 0 || c->cur_step % m != 0)
+            return fail(c, BOUNCE_ERR_INVALID_ARG, "BOUNCE-RESPA runs whole outer steps (multiples of respa_m)");
+    }
     return BOUNCE_OK;
 }
 
@@ -488,7 +628,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
         (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, (size_t)n * s.caps)) ||
         (r = dalloc(c, &s.refx, n)) || (r = dalloc(c, &s.refy, n)) || (r = dalloc(c, &s.refz, n)) ||
         (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
-        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 1024)))
+        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 2048)))
         return r;
     s.kick = kick;
     s.osd = osd;
@@ -553,6 +693,10 @@ int bounce_set_lj(bounce_ctx* c, int32_t T, const double* sigma, const double* e
     compute_bounds(c, sg, ep);
     fill_params(c, sg, ep);
     drop_graphs(c);
+    if (!c->has_pme) {
+        int r = setup_pme(c);
+        if (r) return r;
+    }
     c->have_lj = true;
     return BOUNCE_OK;
 }
@@ -610,6 +754,7 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
     CU(cudaMemsetAsync(s.err, 0, sizeof(int), st));
     CU(cudaStreamSynchronize(st));
     c->step0 = step;
+    c->cur_step = step;
     c->have_state = true;
     return BOUNCE_OK;
 }
@@ -645,30 +790,30 @@ int bounce_get_state(bounce_ctx* c, double* q, double* v, int32_t where, void* s
 int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
     if (!c) return BOUNCE_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
-    if (n_steps < 0 || (integ != BOUNCE_BAOAB && integ != BOUNCE_BOUNCE))
-        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad run arguments");
+    int r = check_run_args(c, n_steps, integ);
+    if (r) return r;
     if (n_steps == 0) return BOUNCE_OK;
     cudaSetDevice(c->cfg.device);
     cudaStream_t st = (cudaStream_t)stream;
-    int r = ensure_graph(c, integ);
-    if (r) return r;
+    const int m = c->cfg.respa_m > 0 ? c->cfg.respa_m : 1;
+    long long s0 = c->cur_step;
     // head: B/2 [J] A O A at the current step
-    rebuild(c, 0, false, st);
-    launch_step(c->ds, c->pp, integ, 0, 0, st);
+    boundary(c, integ, 0, 0, s0, st);
     launch_advance_step(c->ds, 1, st);
+    long long base = s0 + 1;
     int64_t rem = n_steps - 1;
     while (rem >= CHUNK) {
-        CU(cudaGraphLaunch(c->graph[integ], st));
+        const int phase = (int)(base % m);
+        if ((r = ensure_graph(c, integ, phase))) return r;
+        CU(cudaGraphLaunch(c->graph[integ][phase], st));
         rem -= CHUNK;
+        base += CHUNK;
     }
-    for (int64_t k = 0; k < rem; ++k) {
-        rebuild(c, (int)k, false, st);
-        launch_step(c->ds, c->pp, integ, 1, (int)k, st);
-    }
+    for (int64_t k = 0; k < rem; ++k) boundary(c, integ, 1, (int)k, base + k, st);
     if (rem) launch_advance_step(c->ds, rem, st);
     // tail: [J] B/2
-    rebuild(c, 0, false, st);
-    launch_step(c->ds, c->pp, integ, 2, 0, st);
+    boundary(c, integ, 2, 0, s0 + n_steps, st);
+    c->cur_step = s0 + n_steps;
     CU(cudaGetLastError());
     return check_err(c, st);
 }
@@ -677,27 +822,29 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
                          int64_t* launches) {
     if (!c) return BOUNCE_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
-    if (n_steps < 1 || (integ != BOUNCE_BAOAB && integ != BOUNCE_BOUNCE) || !kernel_ms)
-        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad profile arguments");
+    if (n_steps < 1 || !kernel_ms) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad profile arguments");
+    if (int r0 = check_run_args(c, n_steps, integ)) return r0;
     cudaSetDevice(c->cfg.device);
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<cudaEvent_t> ev(2 * (size_t)(n_steps + 1));
     for (auto& e : ev) CU(cudaEventCreate(&e));
-    auto timed = [&](int k, int variant, int off) {
+    const long long s0 = c->cur_step;
+    auto timed = [&](int k, int variant, int off, long long step) {
+        bool pme;
+        double hr;
+        plan(c, integ, variant, step, pme, hr);
+        rebuild(c, off, false, st);
+        if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
         cudaEventRecord(ev[2 * k], st);
-        launch_step(c->ds, c->pp, integ, variant, off, st);
+        launch_step(c->ds, c->pp, integ, variant, off, hr, st);
         cudaEventRecord(ev[2 * k + 1], st);
     };
-    rebuild(c, 0, false, st);
-    timed(0, 0, 0);
+    timed(0, 0, 0, s0);
     launch_advance_step(c->ds, 1, st);
-    for (int64_t k = 0; k < n_steps - 1; ++k) {
-        rebuild(c, (int)k, false, st);
-        timed((int)k + 1, 1, (int)k);
-    }
+    for (int64_t k = 0; k < n_steps - 1; ++k) timed((int)k + 1, 1, (int)k, s0 + 1 + k);
     if (n_steps > 1) launch_advance_step(c->ds, n_steps - 1, st);
-    rebuild(c, 0, false, st);
-    timed((int)n_steps, 2, 0);
+    timed((int)n_steps, 2, 0, s0 + n_steps);
+    c->cur_step = s0 + n_steps;
     CU(cudaStreamSynchronize(st));
     double tot = 0.0;
     for (int64_t k = 0; k <= n_steps; ++k) {
@@ -711,12 +858,19 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
     return check_err(c, st);
 }
 
-int64_t bounce_run_launch_count(int64_t n) {
-    if (n <= 0) return 0;
-    const int64_t per_step = 6;  // 5 gated row-rebuild kernels + the fused step kernel
-    const int64_t rem_all = n - 1;
-    const int64_t chunks = rem_all / CHUNK, rem = rem_all % CHUNK;
-    return per_step + 1 + chunks * (CHUNK * per_step + 1) + rem * per_step + (rem ? 1 : 0) + per_step;
+int64_t bounce_run_launch_count(const bounce_ctx* c, int64_t n, int32_t integ) {
+    if (!c || n <= 0) return 0;
+    const int64_t per_boundary = 6;  // 5 gated row-rebuild kernels + the fused step kernel
+    const int64_t pme_launches = 10; // spread, load, 3 + 3 transforms, convolve, gather
+    int64_t total = 2;               // step-counter updates after the head and the bodies
+    for (int64_t k = 0; k <= n; ++k) {
+        bool pme;
+        double hr;
+        plan(c, integ, k == 0 ? 0 : (k == n ? 2 : 1), c->cur_step + k, pme, hr);
+        total += per_boundary + (pme ? pme_launches : 0);
+    }
+    total += (n - 1) / CHUNK;        // one counter update per replayed graph chunk
+    return total;
 }
 
 int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
@@ -729,7 +883,12 @@ int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     CU(cudaStreamSynchronize(st));
     rebuild(c, 0, false, st);
     launch_energies(c->ds, c->pp, (int)(step & 1), c->terms, st);
-    double tot[5];
+    double tot[5], pe[2] = {0.0, 0.0};
+    if (c->has_pme) {
+        launch_pme(c->ds, c->pp, c->pme, 0, st);
+        launch_pme_energy(c->pme, c->n, c->terms + 6 * (size_t)c->n + 1024, st);
+        CU(cudaMemcpyAsync(pe, c->terms + 6 * (size_t)c->n + 1024, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     CU(cudaMemcpyAsync(tot, c->terms + 5 * (size_t)c->n, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaMemcpyAsync(c->h_cnt, c->ds.cnt, CNT_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -740,7 +899,8 @@ int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     out->bond = tot[2];
     out->angle = tot[3];
     out->kinetic = tot[4];
-    out->potential = out->coulomb + out->lj + out->bond + out->angle;
+    out->recip = c->has_pme ? pe[0] + pe[1] + c->e_self : 0.0;
+    out->potential = out->coulomb + out->lj + out->bond + out->angle + out->recip;
     out->temperature = 2.0 * tot[4] / (3.0 * c->n * KB_D);
     out->step = step - c->step0;
     out->proposals = (int64_t)c->h_cnt[CNT_PROPOSALS];
@@ -836,7 +996,7 @@ int bounce_get_bounds(bounce_ctx* c, double* L, double* Lstar) {
 }
 
 int bounce_compute_gradient(bounce_ctx* c, int32_t part, double* grad, int32_t where, void* stream) {
-    if (!c || !grad || part < 0 || part > 2 || (where != BOUNCE_HOST && where != BOUNCE_DEVICE))
+    if (!c || !grad || part < 0 || part > 3 || (where != BOUNCE_HOST && where != BOUNCE_DEVICE))
         return fail(c, BOUNCE_ERR_INVALID_ARG, "bad gradient arguments");
     if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
     cudaSetDevice(c->cfg.device);
@@ -845,10 +1005,18 @@ int bounce_compute_gradient(bounce_ctx* c, int32_t part, double* grad, int32_t w
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     rebuild(c, 0, false, st);
-    double* out = c->terms;  // scratch of 6 n doubles >= 3 n
-    launch_gradient(c->ds, c->pp, part, (int)(step & 1), out, st);
-    CU(cudaMemcpyAsync(grad, out, 3 * (size_t)c->n * sizeof(double),
-                       where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    const cudaMemcpyKind kind = where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (part == BOUNCE_GRAD_RECIP) {
+        if (!c->has_pme) return fail(c, BOUNCE_ERR_STATE, "no SPME grid configured");
+        launch_pme(c->ds, c->pp, c->pme, 0, st);
+        for (int d = 0; d < 3; ++d)
+            CU(cudaMemcpy2DAsync(grad + d, 3 * sizeof(double), c->pme.grad + (size_t)d * c->n, sizeof(double),
+                                 sizeof(double), c->n, kind, st));
+    } else {
+        double* out = c->terms;  // scratch of 6 n doubles >= 3 n
+        launch_gradient(c->ds, c->pp, part, (int)(step & 1), out, st);
+        CU(cudaMemcpyAsync(grad, out, 3 * (size_t)c->n * sizeof(double), kind, st));
+    }
     CU(cudaStreamSynchronize(st));
     return check_err(c, st);
 }

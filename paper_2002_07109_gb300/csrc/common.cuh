@@ -68,6 +68,23 @@ struct DevSys {
     int* err;
     unsigned long long* cnt;
     const long long* step_base;
+    const double* grecip;    // reciprocal + exclusion gradient [3 n] (SoA), null without PME
+};
+
+// Smooth particle-mesh Ewald state (periodic boxes with a reciprocal part).
+struct DevPme {
+    int K[3];
+    int order;
+    double L[3];
+    float beta, two_b_sqrtpi;
+    unsigned long long* qgrid;   // int64 fixed-point charge grid (2^40 scale)
+    float2* cgrid;               // complex work grid
+    const float* bc;             // influence function B(m) C(m)
+    double* grad;                // [3 n] SoA gradient of E_recip + E_excl
+    double* eexcl;               // [n] exclusion energy per atom (pairs j > i)
+    double* eterm;               // [256] energy partials of the convolution
+    const int* ex_off;           // [n + 1] same-molecule partners of each atom
+    const int* ex_idx;
 };
 
 // Scalar parameters (passed by value; fits the kernel parameter space).
@@ -322,7 +339,10 @@ __device__ __forceinline__ float3 bonded_grad(const Params& p, const DevSys& s, 
 // Launchers implemented in the .cu files.
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
                     cudaStream_t st);
-void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, cudaStream_t st);
+void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
+                 cudaStream_t st);
+void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st);
+void launch_pme_energy(const DevPme& m, int n, double* out, cudaStream_t st);
 void launch_gradient(const DevSys& s, const Params& p, int part, int cur, double* out, cudaStream_t st);
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,
                       cudaStream_t st);

@@ -213,8 +213,11 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
 }
 
 // variant: 0 head (B/2 [J1] A O A), 1 body ([J2] B [J1] A O A), 2 tail ([J2] B/2)
+// hr: time over which the reciprocal-space gradient kicks at this boundary
+// (0 without it; delta or delta/2 when it is part of F_0 or of BAOAB's full
+// gradient; Delta or Delta/2 at BOUNCE-RESPA block boundaries).
 template <int BOUNCE>
-__global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int variant, int step_off) {
+__global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int variant, int step_off, double hr) {
     __shared__ float sG[BOUNCE_GROUP][3];
     __shared__ double sV[BOUNCE_GROUP][3];
     __shared__ JumpSmem js;
@@ -276,6 +279,12 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
         vx -= c * (double)sG[lane][0];
         vy -= c * (double)sG[lane][1];
         vz -= c * (double)sG[lane][2];
+        if (hr != 0.0) {
+            const double cr = hr * s.kick[i];
+            vx -= cr * s.grecip[i];
+            vy -= cr * s.grecip[s.n + i];
+            vz -= cr * s.grecip[2 * (size_t)s.n + i];
+        }
         sV[lane][0] = vx;
         sV[lane][1] = vy;
         sV[lane][2] = vz;
@@ -405,10 +414,11 @@ __global__ void k_advance(DevSys s, long long by) { *const_cast<long long*>(s.st
 
 }  // namespace
 
-void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, cudaStream_t st) {
+void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
+                 cudaStream_t st) {
     const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
-    if (integrator == 1) k_step<1><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off);
-    else k_step<0><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off);
+    if (integrator != 0) k_step<1><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr);
+    else k_step<0><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr);
 }
 
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,

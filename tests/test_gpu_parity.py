@@ -45,6 +45,8 @@ CASES = {
     "droplet_cutoff": (lambda: water_droplet_molecules(300, seed=2), dict(r_on=4.0, r_off=5.0, r_cut=9.0, skin=1.0)),
     "box_ewald": (lambda: water_box(6, seed=3), dict(r_on=4.0, r_off=5.0, r_cut=8.0, skin=1.0, ewald_beta=0.35)),
 }
+PME_CASE = (lambda: water_box(6, seed=3), dict(r_on=7.0, r_off=8.0, r_cut=9.0, skin=1.0, ewald_beta=0.35,
+                                              pme_grid=(20, 20, 20), pme_order=5, max_short=640))
 
 
 def _setup(name, seed=11, perturb=0.0):
@@ -55,7 +57,8 @@ def _setup(name, seed=11, perturb=0.0):
     ctx = bounce.from_system(s, seed=seed, **cfg)
     ctx.set_state(q, s.v, step=7)
     p = Params(r_on=cfg["r_on"], r_off=cfg["r_off"], r_cut=cfg["r_cut"], ewald_beta=cfg.get("ewald_beta", 0.0),
-               box=s.box, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps)
+               box=s.box, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps, pme_grid=cfg.get("pme_grid"),
+               pme_order=cfg.get("pme_order", 5))
     md = OracleMD(q, s.v, _topo(s), p, seed=seed, skin=cfg.get("skin", 1.0), step=7)
     md.ensure_rows()
     return s, ctx, md
@@ -266,4 +269,80 @@ def test_observables(name):
     md.run(5, "baoab")
     q, _ = ctx.get_state()
     assert abs(ctx.msd(0) - msd(q, q0, s.type, 0)) < 1e-12 * max(1.0, msd(q, q0, s.type, 0))
+    ctx.close()
+
+
+def _setup_pme(seed=11, perturb=0.05):
+    CASES.setdefault("box_pme", PME_CASE)
+    return _setup("box_pme", seed=seed, perturb=perturb)
+
+
+def test_recip_gradient_and_energy():
+    from oracle import ewald
+    s, ctx, md = _setup_pme()
+    g = ctx.gradient(bounce.GRAD_RECIP)
+    er, gr = ewald.spme_recip(md.q, s.charge, s.box, 0.35, (20, 20, 20), 5)
+    ex, gx = ewald.exclusion(md.q, s.charge, ewald.molecule_pairs(s.molecule), 0.35, s.box)
+    # error scale: the magnitudes of the two summed parts
+    scale = np.linalg.norm(gr, axis=1) + np.linalg.norm(gx, axis=1)
+    _check_sum(g, gr + gx, scale)
+    e = ctx.energies()
+    ref = md.energies()
+    es = ewald.self_energy(s.charge, 0.35)
+    assert abs(e["recip"] - ref["recip"]) < 1e-6 * (abs(er) + abs(ex) + abs(es)), (e["recip"], ref["recip"])
+    ctx.close()
+
+
+def _kick_scale(md, part, with_recip):
+    """||v_i|| error scale of one step: the summed magnitudes of the gradient
+    terms an atom is kicked with, times dt 4.184e-4 / m."""
+    from oracle import ewald
+    from oracle.forcefield import ACCEL
+    c = md.grad_scale(part)
+    if with_recip:
+        t = md.topo
+        _, gr = ewald.spme_recip(md.q, t.charge, md.p.box, md.p.ewald_beta, md.p.pme_grid, md.p.pme_order)
+        _, gx = ewald.exclusion(md.q, t.charge, ewald.molecule_pairs(t.mol), md.p.ewald_beta, md.p.box)
+        c = c + np.linalg.norm(gr, axis=1) + np.linalg.norm(gx, axis=1)
+    return md.dt * ACCEL / t_mass(md) * c
+
+
+def t_mass(md):
+    return md.topo.mass
+
+
+@pytest.mark.parametrize("integrator", ["baoab", "bounce", "bounce_respa"])
+def test_one_step_with_recip(integrator):
+    s, ctx, md = _setup_pme(perturb=0.0)
+    q0 = md.q.copy()
+    kscale = _kick_scale(md, "full" if integrator == "baoab" else "short", True)
+    tie = np.zeros(s.n_atoms, bool)
+    if integrator == "baoab":
+        ctx.run(1, bounce.BAOAB)
+        md.step_baoab()
+    elif integrator == "bounce":
+        ctx.run(1, bounce.BOUNCE)
+        for r in md.step_bounce(record=True):
+            tie[r["atom"][np.abs(r["U"] - r["ratio"]) < 1e-6]] = True
+    else:
+        ctx.set_state(md.q, md.v, step=8)        # RESPA blocks start at multiples of m
+        md.step_index = 8
+        ctx.run(2, bounce.BOUNCE_RESPA)
+        md.run(2, "bounce_respa", respa_m=2)
+    q, v = ctx.get_state()
+    dq = np.linalg.norm(q - md.q, axis=1) / np.maximum(np.linalg.norm(md.q - q0, axis=1), 1e-6)
+    assert dq[~tie].max() < TOL, dq[~tie].max()
+    dv = np.linalg.norm(v - md.v, axis=1)
+    assert (dv / (np.linalg.norm(md.v, axis=1) + kscale))[~tie].max() < TOL
+    assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
+    e = ctx.energies()
+    assert e["recip"] != 0.0
+    ctx.close()
+
+
+def test_respa_rejects_partial_blocks():
+    s, ctx, md = _setup_pme(perturb=0.0)
+    ctx.set_state(md.q, md.v, step=8)
+    with pytest.raises(bounce.BounceError):
+        ctx.run(3, bounce.BOUNCE_RESPA)
     ctx.close()
