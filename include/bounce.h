@@ -173,6 +173,43 @@ int bounce_jump_half(bounce_ctx* ctx, int64_t step, int32_t stream_id, int32_t* 
  * counts[n] and rows[n * capacity] (ascending atom indices). */
 int bounce_get_rows(bounce_ctx* ctx, int32_t* counts, int32_t* rows, int32_t capacity);
 
+/* Batch of independent replicas in one context (BASELINE's batched
+ * droplets).  The topology holds all replicas back to back; replica r owns
+ * atoms [atom_offsets[r], atom_offsets[r+1]) and draws every random number
+ * with its own Philox key seeds[r] and its atoms' indices inside the
+ * replica, so each replica follows exactly the trajectory it would follow
+ * alone.  Pairs and jump candidates never cross replicas.  Replicas are open
+ * droplets without a cutoff (every other-molecule atom of the replica);
+ * max_neighbors must be at least the largest replica size - 1.  Every
+ * bounce_run step then advances all replicas in the same kernel launches;
+ * energies and counters are totals over the batch.  Call after
+ * bounce_set_topology. */
+int bounce_set_replicas(bounce_ctx* ctx, int32_t n_replicas, const int32_t* atom_offsets, const uint64_t* seeds);
+
+/* Differentiable direct-space pair forces (force matching; the pair terms of
+ * Sec. IV.A / V with trainable per-type parameters).  Parameters are host
+ * tables: q_type[T] charges per atom type (replacing the topology charges in
+ * these two calls), sigma[T*T] and eps[T*T] read from the upper triangle
+ * (entry (a, b), a <= b, is the parameter of both orders).  Pairs: other
+ * molecules with r^2 < r_c^2 (Coulomb or Ewald direct erfc, plus LJ); the
+ * reciprocal and bonded parts are not included.
+ *
+ * bounce_pair_forward: with q (device [n,3]) non-NULL the positions are first
+ * replaced and the rows rebuilt; forces (device [n,3]) receive
+ * F_i = -dE_pair/dq_i and *energy (host, may be NULL) E_pair = sum_{i<j} W. */
+int bounce_pair_forward(bounce_ctx* ctx, const double* q, int32_t n_types, const double* q_type, const double* sigma,
+                        const double* eps, double* forces, double* energy, void* stream);
+
+/* Backward of the last forward for a loss L(F, E): grad_forces (device
+ * [n,3]) = dL/dF, grad_energy = dL/dE.  Receives grad_pos (device [n,3]) =
+ * dL/dq (through the pair Hessian), and on the host grad_q_type[T],
+ * grad_sigma[T*T], grad_eps[T*T] (entry (a, b) and (b, a) both hold the
+ * derivative with respect to the shared table entry).  FP32 pair math, FP64
+ * fixed-order reductions. */
+int bounce_pair_backward(bounce_ctx* ctx, int32_t n_types, const double* q_type, const double* sigma,
+                         const double* eps, const double* grad_forces, double grad_energy, double* grad_pos,
+                         double* grad_q_type, double* grad_sigma, double* grad_eps, void* stream);
+
 /* Observables (paper Sec. VI). */
 
 /* Counts of unordered pairs (different molecules) of the type pair

@@ -62,6 +62,9 @@ _sig = {
     "bounce_compute_gradient": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
     "bounce_jump_half": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, C.c_int32, _P]),
     "bounce_get_rows": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "bounce_set_replicas": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "bounce_pair_forward": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, C.POINTER(C.c_double), _P]),
+    "bounce_pair_backward": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_double, _P, _P, _P, _P, _P]),
     "bounce_pair_histogram": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_double, C.c_int32, _P, _P]),
     "bounce_set_msd_reference": (C.c_int, [_P, _P]),
     "bounce_msd": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), _P]),
@@ -159,6 +162,12 @@ class Context:
         self.n = n
         self.n_types = int(t.max()) + 1
 
+    def set_replicas(self, atom_offsets, seeds):
+        off = _host(atom_offsets, np.int32)
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        self._keep_rep = (off, sd)
+        self._check(bounce_set_replicas(self.h, len(off) - 1, _ptr(off), _ptr(sd)), "set_replicas")
+
     def set_lj(self, sigma, eps):
         s = _host(sigma, np.float64)
         e = _host(eps, np.float64)
@@ -175,6 +184,30 @@ class Context:
     # ---- run / read
     def run(self, n_steps, integrator=BOUNCE, stream=None):
         self._check(bounce_run(self.h, int(n_steps), int(integrator), stream), "run")
+
+    def pair_forward(self, q, q_type, sigma, eps, forces, stream=None):
+        """Pair forces (into the device tensor `forces`) and pair energy at the
+        device positions q (None: the current positions)."""
+        qt = _host(q_type, np.float64)
+        sg = _host(sigma, np.float64)
+        ep = _host(eps, np.float64)
+        e = C.c_double()
+        self._check(bounce_pair_forward(self.h, None if q is None else _ptr(q), len(qt), _ptr(qt), _ptr(sg), _ptr(ep),
+                                        _ptr(forces), C.byref(e), stream), "pair_forward")
+        return e.value
+
+    def pair_backward(self, q_type, sigma, eps, grad_forces, grad_energy, grad_pos, stream=None):
+        """dL/dq into the device tensor grad_pos; returns host arrays
+        (dL/dq_type, dL/dsigma, dL/deps)."""
+        qt = _host(q_type, np.float64)
+        sg = _host(sigma, np.float64)
+        ep = _host(eps, np.float64)
+        T = len(qt)
+        gq, gs, ge = np.zeros(T), np.zeros(T * T), np.zeros(T * T)
+        self._check(bounce_pair_backward(self.h, T, _ptr(qt), _ptr(sg), _ptr(ep), _ptr(grad_forces),
+                                         float(grad_energy), _ptr(grad_pos), _ptr(gq), _ptr(gs), _ptr(ge), stream),
+                    "pair_backward")
+        return gq, gs.reshape(T, T), ge.reshape(T, T)
 
     def pair_histogram(self, type_a, type_b, r_max, n_bins, stream=None):
         h = np.zeros(int(n_bins), np.int64)
@@ -273,3 +306,37 @@ def from_system(sys, **kw):
                      sys.angle_k_t0)
     ctx.set_lj(sys.lj_sigma, sys.lj_eps)
     return ctx
+
+
+def pair_forces_function():
+    """A torch.autograd.Function over bounce_pair_forward / bounce_pair_backward:
+    apply(q, q_type, sigma, eps, ctx) -> (forces, energy) with q a CUDA
+    float64 (n, 3) tensor and the parameters CPU float64 tensors; sigma and
+    eps are symmetric tables whose gradients hold, at (a, b) and (b, a), the
+    derivative with respect to the shared entry."""
+    import torch
+
+    class PairForces(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, q, q_type, sigma, eps, ctx):
+            q = q.contiguous()
+            F = torch.empty_like(q)
+            stream = torch.cuda.current_stream(q.device).cuda_stream
+            E = ctx.pair_forward(q, q_type.detach().numpy(), sigma.detach().numpy(), eps.detach().numpy(), F,
+                                 stream=stream)
+            fctx.save_for_backward(q_type, sigma, eps)
+            fctx.bctx = ctx
+            return F, torch.tensor(E, dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, gF, gE):
+            q_type, sigma, eps = fctx.saved_tensors
+            gF = torch.zeros_like(gF) if gF is None else gF.contiguous()
+            gpos = torch.empty_like(gF)
+            stream = torch.cuda.current_stream(gF.device).cuda_stream
+            gq, gs, ge = fctx.bctx.pair_backward(q_type.detach().numpy(), sigma.detach().numpy(),
+                                                 eps.detach().numpy(), gF, 0.0 if gE is None else float(gE), gpos,
+                                                 stream=stream)
+            return (gpos, torch.from_numpy(gq), torch.from_numpy(gs), torch.from_numpy(ge), None)
+
+    return PairForces

@@ -13,6 +13,12 @@
 #include "common.cuh"
 
 void nlist_set_smem_limit(size_t bytes);
+int diff_param_count();
+void launch_pair_forward(const DevSys& s, const Params& p, const float* qt, const float* sig, const float* eps, int T,
+                         int cur, double* F, double* eatom, double* esum, cudaStream_t st);
+void launch_pair_backward(const DevSys& s, const Params& p, const float* qt, const float* sig, const float* eps, int T,
+                          int cur, const double* U, double w, double* gpos, double* part, double* psum,
+                          cudaStream_t st);
 void launch_pair_hist(const DevSys& s, const Params& p, int cur, int ta, int tb, double r_max, int n_bins,
                       unsigned long long* hist, cudaStream_t st);
 void launch_msd(const DevSys& s, const double* rx, const double* ry, const double* rz, int cur, int t,
@@ -64,6 +70,7 @@ struct bounce_ctx {
     long long cur_step = 0;              // host mirror of the device step counter
     bool has_pme = false;
     DevPme pme{};
+    double* diff_part = nullptr;   // [NPAR n + NPAR] parameter partials and sums of the pair backward
     double e_self = 0.0;
 };
 
@@ -115,6 +122,7 @@ void free_all(bounce_ctx* c) {
     c->have_msd_ref = false;
     c->has_pme = false;
     c->pme = DevPme{};
+    c->diff_part = nullptr;
 }
 
 // ---------------------------------------------------------------- bounds
@@ -617,7 +625,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     int4* bidx;
     float2* bpar;
     const double rl = r_list(c->cfg);
-    s.cap = std::isfinite(rl) ? c->cfg.max_neighbors : std::max(1, n - 1);
+    s.cap = std::isfinite(rl) ? c->cfg.max_neighbors : std::max(1, std::min(n - 1, c->cfg.max_neighbors));
     const double rs = c->cfg.r_off + c->cfg.skin;
     s.caps = (std::isfinite(rs) && rs < rl) ? c->cfg.max_short : s.cap;
     if ((r = dalloc(c, &s.vx, n)) || (r = dalloc(c, &s.vy, n)) || (r = dalloc(c, &s.vz, n)) ||
@@ -1064,6 +1072,132 @@ int bounce_get_rows(bounce_ctx* c, int32_t* counts, int32_t* rows, int32_t capac
         for (int k = 0; k < std::min(cnt[i], capacity); ++k) rows[(size_t)i * capacity + k] = all[(size_t)i * cap + k];
     }
     return BOUNCE_OK;
+}
+
+int bounce_set_replicas(bounce_ctx* c, int32_t n_rep, const int32_t* off, const uint64_t* seeds) {
+    if (!c || n_rep < 1 || !off || !seeds) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad replica arguments");
+    if (!c->have_topo) return fail(c, BOUNCE_ERR_STATE, "set the topology first");
+    if (c->cfg.periodic || (std::isfinite(c->cfg.r_cut) && c->cfg.r_cut > 0))
+        return fail(c, BOUNCE_ERR_UNSUPPORTED, "replica batches are open droplets without a cutoff");
+    if (off[0] != 0 || off[n_rep] != c->n) return fail(c, BOUNCE_ERR_INVALID_ARG, "offsets must cover all atoms");
+    std::vector<int> rep(c->n), loc(c->n);
+    int maxn = 0;
+    for (int r = 0; r < n_rep; ++r) {
+        if (off[r + 1] <= off[r]) return fail(c, BOUNCE_ERR_INVALID_ARG, "empty or unordered replica");
+        maxn = std::max(maxn, off[r + 1] - off[r]);
+        for (int i = off[r]; i < off[r + 1]; ++i) {
+            rep[i] = r;
+            loc[i] = i - off[r];
+        }
+    }
+    // a molecule must not span two replicas
+    std::vector<int> mol_rep;
+    for (int i = 0; i < c->n; ++i) {
+        const int m = c->mol[i];
+        if (m >= (int)mol_rep.size()) mol_rep.resize(m + 1, -1);
+        if (mol_rep[m] >= 0 && mol_rep[m] != rep[i]) return fail(c, BOUNCE_ERR_INVALID_ARG, "molecule spans replicas");
+        mol_rep[m] = rep[i];
+    }
+    if (maxn - 1 > c->ds.cap) return fail(c, BOUNCE_ERR_INVALID_ARG, "max_neighbors below the largest replica size - 1");
+    cudaSetDevice(c->cfg.device);
+    std::vector<uint2> keys(n_rep);
+    for (int r = 0; r < n_rep; ++r) keys[r] = make_uint2((uint32_t)(seeds[r] & 0xFFFFFFFFull), (uint32_t)(seeds[r] >> 32));
+    int *drep, *dloc, *doff;
+    uint2* dkey;
+    int rr;
+    if ((rr = dalloc(c, &drep, c->n)) || (rr = dalloc(c, &dloc, c->n)) || (rr = dalloc(c, &doff, n_rep + 1)) ||
+        (rr = dalloc(c, &dkey, n_rep)))
+        return rr;
+    CU(cudaMemcpy(drep, rep.data(), c->n * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dloc, loc.data(), c->n * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(doff, off, (n_rep + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dkey, keys.data(), n_rep * sizeof(uint2), cudaMemcpyHostToDevice));
+    c->ds.rep_of = drep;
+    c->ds.local_idx = dloc;
+    c->ds.rep_off = doff;
+    c->ds.rep_key = dkey;
+    drop_graphs(c);
+    return BOUNCE_OK;
+}
+
+// Per-type parameters as FP32 tables, sigma and eps symmetrised from the
+// upper triangle (entry (a, b) with a <= b is the parameter of the pair).
+static int diff_tables(bounce_ctx* c, int32_t T, const double* qt, const double* sig, const double* eps, float* fq,
+                       float* fs, float* fe) {
+    if (T < c->n_types || T > BOUNCE_MAXT || !qt || !sig || !eps)
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad parameter tables");
+    for (int a = 0; a < BOUNCE_MAXT; ++a) fq[a] = a < T ? (float)qt[a] : 0.f;
+    for (int a = 0; a < BOUNCE_MAXT * BOUNCE_MAXT; ++a) fs[a] = fe[a] = 0.f;
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const int lo = std::min(a, b), hi = std::max(a, b);
+            fs[a * BOUNCE_MAXT + b] = (float)sig[lo * T + hi];
+            fe[a * BOUNCE_MAXT + b] = (float)eps[lo * T + hi];
+        }
+    return BOUNCE_OK;
+}
+
+int bounce_pair_forward(bounce_ctx* c, const double* q, int32_t T, const double* qt, const double* sig,
+                        const double* eps, double* forces, double* energy, void* stream) {
+    if (!c || !forces) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad forward arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    float fq[BOUNCE_MAXT], fs[BOUNCE_MAXT * BOUNCE_MAXT], fe[BOUNCE_MAXT * BOUNCE_MAXT];
+    int r = diff_tables(c, T, qt, sig, eps, fq, fs, fe);
+    if (r) return r;
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int cur = (int)(c->cur_step & 1);
+    const int n = c->n;
+    if (q) {
+        CU(cudaMemcpy2DAsync(c->ds.qx[cur], sizeof(double), q + 0, 3 * sizeof(double), sizeof(double), n,
+                             cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpy2DAsync(c->ds.qy[cur], sizeof(double), q + 1, 3 * sizeof(double), sizeof(double), n,
+                             cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpy2DAsync(c->ds.qz[cur], sizeof(double), q + 2, 3 * sizeof(double), sizeof(double), n,
+                             cudaMemcpyDeviceToDevice, st));
+        launch_pack_positions(c->ds, c->pp, cur, st);
+        rebuild(c, 0, true, st);
+    } else {
+        rebuild(c, 0, false, st);
+    }
+    double* eatom = c->terms;
+    double* esum = c->terms + 6 * (size_t)n + 1024;
+    launch_pair_forward(c->ds, c->pp, fq, fs, fe, T, cur, forces, eatom, esum, st);
+    double e = 0.0;
+    CU(cudaMemcpyAsync(&e, esum, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (energy) *energy = e;
+    return check_err(c, st);
+}
+
+int bounce_pair_backward(bounce_ctx* c, int32_t T, const double* qt, const double* sig, const double* eps,
+                         const double* grad_forces, double grad_energy, double* grad_pos, double* grad_qt,
+                         double* grad_sig, double* grad_eps, void* stream) {
+    if (!c || !grad_forces || !grad_pos) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad backward arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    float fq[BOUNCE_MAXT], fs[BOUNCE_MAXT * BOUNCE_MAXT], fe[BOUNCE_MAXT * BOUNCE_MAXT];
+    int r = diff_tables(c, T, qt, sig, eps, fq, fs, fe);
+    if (r) return r;
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int np = diff_param_count();
+    if (!c->diff_part && (r = dalloc(c, &c->diff_part, (size_t)np * c->n + np))) return r;
+    const int cur = (int)(c->cur_step & 1);
+    double* psum = c->diff_part + (size_t)np * c->n;
+    launch_pair_backward(c->ds, c->pp, fq, fs, fe, T, cur, grad_forces, grad_energy, grad_pos, c->diff_part, psum, st);
+    std::vector<double> ps(np);
+    CU(cudaMemcpyAsync(ps.data(), psum, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const int M = BOUNCE_MAXT;
+    for (int a = 0; a < T; ++a) {
+        if (grad_qt) grad_qt[a] = ps[a];
+        for (int b = 0; b < T; ++b) {
+            const int lo = std::min(a, b), hi = std::max(a, b);
+            if (grad_sig) grad_sig[a * T + b] = ps[M + lo * M + hi];
+            if (grad_eps) grad_eps[a * T + b] = ps[M + M * M + lo * M + hi];
+        }
+    }
+    return check_err(c, st);
 }
 
 const char* bounce_last_error(const bounce_ctx* c) {

@@ -69,6 +69,12 @@ struct DevSys {
     unsigned long long* cnt;
     const long long* step_base;
     const double* grecip;    // reciprocal + exclusion gradient [3 n] (SoA), null without PME
+    // batched independent replicas (null for one system): replica of each
+    // atom, its index inside the replica and each replica's Philox key
+    const int* rep_of;
+    const int* local_idx;
+    const uint2* rep_key;
+    const int* rep_off;      // [replicas + 1] first atom of each replica
 };
 
 // Smooth particle-mesh Ewald state (periodic boxes with a reciprocal part).
@@ -137,6 +143,20 @@ __device__ __forceinline__ uint4 rng_draw(const Params& p, uint32_t slot, uint32
                                           uint32_t stream) {
     uint4 c = make_uint4(slot, atom, (uint32_t)(step & 0xFFFFFFFFll),
                          (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFll));
+    return philox4x32_10(c, p.key0, p.key1);
+}
+
+// Draw for atom i: its replica's key and its index inside the replica when
+// the context holds a batch, the run key and the global index otherwise.
+__device__ __forceinline__ uint4 rng_atom(const DevSys& s, const Params& p, uint32_t slot, int i, long long step,
+                                          uint32_t stream) {
+    uint4 c = make_uint4(slot, 0u, (uint32_t)(step & 0xFFFFFFFFll), (stream << 24) | (uint32_t)((step >> 32) & 0xFFFFFFll));
+    if (s.rep_of) {
+        const uint2 k = s.rep_key[s.rep_of[i]];
+        c.y = (uint32_t)s.local_idx[i];
+        return philox4x32_10(c, k.x, k.y);
+    }
+    c.y = (uint32_t)i;
     return philox4x32_10(c, p.key0, p.key1);
 }
 

@@ -319,6 +319,60 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
     }
 }
 
+// Rows of a batch of independent all-pairs replicas: every atom of the same
+// replica outside the own molecule, ascending (no distance test: replicas
+// have no cutoff), then the short rows and reference positions as above.
+__global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
+    if (!pending(s, force)) return;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int cur = (int)((*s.step_base + step_off) & 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < s.n; i += gridDim.x * wpb) {
+        const int r = s.rep_of[i], b = s.rep_off[r], e = s.rep_off[r + 1], mi = s.mol[i];
+        int* row = s.rows + (size_t)i * s.cap;
+        int total = 0;
+        for (int j0 = b; j0 < e; j0 += 32) {
+            const int j = j0 + lane;
+            const bool keep = j < e && s.mol[j] != mi;
+            const uint32_t m = __ballot_sync(0xffffffffu, keep);
+            const int pos = total + __popc(m & ((1u << lane) - 1u));
+            if (keep && pos < s.cap) row[pos] = j;
+            total += __popc(m);
+        }
+        __syncwarp();
+        const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
+        const int nl = min(total, s.cap);
+        int ns = 0;
+        int* srow = s.srows + (size_t)i * s.caps;
+        for (int k0 = 0; k0 < nl; k0 += 32) {
+            const int k = k0 + lane;
+            bool keep = false;
+            int j = 0;
+            if (k < nl) {
+                j = row[k];
+                const float3 d = pair_disp(p, hi, lo, s.phi[cur][j], s.plo[cur][j]);
+                keep = (d.x * d.x + d.y * d.y + d.z * d.z) < p.rshort2;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = ns + __popc(m & ((1u << lane) - 1u));
+                if (pos < s.caps) srow[pos] = j;
+            }
+            ns += __popc(m);
+        }
+        if (lane == 0) {
+            s.nlong[i] = nl;
+            if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
+            s.nshort[i] = min(ns, s.caps);
+            if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
+            s.refx[i] = s.qx[cur][i];
+            s.refy[i] = s.qy[cur][i];
+            s.refz[i] = s.qz[cur][i];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_rebuild_clear(DevSys s) { *s.rebuild = 0; }
 
 }  // namespace
@@ -326,6 +380,12 @@ __global__ void k_rebuild_clear(DevSys s) { *s.rebuild = 0; }
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
                     cudaStream_t st) {
     const int f = force ? 1 : 0;
+    if (s.rep_of) {
+        const int wpb = 8;
+        k_rows_batch<<<(s.n + wpb - 1) / wpb, wpb * 32, 0, st>>>(s, p, step_off, f);
+        k_rebuild_clear<<<1, 1, 0, st>>>(s);
+        return;
+    }
     const int tb = 256;
     const int gb = (s.n + tb - 1) / tb;
     k_cells_count<<<gb, tb, 0, st>>>(s, p, step_off, f);

@@ -89,7 +89,7 @@ __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int c
     const int nch = js.nch[a];
     int M = 0;
     for (int c = lane; c < nch; c += 32) {
-        const uint4 x = rng_draw(p, BOUNCE_POISSON_SLOT | (uint32_t)c, (uint32_t)i, step, stream);
+        const uint4 x = rng_atom(s, p, BOUNCE_POISSON_SLOT | (uint32_t)c, i, step, stream);
         M += poisson_invert_f32(u24(x.x), js.muc[a]);
     }
     M = warp_sum_i(M);
@@ -110,7 +110,7 @@ __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int c
             float gx = 0.f, gy = 0.f, gz = 0.f, uf = 1.f;
             uint32_t x1 = 0, x2 = 0;
             if (act) {
-                const uint4 x = rng_draw(p, (uint32_t)k, (uint32_t)i, step, stream);
+                const uint4 x = rng_atom(s, p, (uint32_t)k, i, step, stream);
                 const int J = (int)__umulhi(x.x, (uint32_t)n);
                 const int j = row[J];
                 const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
             const double h = 0.5 * p.dt;
             double x = s.qx[cur][i] + h * vx, y = s.qy[cur][i] + h * vy, z = s.qz[cur][i] + h * vz;
             // O: Box-Muller on Philox slot 0, stream 0
-            const uint4 r = rng_draw(p, 0u, (uint32_t)i, step, BOUNCE_STREAM_O);
+            const uint4 r = rng_atom(s, p, 0u, i, step, BOUNCE_STREAM_O);
             const float ra = sqrtf(-2.f * logf(u24_open0(r.x)));
             float sn, cs;
             sincospif(2.f * u24(r.y), &sn, &cs);

@@ -166,3 +166,34 @@ def replica_sizes(n_replicas, lo=64, hi=1024, seed=0):
     """Molecule counts of a batch of independent droplets, uniform on [lo, hi]."""
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi + 1, size=n_replicas)
+
+
+def concat_systems(systems, spacing=500.0):
+    """Back-to-back concatenation of open droplets into one topology (molecule
+    ids and bonded indices renumbered, replica r shifted by r * spacing along
+    x).  Returns the combined System and the atom offsets [R + 1]."""
+    offs = [0]
+    parts = {k: [] for k in ("q", "v", "type", "mass", "charge", "molecule", "bonds", "bond_k_r0", "angles",
+                             "angle_k_t0")}
+    mol0 = 0
+    for r, s in enumerate(systems):
+        a0 = offs[-1]
+        parts["q"].append(s.q + np.array([r * spacing, 0.0, 0.0]))
+        parts["v"].append(s.v)
+        parts["type"].append(s.type)
+        parts["mass"].append(s.mass)
+        parts["charge"].append(s.charge)
+        parts["molecule"].append(s.molecule + mol0)
+        parts["bonds"].append(s.bonds + a0)
+        parts["bond_k_r0"].append(s.bond_k_r0)
+        parts["angles"].append(s.angles + a0)
+        parts["angle_k_t0"].append(s.angle_k_t0)
+        mol0 += int(s.molecule.max()) + 1
+        offs.append(a0 + s.n_atoms)
+    cat = {k: np.concatenate(v) for k, v in parts.items()}
+    out = System(q=cat["q"], v=cat["v"], type=cat["type"].astype(np.int32), mass=cat["mass"], charge=cat["charge"],
+                 molecule=cat["molecule"].astype(np.int32), bonds=cat["bonds"].astype(np.int32),
+                 bond_k_r0=cat["bond_k_r0"], angles=cat["angles"].astype(np.int32), angle_k_t0=cat["angle_k_t0"],
+                 lj_sigma=systems[0].lj_sigma, lj_eps=systems[0].lj_eps, box=None)
+    out.meta.update(kind="batch", replicas=len(systems))
+    return out, np.array(offs, dtype=np.int32)
