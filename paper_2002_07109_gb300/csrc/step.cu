@@ -38,8 +38,10 @@ struct JumpSmem {
     float dv[BOUNCE_GROUP][3];    // accumulated jump increment
     float muc[BOUNCE_GROUP];      // Poisson chunk mean (FP32)
     int nch[BOUNCE_GROUP];        // number of Poisson chunks
-    int M[BOUNCE_GROUP];          // proposals (for the diagnostics entry point)
+    int M[BOUNCE_GROUP];          // proposals of each atom (sum of its Poisson chunks)
     int nacc[BOUNCE_GROUP];
+    int chp[BOUNCE_GROUP + 1];    // prefix of the chunk counts
+    float inv[129];               // 1/k, k = 0..128 (round-to-nearest reciprocals)
     int next;
     unsigned long long cnt[3];    // proposals, accepts, near ties
 };
@@ -82,17 +84,54 @@ __device__ __noinline__ int exact_decision(float vx, float vy, float vz, float g
     return td < ad ? 1 : 0;
 }
 
+// Poisson counts of the CTA's atoms (one half step): every thread takes
+// whole chunks (chunk c of atom a inverts Poisson(mu_c) with the uniform of
+// Philox slot 0x80000000 | c), one chunk per thread at a time, and adds its
+// count to the atom's total.  Called by all threads of the CTA.
+__device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, int base, int na, long long step,
+                              uint32_t stream) {
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int a = 0; a < na; ++a) {
+            js.chp[a] = acc;
+            acc += js.nch[a];
+            js.M[a] = 0;
+        }
+        js.chp[na] = acc;
+    }
+    __syncthreads();
+    const int tot = js.chp[na];
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int lo = 0, hi = na - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (js.chp[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int c = t - js.chp[lo];
+        const uint4 x = rng_atom(s, p, BOUNCE_POISSON_SLOT | (uint32_t)c, base + lo, step, stream);
+        // sequential search of the FP32 CDF (same operations as poisson_invert_f32)
+        const float u = u24(x.x), mu_c = js.muc[lo];
+        float pk = expneg_f32(mu_c), cdf = pk;
+        int k = 0;
+        while (u > cdf && k < 128) {
+            ++k;
+            const float q = __fmul_rn(__fmul_rn(pk, mu_c), js.inv[k]);
+            const float cn = __fadd_rn(cdf, q);
+            if (cn == cdf) break;
+            pk = q;
+            cdf = cn;
+        }
+        atomicAdd(&js.M[lo], k);
+    }
+    __syncthreads();
+}
+
 // Warp-cooperative jump chain of atom `a` (one half step).
 __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int cur, int a, int i, long long step,
                            uint32_t stream) {
     const int lane = threadIdx.x & 31;
-    const int nch = js.nch[a];
-    int M = 0;
-    for (int c = lane; c < nch; c += 32) {
-        const uint4 x = rng_atom(s, p, BOUNCE_POISSON_SLOT | (uint32_t)c, i, step, stream);
-        M += poisson_invert_f32(u24(x.x), js.muc[a]);
-    }
-    M = warp_sum_i(M);
+    const int M = js.M[a];
     float vx = js.vf[a][0], vy = js.vf[a][1], vz = js.vf[a][2];
     float dvx = 0.f, dvy = 0.f, dvz = 0.f;
     int nacc = 0, near = 0;
@@ -165,7 +204,6 @@ __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int c
         js.dv[a][0] = dvx;
         js.dv[a][1] = dvy;
         js.dv[a][2] = dvz;
-        js.M[a] = M;
         js.nacc[a] = nacc;
         atomicAdd(&js.cnt[0], (unsigned long long)M);
         atomicAdd(&js.cnt[1], (unsigned long long)nacc);
@@ -235,6 +273,8 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
         sPairs = 0ull;
         js.cnt[0] = js.cnt[1] = js.cnt[2] = 0ull;
     }
+    if (BOUNCE)
+        for (int k = threadIdx.x; k < 129; k += blockDim.x) js.inv[k] = k ? __frcp_rn((float)k) : 0.f;
     __syncthreads();
     // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n
     for (int a = warp; a < na; a += NW) {
@@ -258,6 +298,7 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
     if (threadIdx.x == 0) js.next = 0;
     __syncthreads();
     if (do_j2) {
+        poisson_phase(s, p, js, base, na, step - 1, BOUNCE_STREAM_J2);
         for (;;) {
             int a = 0;
             if (lane == 0) a = atomicAdd(&js.next, 1);
@@ -293,6 +334,7 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
     if (threadIdx.x == 0) js.next = 0;
     __syncthreads();
     if (do_j1) {
+        poisson_phase(s, p, js, base, na, step, BOUNCE_STREAM_J1);
         for (;;) {
             int a = 0;
             if (lane == 0) a = atomicAdd(&js.next, 1);
@@ -369,11 +411,13 @@ __global__ void __launch_bounds__(NW * 32) k_jump_half(DevSys s, Params p, int c
         js.cnt[0] = js.cnt[1] = js.cnt[2] = 0ull;
         js.next = 0;
     }
+    for (int k = threadIdx.x; k < 129; k += blockDim.x) js.inv[k] = k ? __frcp_rn((float)k) : 0.f;
     if (warp == 0 && lane < na) {
         const int i = base + lane;
         jump_prep(s, p, js, lane, i, s.vx[i], s.vy[i], s.vz[i]);
     }
     __syncthreads();
+    poisson_phase(s, p, js, base, na, step, (uint32_t)stream_id);
     for (;;) {
         int a = 0;
         if (lane == 0) a = atomicAdd(&js.next, 1);
