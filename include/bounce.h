@@ -52,6 +52,8 @@ extern "C" {
 #define BOUNCE_BOUNCE 1 /* B J A O A J B (paper Sec. III.C and Sec. IV.B)    */
 #define BOUNCE_BOUNCE_RESPA 2 /* reciprocal-space kick over Delta/2 = m delta/2
                                * around every block of m BJAOAJB steps (Sec. V) */
+#define BOUNCE_BOUNCE_RESPA_EXT 3 /* extended split (Sec. V): the outer kicks add the
+                                   * short-range pair part; inner F_0 = bonded only */
 
 /* Gradient parts (bounce_compute_gradient). */
 #define BOUNCE_GRAD_FULL 0  /* dE_pot/dq: all pairs within r_c + bonded     */
@@ -140,8 +142,8 @@ int bounce_get_state(bounce_ctx* ctx, double* q, double* v, int32_t where, void*
  * BOUNCE_BOUNCE or BOUNCE_BOUNCE_RESPA); the returned state is after the
  * last B half-kick.  With an SPME grid set, the reciprocal gradient is part
  * of the full gradient (BAOAB) or of F_0 (BOUNCE, Sec. V basic BOUNCE);
- * BOUNCE_BOUNCE_RESPA needs the grid, a step counter and n_steps that are
- * multiples of respa_m (else INVALID_ARG).  All
+ * BOUNCE_BOUNCE_RESPA needs the grid; both RESPA integrators need a step
+ * counter and n_steps that are multiples of respa_m (else INVALID_ARG).  All
  * work stays on the device; the call does not synchronise `stream` except
  * to report row overflows, which it checks once at the end.
  * Errors: STATE, LIST_OVERFLOW (a row exceeded max_neighbors; the state is

@@ -158,10 +158,16 @@ class OracleMD:
 
     def grad_short(self):
         """F_0: bonded + (1 - chi) pair part."""
+        return self.grad_short_pairs() + self.grad_bonded()
+
+    def grad_short_pairs(self):
         ii, jj = self.pairs()
         t = self.topo
-        return (pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "short")
-                + bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box))
+        return pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "short")
+
+    def grad_bonded(self):
+        t = self.topo
+        return bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box)
 
     def grad_full(self):
         ii, jj = self.pairs()
@@ -227,36 +233,49 @@ class OracleMD:
         self.kick(self.grad_full() + self.recip()[1], h)
         self.step_index += 1
 
-    def step_bounce(self, record=False, with_recip=True):
+    def _f0(self, with_recip, bonded_only):
+        g = self.grad_bonded() if bonded_only else self.grad_short()
+        return g + (self.recip()[1] if with_recip else 0.0)
+
+    def step_bounce(self, record=False, with_recip=True, bonded_only=False):
         """One BJAOAJB step; F_0 includes G_recip unless with_recip is False
-        (BOUNCE-RESPA moves it to the outer kicks)."""
+        (BOUNCE-RESPA moves it to the outer kicks) and holds only the bonded
+        terms when bonded_only (the extended split's inner steps)."""
         h = 0.5 * self.dt
         self.ensure_rows()
-        self.kick(self.grad_short() + (self.recip()[1] if with_recip else 0.0), h)
+        self.kick(self._f0(with_recip, bonded_only), h)
         r1 = self.jump(philox.STREAM_J1, record)
         self.drift(h)
         self.v = o_step(self.v, self.topo.mass, self.T, self.gamma, self.dt, self.seed, self.step_index)
         self.drift(h)
         self.ensure_rows()
         r2 = self.jump(philox.STREAM_J2, record)
-        self.kick(self.grad_short() + (self.recip()[1] if with_recip else 0.0), h)
+        self.kick(self._f0(with_recip, bonded_only), h)
         self.step_index += 1
         return (r1, r2) if record else None
 
-    def block_bounce_respa(self, m=2):
-        """One outer step Delta = m delta of BOUNCE-RESPA: kick with G_recip
-        over Delta/2, m BJAOAJB steps without it, kick again over Delta/2."""
+    def block_bounce_respa(self, m=2, extended=False):
+        """One outer step Delta = m delta of BOUNCE-RESPA: kick with G_out over
+        Delta/2, m BJAOAJB steps without it, kick again over Delta/2.
+        G_out = G_recip, or with extended = True (Sec. V, the bonded/non-bonded
+        split) G_out = short-range pair part + G_recip and the inner F_0 holds
+        only the bonded terms."""
         H = 0.5 * m * self.dt
-        self.kick(self.recip()[1], H)
+
+        def g_out():
+            self.ensure_rows()
+            return self.recip()[1] + (self.grad_short_pairs() if extended else 0.0)
+
+        self.kick(g_out(), H)
         for _ in range(m):
-            self.step_bounce(with_recip=False)
-        self.kick(self.recip()[1], H)
+            self.step_bounce(with_recip=False, bonded_only=extended)
+        self.kick(g_out(), H)
 
     def run(self, n, integrator="bounce", respa_m=2):
-        if integrator == "bounce_respa":
+        if integrator in ("bounce_respa", "bounce_respa_ext"):
             assert n % respa_m == 0
             for _ in range(n // respa_m):
-                self.block_bounce_respa(respa_m)
+                self.block_bounce_respa(respa_m, extended=integrator == "bounce_respa_ext")
             return
         for _ in range(n):
             if integrator == "bounce":

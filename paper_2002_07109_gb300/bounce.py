@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "NONFINITE", -4: "LIST_OVERFLOW", -5: "STATE", -6: "UNSUPPORTED"}
 HOST, DEVICE = 0, 1
-BAOAB, BOUNCE, BOUNCE_RESPA = 0, 1, 2
+BAOAB, BOUNCE, BOUNCE_RESPA, BOUNCE_RESPA_EXT = 0, 1, 2, 3
 GRAD_FULL, GRAD_SHORT, GRAD_LONG, GRAD_RECIP = 0, 1, 2, 3
 MAX_TYPES = 4
 

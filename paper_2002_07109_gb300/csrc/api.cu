@@ -66,7 +66,7 @@ struct bounce_ctx {
     size_t bitmap_bytes = 0;
     int ncell_alloc = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[3][8] = {};   // [integrator][RESPA phase of the chunk's first step]
+    cudaGraphExec_t graph[4][8] = {};   // [integrator][RESPA phase of the chunk's first step]
     long long cur_step = 0;              // host mirror of the device step counter
     bool has_pme = false;
     DevPme pme{};
@@ -451,31 +451,35 @@ int check_err(bounce_ctx* c, cudaStream_t st) {
 
 // What happens at one step boundary: whether the reciprocal gradient is
 // evaluated there and the time hr it kicks over (see k_step).
-void plan(const bounce_ctx* c, int integ, int variant, long long step, bool& pme, double& hr) {
+void plan(const bounce_ctx* c, int integ, int variant, long long step, bool& pme, double& hr, double& hout) {
     const double dt = c->cfg.dt_fs;
     const double hk = variant == 1 ? dt : 0.5 * dt;
     pme = false;
     hr = 0.0;
-    if (!c->has_pme) return;
-    if (integ != BOUNCE_BOUNCE_RESPA) {
-        pme = true;
-        hr = hk;
+    hout = 0.0;
+    if (integ == BOUNCE_BOUNCE_RESPA || integ == BOUNCE_BOUNCE_RESPA_EXT) {
+        const int m = c->cfg.respa_m;
+        if (step % m == 0) {
+            const double H = (variant == 1 ? 1.0 : 0.5) * m * dt;
+            pme = c->has_pme;
+            hr = c->has_pme ? H : 0.0;
+            if (integ == BOUNCE_BOUNCE_RESPA_EXT) hout = H;
+        }
         return;
     }
-    const int m = c->cfg.respa_m;
-    if (step % m == 0) {
+    if (c->has_pme) {
         pme = true;
-        hr = (variant == 1 ? 1.0 : 0.5) * m * dt;
+        hr = hk;
     }
 }
 
 void boundary(bounce_ctx* c, int integ, int variant, int off, long long step, cudaStream_t st) {
     bool pme;
-    double hr;
-    plan(c, integ, variant, step, pme, hr);
+    double hr, hout;
+    plan(c, integ, variant, step, pme, hr, hout);
     rebuild(c, off, false, st);
     if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
-    launch_step(c->ds, c->pp, integ, variant, off, hr, st);
+    launch_step(c->ds, c->pp, integ, variant, off, hr, hout, st);
 }
 
 // Graph of CHUNK body steps whose first step index is congruent to `phase`
@@ -495,11 +499,12 @@ int ensure_graph(bounce_ctx* c, int integ, int phase) {
 }
 
 int check_run_args(bounce_ctx* c, int64_t n_steps, int32_t integ) {
-    if (n_steps < 0 || (integ != BOUNCE_BAOAB && integ != BOUNCE_BOUNCE && integ != BOUNCE_BOUNCE_RESPA))
+    if (n_steps < 0 || integ < BOUNCE_BAOAB || integ > BOUNCE_BOUNCE_RESPA_EXT)
         return fail(c, BOUNCE_ERR_INVALID_ARG, "bad run arguments");
-    if (integ == BOUNCE_BOUNCE_RESPA) {
+    if (integ == BOUNCE_BOUNCE_RESPA || integ == BOUNCE_BOUNCE_RESPA_EXT) {
         const int m = c->cfg.respa_m;
-        if (!c->has_pme) return fail(c, BOUNCE_ERR_INVALID_ARG, "BOUNCE-RESPA needs an SPME grid");
+        if (integ == BOUNCE_BOUNCE_RESPA && !c->has_pme)
+            return fail(c, BOUNCE_ERR_INVALID_ARG, "BOUNCE-RESPA needs an SPME grid");
         if (n_steps % m != 0 || c->cur_step % m != 0)
             return fail(c, BOUNCE_ERR_INVALID_ARG, "BOUNCE-RESPA runs whole outer steps (multiples of respa_m)");
     }
@@ -839,12 +844,12 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
     const long long s0 = c->cur_step;
     auto timed = [&](int k, int variant, int off, long long step) {
         bool pme;
-        double hr;
-        plan(c, integ, variant, step, pme, hr);
+        double hr, hout;
+        plan(c, integ, variant, step, pme, hr, hout);
         rebuild(c, off, false, st);
         if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
         cudaEventRecord(ev[2 * k], st);
-        launch_step(c->ds, c->pp, integ, variant, off, hr, st);
+        launch_step(c->ds, c->pp, integ, variant, off, hr, hout, st);
         cudaEventRecord(ev[2 * k + 1], st);
     };
     timed(0, 0, 0, s0);
@@ -873,8 +878,8 @@ int64_t bounce_run_launch_count(const bounce_ctx* c, int64_t n, int32_t integ) {
     int64_t total = 2;               // step-counter updates after the head and the bodies
     for (int64_t k = 0; k <= n; ++k) {
         bool pme;
-        double hr;
-        plan(c, integ, k == 0 ? 0 : (k == n ? 2 : 1), c->cur_step + k, pme, hr);
+        double hr, hout;
+        plan(c, integ, k == 0 ? 0 : (k == n ? 2 : 1), c->cur_step + k, pme, hr, hout);
         total += per_boundary + (pme ? pme_launches : 0);
     }
     total += (n - 1) / CHUNK;        // one counter update per replayed graph chunk

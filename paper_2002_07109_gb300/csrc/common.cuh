@@ -360,7 +360,7 @@ __device__ __forceinline__ float3 bonded_grad(const Params& p, const DevSys& s, 
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
                     cudaStream_t st);
 void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
-                 cudaStream_t st);
+                 double hout, cudaStream_t st);
 void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st);
 void launch_pme_energy(const DevPme& m, int n, double* out, cudaStream_t st);
 void launch_gradient(const DevSys& s, const Params& p, int part, int cur, double* out, cudaStream_t st);

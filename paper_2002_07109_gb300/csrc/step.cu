@@ -212,15 +212,17 @@ __device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int c
 }
 
 // Warp-cooperative gradient of atom i: part 0 = full (long rows, chi = 1),
-// 1 = short (short rows, 1 - chi), 2 = long (long rows, chi); bonded terms
-// are added for parts 0 and 1.
+// 1 = short (short rows, 1 - chi), 2 = long (long rows, chi), 3 = short
+// pairs without bonded terms, 4 = bonded terms only; bonded terms are added
+// for parts 0, 1 and 4.
 __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i, int part, int& npairs) {
     const int lane = threadIdx.x & 31;
     const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
     const float qi = hi.w;
     const int ti = type_of(lo);
-    const int n = part == 1 ? s.nshort[i] : s.nlong[i];
-    const int* row = part == 1 ? s.srows + (size_t)i * s.caps : s.rows + (size_t)i * s.cap;
+    const bool shortrows = part == 1 || part == 3;
+    const int n = part == 4 ? 0 : (shortrows ? s.nshort[i] : s.nlong[i]);
+    const int* row = shortrows ? s.srows + (size_t)i * s.caps : s.rows + (size_t)i * s.cap;
     float gx = 0.f, gy = 0.f, gz = 0.f;
     for (int k = lane; k < n; k += 32) {
         const int j = row[k];
@@ -231,14 +233,14 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
             float w = pair_dW_over_r(p, r2, p.kcoul * qi * hj.w, ti * BOUNCE_MAXT + type_of(lj));
             if (part != 0) {
                 const float c = chi_of(p, sqrtf(r2));
-                w *= part == 1 ? 1.f - c : c;
+                w *= part == 2 ? c : 1.f - c;
             }
             gx += w * d.x;
             gy += w * d.y;
             gz += w * d.z;
         }
     }
-    if (part != 2) {
+    if (part == 0 || part == 1 || part == 4) {
         for (int t = s.bt_off[i] + lane; t < s.bt_off[i + 1]; t += 32) {
             const float3 g = bonded_grad(p, s, cur, i, s.bt_idx[t], s.bt_par[t]);
             gx += g.x;
@@ -254,9 +256,14 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
 // hr: time over which the reciprocal-space gradient kicks at this boundary
 // (0 without it; delta or delta/2 when it is part of F_0 or of BAOAB's full
 // gradient; Delta or Delta/2 at BOUNCE-RESPA block boundaries).
+// ext: the extended RESPA split -- F_0 holds only the bonded terms and the
+// short-range pair part kicks over hout (Delta or Delta/2 at block
+// boundaries, 0 elsewhere, where the pair sums are skipped).
 template <int BOUNCE>
-__global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int variant, int step_off, double hr) {
+__global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int variant, int step_off, double hr,
+                                                     int ext, double hout) {
     __shared__ float sG[BOUNCE_GROUP][3];
+    __shared__ float sGp[BOUNCE_GROUP][3];
     __shared__ double sV[BOUNCE_GROUP][3];
     __shared__ JumpSmem js;
     __shared__ unsigned long long sPairs;
@@ -278,13 +285,18 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
     __syncthreads();
     // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n
     for (int a = warp; a < na; a += NW) {
-        int np;
-        const float3 g = atom_gradient(s, p, cur, base + a, BOUNCE ? 1 : 0, np);
+        int np = 0, np2 = 0;
+        const float3 g = atom_gradient(s, p, cur, base + a, ext ? 4 : (BOUNCE ? 1 : 0), np);
+        float3 gp = make_float3(0.f, 0.f, 0.f);
+        if (ext && hout != 0.0) gp = atom_gradient(s, p, cur, base + a, 3, np2);
         if (lane == 0) {
             sG[a][0] = g.x;
             sG[a][1] = g.y;
             sG[a][2] = g.z;
-            atomicAdd(&sPairs, (unsigned long long)np);
+            sGp[a][0] = gp.x;
+            sGp[a][1] = gp.y;
+            sGp[a][2] = gp.z;
+            atomicAdd(&sPairs, (unsigned long long)(np + np2));
         }
     }
     if (warp == 0 && lane < na) {
@@ -325,6 +337,12 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
             vx -= cr * s.grecip[i];
             vy -= cr * s.grecip[s.n + i];
             vz -= cr * s.grecip[2 * (size_t)s.n + i];
+        }
+        if (ext && hout != 0.0) {
+            const double co = hout * s.kick[i];
+            vx -= co * (double)sGp[lane][0];
+            vy -= co * (double)sGp[lane][1];
+            vz -= co * (double)sGp[lane][2];
         }
         sV[lane][0] = vx;
         sV[lane][1] = vy;
@@ -459,10 +477,11 @@ __global__ void k_advance(DevSys s, long long by) { *const_cast<long long*>(s.st
 }  // namespace
 
 void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
-                 cudaStream_t st) {
+                 double hout, cudaStream_t st) {
     const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
-    if (integrator != 0) k_step<1><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr);
-    else k_step<0><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr);
+    const int ext = integrator == 3 ? 1 : 0;
+    if (integrator != 0) k_step<1><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr, ext, hout);
+    else k_step<0><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr, 0, 0.0);
 }
 
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,

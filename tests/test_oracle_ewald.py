@@ -111,3 +111,13 @@ def test_bounce_respa_reduces_to_baoab_and_is_second_order():
         dev.append(worst)
     assert 2.5 < dev[0] / dev[1] < 6.0, dev
     assert md.proposals == 0
+
+
+def test_extended_respa_with_one_inner_step_is_baoab():
+    """With m = 1 and no jump part, the extended split kicks the same total
+    gradient as BAOAB at the same positions."""
+    a = _respa_setup(0.25)
+    b = _respa_setup(0.25)
+    a.run(12, "baoab")
+    b.run(12, "bounce_respa_ext", respa_m=1)
+    assert np.allclose(a.q, b.q, rtol=0, atol=1e-10) and np.allclose(a.v, b.v, rtol=0, atol=1e-12)
