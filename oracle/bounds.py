@@ -65,8 +65,9 @@ def bound_table(charge, typ, n_types, lj_sigma, lj_eps, p):
     for a in range(T):
         for b in range(T):
             best = 0.0
-            for qa in set(ext[a]):
-                for qb in set(ext[b]):
+            charged = getattr(p, "coulomb_jumps", True)
+            for qa in (set(ext[a]) if charged else {0.0}):
+                for qb in (set(ext[b]) if charged else {0.0}):
                     best = max(best, sup_chi_dW(qa, qb, lj_sigma[a, b], lj_eps[a, b], p))
             L[a, b] = best * (1.0 + PAD)
     return L, L.max(axis=1)

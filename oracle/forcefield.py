@@ -42,6 +42,7 @@ class Params:
     lj_eps: np.ndarray = None
     pme_grid: tuple = None     # SPME grid (K1, K2, K3) for periodic Ewald, None = no reciprocal part
     pme_order: int = 5         # B-spline order
+    coulomb_jumps: bool = True # False: Coulomb wholly in F_0, only the LJ part is split (Sec. IV.A first example)
 
 
 def chi(r, r_on, r_off):
@@ -96,7 +97,17 @@ def displacement(qi, qj, box):
 def _uncut(p):
     """The same parameters without the cutoff (callers apply inside_cut)."""
     return Params(r_on=p.r_on, r_off=p.r_off, r_cut=math.inf, ewald_beta=p.ewald_beta, box=p.box,
-                  lj_sigma=p.lj_sigma, lj_eps=p.lj_eps, pme_grid=p.pme_grid, pme_order=p.pme_order)
+                  lj_sigma=p.lj_sigma, lj_eps=p.lj_eps, pme_grid=p.pme_grid, pme_order=p.pme_order,
+                  coulomb_jumps=p.coulomb_jumps)
+
+
+def split_dW(r, qa, qb, sig, eps, p):
+    """(part of W' switched by chi, part always in F_0): the whole W' and 0,
+    or the LJ part and the Coulomb part when Coulomb stays in F_0."""
+    if p.coulomb_jumps:
+        return pair_dW(r, qa, qb, sig, eps, p), 0.0
+    lj_only = pair_dW(r, 0.0, 0.0, sig, eps, p)
+    return lj_only, pair_dW(r, qa, qb, sig, eps, p) - lj_only
 
 
 def all_pairs(mol):
@@ -135,11 +146,15 @@ def pair_gradients(q, charge, typ, ii, jj, p, part="full"):
     if len(ii) == 0:
         return g
     d, r, qa, qb, sig, eps = pair_terms(q, charge, typ, ii, jj, p)
-    w = np.where(inside_cut(r2_of(d), p), pair_dW(r, qa, qb, sig, eps, _uncut(p)), 0.0)
+    inside = inside_cut(r2_of(d), p)
+    sw, fixed = split_dW(r, qa, qb, sig, eps, _uncut(p))
     if part == "short":
-        w = w * (1.0 - chi(r, p.r_on, p.r_off))
+        w = sw * (1.0 - chi(r, p.r_on, p.r_off)) + fixed
     elif part == "long":
-        w = w * chi(r, p.r_on, p.r_off)
+        w = sw * chi(r, p.r_on, p.r_off)
+    else:
+        w = sw + fixed
+    w = np.where(inside, w, 0.0)
     contrib = (w / r)[:, None] * d
     np.add.at(g, ii, contrib)
     return g
@@ -154,12 +169,16 @@ def pair_gradient_magnitudes(q, charge, typ, ii, jj, p, part="full"):
     if len(ii) == 0:
         return m
     d, r, qa, qb, sig, eps = pair_terms(q, charge, typ, ii, jj, p)
-    w = np.where(inside_cut(r2_of(d), p), pair_dW(r, qa, qb, sig, eps, _uncut(p)), 0.0)
+    inside = inside_cut(r2_of(d), p)
+    sw, fixed = split_dW(r, qa, qb, sig, eps, _uncut(p))
+    c = chi(r, p.r_on, p.r_off)
     if part == "short":
-        w = w * (1.0 - chi(r, p.r_on, p.r_off))
+        w = np.abs(sw * (1.0 - c)) + np.abs(fixed)
     elif part == "long":
-        w = w * chi(r, p.r_on, p.r_off)
-    np.add.at(m, ii, np.abs(w))
+        w = np.abs(sw * c)
+    else:
+        w = np.abs(sw) + np.abs(fixed)
+    np.add.at(m, ii, np.where(inside, w, 0.0))
     return m
 
 
@@ -169,11 +188,15 @@ def pair_gradient_one(qi, qj, qa, qb, sig, eps, p, part="long"):
     r2 = r2_of(d)
     r = np.sqrt(r2)
     with np.errstate(divide='ignore', invalid='ignore'):
-        w = np.where(inside_cut(r2, p), pair_dW(r, qa, qb, sig, eps, _uncut(p)), 0.0)
-    if part == "long":
-        w = w * chi(r, p.r_on, p.r_off)
-    elif part == "short":
-        w = w * (1.0 - chi(r, p.r_on, p.r_off))
+        sw, fixed = split_dW(r, qa, qb, sig, eps, _uncut(p))
+        c = chi(r, p.r_on, p.r_off)
+        if part == "long":
+            w = sw * c
+        elif part == "short":
+            w = sw * (1.0 - c) + fixed
+        else:
+            w = sw + fixed
+        w = np.where(inside_cut(r2, p), w, 0.0)
     with np.errstate(divide='ignore', invalid='ignore'):
         f = np.where(r > 0, w / r, 0.0)
     return f[..., None] * d
