@@ -65,6 +65,7 @@ class Clocks:
         self.index = index
         self.samples = []
         self.proc = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -72,19 +73,31 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_wait = time.perf_counter()
+            while not self.samples and time.perf_counter() - t_wait < 5.0:   # sampler running before timing
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def stop(self):
+        self.t1 = time.perf_counter()
+        t_wait = time.perf_counter()
+        while not any(t >= self.t1 for t, _ in self.samples) and time.perf_counter() - t_wait < 1.0:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.samples.append(parts)
+                self.samples.append((time.perf_counter(), parts))
 
     def __exit__(self, *a):
         if self.proc:
@@ -95,14 +108,20 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        if not self.samples:
+        """Samples taken while the timed region ran, plus the first one after it."""
+        t0 = self.t0 if self.t0 is not None else -math.inf
+        t1 = self.t1 if self.t1 is not None else math.inf
+        inside = [p for t, p in self.samples if t0 <= t <= t1]
+        after = [p for t, p in self.samples if t > t1][:1]
+        samples = inside + after
+        if not samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace('.', '', 1).isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace('.', '', 1).isdigit()]
+        sm = [float(s[1]) for s in samples if s[1].replace('.', '', 1).isdigit()]
+        mx = [float(s[2]) for s in samples if s[2].replace('.', '', 1).isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k].lower() == "active"})
+        reasons = sorted({names[k] for s in samples for k in range(4) if s[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(samples), "samples_inside_timed_region": len(inside)}
 
 
 def _dist():
@@ -180,6 +199,7 @@ def our_arm(args):
         with Clocks(local) as clk:
             _barrier(ws)
             torch.cuda.synchronize()
+            clk.start()
             torch.cuda.nvtx.range_push(name + "_timed")
             for k, w in enumerate(windows):
                 ctx.set_state(q0, v0, step=100000 * (k + 1))
@@ -195,6 +215,7 @@ def our_arm(args):
                 t_end.append(ctx.energies(stream=sh)["temperature"])
             torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
+            clk.stop()
             _barrier(ws)
         e = ctx.energies(stream=sh)
         # e2e through the public API with host buffers

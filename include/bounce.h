@@ -85,6 +85,9 @@ typedef struct bounce_config {
     int32_t pme_grid[3];   /* SPME grid K1 K2 K3; 0 = no reciprocal part (0)     */
     int32_t pme_order;     /* SPME B-spline order, 3..8 (5)                      */
     int32_t respa_m;       /* inner steps per BOUNCE-RESPA outer step (2)        */
+    int32_t jump_coulomb;  /* 1: Coulomb is split by chi like LJ (Sec. V droplets);
+                            * 0: Coulomb wholly in F_0, only LJ on jumps
+                            * (the first example of Sec. IV) (1)                 */
 } bounce_config;
 
 /* Energies and counters (bounce_get_energies). */

@@ -209,7 +209,8 @@ void compute_bounds(bounce_ctx* c, const std::vector<double>& sig, const std::ve
             const double qa[2] = {qmin[a], qmax[a]}, qb[2] = {qmin[b], qmax[b]};
             for (int x = 0; x < 2; ++x)
                 for (int y = 0; y < 2; ++y)
-                    best = std::max(best, sup_chi_dW(c->cfg, qa[x] * qb[y], sig[a * T + b], eps[a * T + b]));
+                    best = std::max(best, sup_chi_dW(c->cfg, c->cfg.jump_coulomb ? qa[x] * qb[y] : 0.0,
+                                                     sig[a * T + b], eps[a * T + b]));
             c->L[a * T + b] = best * (1.0 + 1e-6);
             c->Lstar[a] = std::max(c->Lstar[a], c->L[a * T + b]);
         }
@@ -350,7 +351,8 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     p.rlist2_lo = std::isfinite(rl2) ? (float)(rl2 * (1.0 - 1e-5)) : INFINITY;
     p.rlist2_hi = std::isfinite(rl2) ? (float)(rl2 * (1.0 + 1e-5)) : INFINITY;
     const double rs = g.r_off + g.skin;
-    p.rshort2 = (std::isfinite(rs) && rs < rl) ? (float)(rs * rs * (1.0 + 1e-4)) : INFINITY;
+    p.rshort2 = (g.jump_coulomb && std::isfinite(rs) && rs < rl) ? (float)(rs * rs * (1.0 + 1e-4)) : INFINITY;
+    p.coul_jump = g.jump_coulomb ? 1 : 0;
     for (int a = 0; a < BOUNCE_MAXT; ++a) {
         p.Lstar_d[a] = c->Lstar[a];
         p.Lstar_f[a] = (float)c->Lstar[a];
@@ -537,6 +539,9 @@ void bounce_config_default(bounce_config* cfg) {
     cfg->max_neighbors = 2048;
     cfg->max_short = 256;
     cfg->device = 0;
+    cfg->pme_order = 5;
+    cfg->respa_m = 2;
+    cfg->jump_coulomb = 1;
 }
 
 int bounce_create(bounce_ctx** out, const bounce_config* cfg) {
@@ -632,15 +637,20 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     const double rl = r_list(c->cfg);
     s.cap = std::isfinite(rl) ? c->cfg.max_neighbors : std::max(1, std::min(n - 1, c->cfg.max_neighbors));
     const double rs = c->cfg.r_off + c->cfg.skin;
-    s.caps = (std::isfinite(rs) && rs < rl) ? c->cfg.max_short : s.cap;
+    // Short rows exist only when they are a strict subset of the long rows;
+    // otherwise F_0 reads the long rows (rshort2 = +inf) and one slot is kept.
+    const bool distinct_short = c->cfg.jump_coulomb && std::isfinite(rs) && rs < rl;
+    s.caps = distinct_short ? c->cfg.max_short : 1;
     if ((r = dalloc(c, &s.vx, n)) || (r = dalloc(c, &s.vy, n)) || (r = dalloc(c, &s.vz, n)) ||
         (r = dalloc(c, &kick, n)) || (r = dalloc(c, &osd, n)) || (r = dalloc(c, &dtype, n)) ||
         (r = dalloc(c, &dmol, n)) || (r = dalloc(c, &boff, n + 1)) ||
         (r = dalloc(c, &bidx, c->bt_idx.size())) || (r = dalloc(c, &bpar, c->bt_par.size())) ||
         (r = dalloc(c, &s.nlong, n)) || (r = dalloc(c, &s.rows, (size_t)n * s.cap)) ||
-        (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, (size_t)n * s.caps)) ||
+        (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, distinct_short ? (size_t)n * s.caps : 1)) ||
         (r = dalloc(c, &s.refx, n)) || (r = dalloc(c, &s.refy, n)) || (r = dalloc(c, &s.refz, n)) ||
-        (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
+        (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.cell_phi, n)) || (r = dalloc(c, &s.cell_mol, n)) ||
+        (r = dalloc(c, &s.done_ctr, 2)) ||
+        (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
         (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 2048)))
         return r;
     s.kick = kick;
@@ -873,7 +883,9 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
 
 int64_t bounce_run_launch_count(const bounce_ctx* c, int64_t n, int32_t integ) {
     if (!c || n <= 0) return 0;
-    const int64_t per_boundary = 6;  // 5 gated row-rebuild kernels + the fused step kernel
+    // gated row-rebuild kernels (cells count + scan, scatter, rows + flag clear;
+    // one kernel for a batch of replicas) + the fused step kernel
+    const int64_t per_boundary = (c->ds.rep_of ? 1 : 3) + 1;
     const int64_t pme_launches = 10; // spread, load, 3 + 3 transforms, convolve, gather
     int64_t total = 2;               // step-counter updates after the head and the bodies
     for (int64_t k = 0; k <= n; ++k) {

@@ -58,6 +58,9 @@ struct DevSys {
     int* cell_start;
     int* cell_fill;
     int* cell_atoms;
+    float4* cell_phi;  // high position parts in cell order (coalesced candidate reads)
+    unsigned int* done_ctr;  // [2] finished-CTA counters of the rebuild kernels (zero between launches)
+    int* cell_mol;     // molecule ids in cell order
     int ncx, ncy, ncz;
     float ox, oy, oz;        // grid origin (droplets)
     float ihx, ihy, ihz;     // inverse cell edges
@@ -111,6 +114,7 @@ struct Params {
     double rlist2_d;             // exact FP64 threshold r_list^2 (+inf = all)
     float rshort2;               // short-row threshold
     float rcull;                 // r_list with a safety margin for cell culling (+inf = all)
+    int coul_jump;               // 1: Coulomb is switched by chi like LJ; 0: Coulomb wholly in F_0
     float Lstar_f[BOUNCE_MAXT];
     double Lstar_d[BOUNCE_MAXT];
     double beta;
@@ -254,6 +258,21 @@ __device__ __forceinline__ float pair_dW_over_r(const Params& p, float r2, float
         w -= (12.f * c12 * ir6 - 6.f * p.c6[tp]) * ir6 * ir2;
     }
     return w;
+}
+
+// W'/r split into the part switched by chi (sw) and the part that always
+// stays in F_0 (fixed): (all, 0), or (LJ, Coulomb) when Coulomb is kept out
+// of the jumps.
+__device__ __forceinline__ void pair_dW_split(const Params& p, float r2, float qq, int tp, float& sw, float& fixed) {
+    const float all = pair_dW_over_r(p, r2, qq, tp);
+    if (p.coul_jump) {
+        sw = all;
+        fixed = 0.f;
+    } else {
+        const float lj = pair_dW_over_r(p, r2, 0.f, tp);
+        sw = lj;
+        fixed = all - lj;
+    }
 }
 
 // Switching function chi(r) (quintic smoothstep on [r', r'']).

@@ -12,7 +12,10 @@
 // duplicate visits of a cell (grids narrower than 3 cells) are harmless.
 // Every kernel returns at once unless a rebuild is pending (the step kernel
 // raises the flag when an atom has moved more than skin/2 since the last
-// build), so the sequence can sit in a captured CUDA graph.
+// build), so the sequence can sit in a captured CUDA graph.  Three launches:
+// cell counts (the CTA finishing last scans them), scatter into cell order
+// (indices, positions and molecule ids), rows (the CTA finishing last clears
+// the flag).
 #include "common.cuh"
 
 namespace {
@@ -33,20 +36,24 @@ __device__ __forceinline__ void cell_of(const DevSys& s, const Params& p, float4
     }
 }
 
-__global__ void k_cells_count(DevSys s, Params p, int step_off, int force) {
-    if (!pending(s, force)) return;
-    int cur = (int)((*s.step_base + step_off) & 1);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
-        int cx, cy, cz;
-        cell_of(s, p, s.phi[cur][i], cx, cy, cz);
-        atomicAdd(&s.cell_count[(cz * s.ncy + cy) * s.ncx + cx], 1);
+// True in the one CTA of the grid that finishes last (all others have
+// completed their global writes); that CTA resets the counter to zero.
+__device__ bool last_cta(unsigned int* ctr) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+        if (last) atomicExch(ctr, 0u);
     }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
 }
 
 // Exclusive scan of the cell counts by one CTA; resets the counts to zero
 // for the next rebuild.
-__global__ void k_cells_scan(DevSys s, int force) {
-    if (!pending(s, force)) return;
+__device__ void cells_scan(const DevSys& s) {
     __shared__ int warp_tot[32];
     __shared__ int carry;
     int nc = s.ncx * s.ncy * s.ncz;
@@ -54,7 +61,7 @@ __global__ void k_cells_scan(DevSys s, int force) {
     __syncthreads();
     for (int base = 0; base < nc; base += blockDim.x) {
         int c = base + threadIdx.x;
-        int v = c < nc ? s.cell_count[c] : 0;
+        int v = c < nc ? __ldcg(&s.cell_count[c]) : 0;  // written by other CTAs' atomics
         int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
         int x = v;
         for (int o = 1; o < 32; o <<= 1) {
@@ -85,14 +92,29 @@ __global__ void k_cells_scan(DevSys s, int force) {
     if (threadIdx.x == 0) s.cell_start[nc] = carry;
 }
 
-__global__ void k_cells_scatter(DevSys s, Params p, int step_off, int force) {
+// Cell counts; the CTA that finishes last scans them.
+__global__ void k_cells_count(DevSys s, Params p, int step_off, int force) {
     if (!pending(s, force)) return;
     int cur = (int)((*s.step_base + step_off) & 1);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
         int cx, cy, cz;
         cell_of(s, p, s.phi[cur][i], cx, cy, cz);
+        atomicAdd(&s.cell_count[(cz * s.ncy + cy) * s.ncx + cx], 1);
+    }
+    if (last_cta(&s.done_ctr[0])) cells_scan(s);
+}
+
+__global__ void k_cells_scatter(DevSys s, Params p, int step_off, int force) {
+    if (!pending(s, force)) return;
+    int cur = (int)((*s.step_base + step_off) & 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        int cx, cy, cz;
+        const float4 hi = s.phi[cur][i];
+        cell_of(s, p, hi, cx, cy, cz);
         int pos = atomicAdd(&s.cell_fill[(cz * s.ncy + cy) * s.ncx + cx], 1);
         s.cell_atoms[pos] = i;
+        s.cell_phi[pos] = hi;
+        s.cell_mol[pos] = s.mol[i];
     }
 }
 
@@ -236,18 +258,17 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
             total_c += __shfl_sync(0xffffffffu, x, 31);
         }
         __syncwarp();
-        // 3) all lanes stride over the concatenated candidates
+        // 3) all lanes stride over the concatenated candidates (cell-ordered
+        //    copies: consecutive lanes read consecutive entries of a run)
+        int lo_r = 0;  // run of candidate t: rp[lo_r] <= t < rp[lo_r + 1]; t only grows
         for (int t = lane; t < total_c; t += 32) {
-            int lo_r = 0, hi_r = nr_tot - 1;
-            while (lo_r < hi_r) {  // last run with prefix <= t
-                const int mid = (lo_r + hi_r + 1) >> 1;
-                if (rp[mid] <= t) lo_r = mid;
-                else hi_r = mid - 1;
-            }
-            const int j = s.cell_atoms[rb[lo_r] + (t - rp[lo_r])];
-            if (j == i || s.mol[j] == mi) continue;
+            while (lo_r + 1 < nr_tot && rp[lo_r + 1] <= t) ++lo_r;
+            const int idx = rb[lo_r] + (t - rp[lo_r]);
+            const int j = s.cell_atoms[idx];
+            const int mj = s.cell_mol[idx];
             // screen with the high FP32 parts; the band covers their error
-            const float4 hj = s.phi[cur][j];
+            const float4 hj = s.cell_phi[idx];
+            if (j == i || mj == mi) continue;
             float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
             if (p.periodic) {
                 dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
@@ -289,10 +310,11 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
         }
         __syncwarp();
         // short rows: the members of the (ascending) row with r < r_off + skin
+        // (none when F_0 reads the long rows, rshort2 = +inf)
         const int nl = min(total, s.cap);
         int ns = 0;
         int* srow = s.srows + (size_t)i * s.caps;
-        for (int k0 = 0; k0 < nl; k0 += 32) {
+        for (int k0 = 0; p.rshort2 < INFINITY && k0 < nl; k0 += 32) {
             const int k = k0 + lane;
             bool keep = false;
             int j = 0;
@@ -317,6 +339,7 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
         }
         __syncwarp();
     }
+    if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
 }
 
 // Rows of a batch of independent all-pairs replicas: every atom of the same
@@ -344,7 +367,7 @@ __global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
         const int nl = min(total, s.cap);
         int ns = 0;
         int* srow = s.srows + (size_t)i * s.caps;
-        for (int k0 = 0; k0 < nl; k0 += 32) {
+        for (int k0 = 0; p.rshort2 < INFINITY && k0 < nl; k0 += 32) {
             const int k = k0 + lane;
             bool keep = false;
             int j = 0;
@@ -371,9 +394,8 @@ __global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
         }
         __syncwarp();
     }
+    if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
 }
-
-__global__ void k_rebuild_clear(DevSys s) { *s.rebuild = 0; }
 
 }  // namespace
 
@@ -383,18 +405,15 @@ void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, 
     if (s.rep_of) {
         const int wpb = 8;
         k_rows_batch<<<(s.n + wpb - 1) / wpb, wpb * 32, 0, st>>>(s, p, step_off, f);
-        k_rebuild_clear<<<1, 1, 0, st>>>(s);
         return;
     }
-    const int tb = 256;
+    const int tb = 1024;
     const int gb = (s.n + tb - 1) / tb;
     k_cells_count<<<gb, tb, 0, st>>>(s, p, step_off, f);
-    k_cells_scan<<<1, 1024, 0, st>>>(s, f);
     k_cells_scatter<<<gb, tb, 0, st>>>(s, p, step_off, f);
     const int words = (int)(bitmap_bytes / 4 / bitmap_warps);
     const int blocks = (s.n + bitmap_warps - 1) / bitmap_warps;
     k_rows<<<blocks, bitmap_warps * 32, bitmap_bytes, st>>>(s, p, step_off, f, words);
-    k_rebuild_clear<<<1, 1, 0, st>>>(s);
 }
 
 void nlist_set_smem_limit(size_t bytes) {

@@ -30,6 +30,8 @@
 namespace {
 
 constexpr int NW = 8;  // warps per CTA
+constexpr int GU = 2;  // row entries per lane in flight in the pair sums
+constexpr int FU = 2;  // proposals per thread in flight in the jump phase
 
 struct JumpSmem {
     double s[BOUNCE_GROUP];       // ||v|| (FP64)
@@ -42,7 +44,6 @@ struct JumpSmem {
     int nacc[BOUNCE_GROUP];
     int chp[BOUNCE_GROUP + 1];    // prefix of the chunk counts
     float inv[129];               // 1/k, k = 0..128 (round-to-nearest reciprocals)
-    int next;
     unsigned long long cnt[3];    // proposals, accepts, near ties
 };
 
@@ -127,117 +128,239 @@ __device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, in
     __syncthreads();
 }
 
-// Warp-cooperative jump chain of atom `a` (one half step).
-__device__ void jump_chain(const DevSys& s, const Params& p, JumpSmem& js, int cur, int a, int i, long long step,
-                           uint32_t stream) {
+// Proposals staged in shared memory per pass of the jump phase.
+constexpr int PC = 2048;
+
+struct PropSmem {
+    float gx[PC], gy[PC], gz[PC];  // F_iJ of each staged proposal (zero outside the cutoff)
+    uint32_t x1[PC], x2[PC];       // the words that make its uniform U
+    int P[BOUNCE_GROUP + 1];       // prefix of the proposal counts M of the CTA's atoms
+    float4 ahi[BOUNCE_GROUP], alo[BOUNCE_GROUP];  // the atoms' split positions at q_n
+    int an[BOUNCE_GROUP];          // their candidate-row lengths
+    int next;                      // next atom to take in the chain pass
+};
+
+// Flattened proposal g of the CTA -> (atom a, slot k = g - P[a] + 1).
+__device__ __forceinline__ int owner_of(const PropSmem& ps, int na, int g) {
+    int lo = 0, hi = na - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ps.P[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One jump half-step of the CTA's atoms after poisson_phase (Sec. IV.B).
+// Passes of up to PC proposals:
+// (1) every thread evaluates proposals of the flattened list (the atom's M
+//     proposals are contiguous and in slot order), FU at a time so their
+//     memory gathers overlap: partner J and U from Philox slot k, and
+//     F_iJ = chi W'_sw d / r at q_n, none of which depends on the velocity;
+// (2) warps walk the chains: 32 staged proposals at once are decided with the
+//     current velocity (accept iff U ||v|| L* < v . F), the first accepted one
+//     reflects it, and the rest are decided again with the new velocity --
+//     the decisions of the sequential loop.  Decisions are screened in FP32
+//     with a rigorous error margin and settled in FP64 inside it.
+// The chain velocity (js.vf), its increment (js.dv) and accept count persist
+// across passes in shared memory.  Called by all threads of the CTA.
+__device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropSmem& ps, int cur, int base, int na,
+                           long long step, uint32_t stream) {
     const int lane = threadIdx.x & 31;
-    const int M = js.M[a];
-    float vx = js.vf[a][0], vy = js.vf[a][1], vz = js.vf[a][2];
-    float dvx = 0.f, dvy = 0.f, dvz = 0.f;
-    int nacc = 0, near = 0;
-    if (M > 0) {
-        const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
-        const float qi = hi.w;
-        const int ti = type_of(lo);
-        const int n = s.nlong[i];
-        const int* row = s.rows + (size_t)i * s.cap;
-        const float sl = js.sl[a];
-        const double sp = js.s[a], Ls = p.Lstar_d[ti];
-        for (int kb = 0; kb < M; kb += 32) {
-            const int k = kb + lane + 1;
-            const bool act = k <= M;
-            float gx = 0.f, gy = 0.f, gz = 0.f, uf = 1.f;
-            uint32_t x1 = 0, x2 = 0;
-            if (act) {
-                const uint4 x = rng_atom(s, p, (uint32_t)k, i, step, stream);
-                const int J = (int)__umulhi(x.x, (uint32_t)n);
-                const int j = row[J];
-                const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
-                const float3 d = pair_disp(p, hi, lo, hj, lj);
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int a = 0; a < na; ++a) {
+            ps.P[a] = acc;
+            acc += js.M[a];
+        }
+        ps.P[na] = acc;
+        js.cnt[0] += (unsigned long long)acc;
+    }
+    if (threadIdx.x < na) {
+        const int a = threadIdx.x, i = base + a;
+        js.nacc[a] = 0;
+        js.dv[a][0] = js.dv[a][1] = js.dv[a][2] = 0.f;
+        ps.ahi[a] = s.phi[cur][i];
+        ps.alo[a] = s.plo[cur][i];
+        ps.an[a] = s.nlong[i];
+    }
+    __syncthreads();
+    const int tot = ps.P[na];
+    int near = 0;
+    for (int c0 = 0; c0 < tot; c0 += PC) {
+        const int cn = min(PC, tot - c0);
+        for (int t0 = threadIdx.x; t0 < cn; t0 += FU * NW * 32) {
+            int ow[FU], jj[FU];
+#pragma unroll
+            for (int u = 0; u < FU; ++u) {
+                const int t = t0 + u * NW * 32;
+                ow[u] = 0;
+                jj[u] = -1;
+                if (t < cn) {
+                    const int g = c0 + t;
+                    ow[u] = owner_of(ps, na, g);
+                    const uint4 x = rng_atom(s, p, (uint32_t)(g - ps.P[ow[u]] + 1), base + ow[u], step, stream);
+                    ps.x1[t] = x.y;
+                    ps.x2[t] = x.z;
+                    jj[u] = (int)__umulhi(x.x, (uint32_t)ps.an[ow[u]]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < FU; ++u)
+                if (jj[u] >= 0) jj[u] = s.rows[(size_t)(base + ow[u]) * s.cap + jj[u]];
+            float4 hj[FU], lj[FU];
+#pragma unroll
+            for (int u = 0; u < FU; ++u)
+                if (jj[u] >= 0) {
+                    hj[u] = s.phi[cur][jj[u]];
+                    lj[u] = s.plo[cur][jj[u]];
+                }
+#pragma unroll
+            for (int u = 0; u < FU; ++u) {
+                if (jj[u] < 0) continue;
+                const int t = t0 + u * NW * 32;
+                const float4 hi = ps.ahi[ow[u]], lo = ps.alo[ow[u]];
+                const float3 d = pair_disp(p, hi, lo, hj[u], lj[u]);
                 const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-                if (inside_cut(s, p, cur, i, j, r2)) {
-                    const float r = sqrtf(r2);
-                    const float w = chi_of(p, r) * pair_dW_over_r(p, r2, p.kcoul * qi * hj.w, ti * BOUNCE_MAXT + type_of(lj));
+                float gx = 0.f, gy = 0.f, gz = 0.f;
+                if (inside_cut(s, p, cur, base + ow[u], jj[u], r2)) {
+                    float sw, fixed;
+                    pair_dW_split(p, r2, p.kcoul * hi.w * hj[u].w, type_of(lo) * BOUNCE_MAXT + type_of(lj[u]), sw,
+                                  fixed);
+                    const float w = chi_of(p, sqrtf(r2)) * sw;
                     gx = w * d.x;
                     gy = w * d.y;
                     gz = w * d.z;
                 }
-                uf = u24(x.y);
-                x1 = x.y;
-                x2 = x.z;
-            }
-            int start = 0;
-            while (true) {
-                // decide with the current velocity: accept iff U ||v|| L* < v . F
-                const float af = vx * gx + vy * gy + vz * gz;
-                const float thr = uf * sl;
-                const float err = 4e-6f * (thr + fabsf(vx * gx) + fabsf(vy * gy) + fabsf(vz * gz)) + 2.4e-7f * sl;
-                int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
-                const bool live = act && lane >= start;
-                if (__any_sync(0xffffffffu, live && dec == 2)) {
-                    if (live && dec == 2) dec = exact_decision(vx, vy, vz, gx, gy, gz, x1, x2, sp, Ls);
-                }
-                const uint32_t acc = __ballot_sync(0xffffffffu, live && dec == 1);
-                const int f = acc ? __ffs(acc) - 1 : 32;
-                // near ties among the decisions that stand (lanes start..f)
-                const bool stands = live && lane <= f;
-                if (stands && fabsf(thr - af) < 1e-6f * sl) ++near;
-                if (!acc) break;
-                const float fx = __shfl_sync(0xffffffffu, gx, f), fy = __shfl_sync(0xffffffffu, gy, f),
-                            fz = __shfl_sync(0xffffffffu, gz, f);
-                const float aa = vx * fx + vy * fy + vz * fz;
-                const float ff = fx * fx + fy * fy + fz * fz;
-                const float coef = (aa + aa) / ff;
-                vx -= coef * fx;
-                vy -= coef * fy;
-                vz -= coef * fz;
-                dvx -= coef * fx;
-                dvy -= coef * fy;
-                dvz -= coef * fz;
-                ++nacc;
-                start = f + 1;
+                ps.gx[t] = gx;
+                ps.gy[t] = gy;
+                ps.gz[t] = gz;
             }
         }
+        if (threadIdx.x == 0) ps.next = 0;
+        __syncthreads();
+        for (;;) {
+            int a = 0;
+            if (lane == 0) a = atomicAdd(&ps.next, 1);
+            a = __shfl_sync(0xffffffffu, a, 0);
+            if (a >= na) break;
+            const int lo = max(ps.P[a], c0), hi = min(ps.P[a + 1], c0 + cn);
+            if (lo >= hi) continue;
+            const float sl = js.sl[a];
+            const double sp = js.s[a], Ls = p.Lstar_d[s.type[base + a]];
+            float vx = js.vf[a][0], vy = js.vf[a][1], vz = js.vf[a][2];
+            float dvx = js.dv[a][0], dvy = js.dv[a][1], dvz = js.dv[a][2];
+            int nacc = js.nacc[a];
+            for (int gb = lo; gb < hi; gb += 32) {
+                const int t = gb - c0 + lane;
+                const bool act = gb + lane < hi;
+                float gx = 0.f, gy = 0.f, gz = 0.f, uf = 1.f;
+                uint32_t x1 = 0, x2 = 0;
+                if (act) {
+                    gx = ps.gx[t];
+                    gy = ps.gy[t];
+                    gz = ps.gz[t];
+                    x1 = ps.x1[t];
+                    x2 = ps.x2[t];
+                    uf = u24(x1);
+                }
+                int start = 0;
+                while (true) {
+                    // decide with the current velocity: accept iff U ||v|| L* < v . F
+                    const float af = vx * gx + vy * gy + vz * gz;
+                    const float thr = uf * sl;
+                    const float err = 4e-6f * (thr + fabsf(vx * gx) + fabsf(vy * gy) + fabsf(vz * gz)) + 2.4e-7f * sl;
+                    int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
+                    const bool live = act && lane >= start;
+                    if (__any_sync(0xffffffffu, live && dec == 2)) {
+                        if (live && dec == 2) dec = exact_decision(vx, vy, vz, gx, gy, gz, x1, x2, sp, Ls);
+                    }
+                    const uint32_t acc = __ballot_sync(0xffffffffu, live && dec == 1);
+                    const int f = acc ? __ffs(acc) - 1 : 32;
+                    // near ties among the decisions that stand (lanes start..f)
+                    if (live && lane <= f && fabsf(thr - af) < 1e-6f * sl) ++near;
+                    if (!acc) break;
+                    const float fx = __shfl_sync(0xffffffffu, gx, f), fy = __shfl_sync(0xffffffffu, gy, f),
+                                fz = __shfl_sync(0xffffffffu, gz, f);
+                    const float aa = vx * fx + vy * fy + vz * fz;
+                    const float ff = fx * fx + fy * fy + fz * fz;
+                    const float coef = (aa + aa) / ff;
+                    vx -= coef * fx;
+                    vy -= coef * fy;
+                    vz -= coef * fz;
+                    dvx -= coef * fx;
+                    dvy -= coef * fy;
+                    dvz -= coef * fz;
+                    ++nacc;
+                    start = f + 1;
+                }
+            }
+            if (lane == 0) {
+                js.vf[a][0] = vx;
+                js.vf[a][1] = vy;
+                js.vf[a][2] = vz;
+                js.dv[a][0] = dvx;
+                js.dv[a][1] = dvy;
+                js.dv[a][2] = dvz;
+                js.nacc[a] = nacc;
+            }
+        }
+        __syncthreads();
     }
     near = warp_sum_i(near);
-    if (lane == 0) {
-        js.dv[a][0] = dvx;
-        js.dv[a][1] = dvy;
-        js.dv[a][2] = dvz;
-        js.nacc[a] = nacc;
-        atomicAdd(&js.cnt[0], (unsigned long long)M);
-        atomicAdd(&js.cnt[1], (unsigned long long)nacc);
-        atomicAdd(&js.cnt[2], (unsigned long long)near);
+    if (lane == 0 && near) atomicAdd(&js.cnt[2], (unsigned long long)near);
+    if (threadIdx.x == 0) {
+        unsigned long long A = 0;
+        for (int a = 0; a < na; ++a) A += (unsigned long long)js.nacc[a];
+        js.cnt[1] += A;
     }
+    __syncthreads();
 }
 
 // Warp-cooperative gradient of atom i: part 0 = full (long rows, chi = 1),
 // 1 = short (short rows, 1 - chi), 2 = long (long rows, chi), 3 = short
-// pairs without bonded terms, 4 = bonded terms only; bonded terms are added
-// for parts 0, 1 and 4.
+// pairs without bonded terms, 4 = bonded terms only, 5 = full pairs without
+// bonded terms; bonded terms are added for parts 0, 1 and 4.
 __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i, int part, int& npairs) {
     const int lane = threadIdx.x & 31;
     const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
     const float qi = hi.w;
     const int ti = type_of(lo);
-    const bool shortrows = part == 1 || part == 3;
+    const bool shortrows = (part == 1 || part == 3) && p.rshort2 < INFINITY;
     const int n = part == 4 ? 0 : (shortrows ? s.nshort[i] : s.nlong[i]);
     const int* row = shortrows ? s.srows + (size_t)i * s.caps : s.rows + (size_t)i * s.cap;
     float gx = 0.f, gy = 0.f, gz = 0.f;
-    for (int k = lane; k < n; k += 32) {
-        const int j = row[k];
-        const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
-        const float3 d = pair_disp(p, hi, lo, hj, lj);
-        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-        if (inside_cut(s, p, cur, i, j, r2)) {
-            float w = pair_dW_over_r(p, r2, p.kcoul * qi * hj.w, ti * BOUNCE_MAXT + type_of(lj));
-            if (part != 0) {
-                const float c = chi_of(p, sqrtf(r2));
-                w *= part == 2 ? c : 1.f - c;
+    // GU row entries per lane per pass: their index and position loads are
+    // issued back to back before any is used; each lane still adds its pairs
+    // in row order.
+    for (int k0 = lane; k0 < n; k0 += GU * 32) {
+        int j[GU];
+        float4 hj[GU], lj[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) j[u] = k0 + 32 * u < n ? row[k0 + 32 * u] : -1;
+#pragma unroll
+        for (int u = 0; u < GU; ++u)
+            if (j[u] >= 0) {
+                hj[u] = s.phi[cur][j[u]];
+                lj[u] = s.plo[cur][j[u]];
             }
-            gx += w * d.x;
-            gy += w * d.y;
-            gz += w * d.z;
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            if (j[u] < 0) continue;
+            const float3 d = pair_disp(p, hi, lo, hj[u], lj[u]);
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            if (inside_cut(s, p, cur, i, j[u], r2)) {
+                float sw, fixed;
+                pair_dW_split(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]), sw, fixed);
+                float w = sw + fixed;
+                if (part != 0 && part != 5) {
+                    const float c = chi_of(p, sqrtf(r2));
+                    w = part == 2 ? sw * c : sw * (1.f - c) + fixed;
+                }
+                gx += w * d.x;
+                gy += w * d.y;
+                gz += w * d.z;
+            }
         }
     }
     if (part == 0 || part == 1 || part == 4) {
@@ -260,12 +383,14 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
 // short-range pair part kicks over hout (Delta or Delta/2 at block
 // boundaries, 0 elsewhere, where the pair sums are skipped).
 template <int BOUNCE>
-__global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int variant, int step_off, double hr,
+__global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int variant, int step_off, double hr,
                                                      int ext, double hout) {
     __shared__ float sG[BOUNCE_GROUP][3];
     __shared__ float sGp[BOUNCE_GROUP][3];
     __shared__ double sV[BOUNCE_GROUP][3];
     __shared__ JumpSmem js;
+    __shared__ PropSmem ps;
+    __shared__ int sBoff[BOUNCE_GROUP + 1];
     __shared__ unsigned long long sPairs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = blockIdx.x * BOUNCE_GROUP;
@@ -282,12 +407,13 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
     }
     if (BOUNCE)
         for (int k = threadIdx.x; k < 129; k += blockDim.x) js.inv[k] = k ? __frcp_rn((float)k) : 0.f;
+    if (threadIdx.x <= na) sBoff[threadIdx.x] = s.bt_off[base + threadIdx.x];
     __syncthreads();
-    // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n
+    // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n: pair sums, warps over atoms
     for (int a = warp; a < na; a += NW) {
         int np = 0, np2 = 0;
-        const float3 g = atom_gradient(s, p, cur, base + a, ext ? 4 : (BOUNCE ? 1 : 0), np);
-        float3 gp = make_float3(0.f, 0.f, 0.f);
+        float3 g = make_float3(0.f, 0.f, 0.f), gp = g;
+        if (!ext) g = atom_gradient(s, p, cur, base + a, BOUNCE ? 3 : 5, np);
         if (ext && hout != 0.0) gp = atom_gradient(s, p, cur, base + a, 3, np2);
         if (lane == 0) {
             sG[a][0] = g.x;
@@ -299,6 +425,40 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
             atomicAdd(&sPairs, (unsigned long long)(np + np2));
         }
     }
+    // bonded terms: one term per thread into the staging area, then each atom
+    // adds its own terms in list order (lane a of warp 0)
+    {
+        const int e0 = sBoff[0], e1 = sBoff[na];
+        for (int c = e0; c < e1; c += NW * 32) {
+            const int e = c + threadIdx.x;
+            if (e < e1) {
+                int lo = 0, hi = na - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sBoff[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                const float3 g = bonded_grad(p, s, cur, base + lo, s.bt_idx[e], s.bt_par[e]);
+                ps.gx[threadIdx.x] = g.x;
+                ps.gy[threadIdx.x] = g.y;
+                ps.gz[threadIdx.x] = g.z;
+            }
+            __syncthreads();
+            if (warp == 0 && lane < na) {
+                const int t0 = max(sBoff[lane], c), t1 = min(sBoff[lane + 1], c + NW * 32);
+                float bx = 0.f, by = 0.f, bz = 0.f;
+                for (int t = t0; t < t1; ++t) {
+                    bx += ps.gx[t - c];
+                    by += ps.gy[t - c];
+                    bz += ps.gz[t - c];
+                }
+                sG[lane][0] += bx;
+                sG[lane][1] += by;
+                sG[lane][2] += bz;
+            }
+            __syncthreads();
+        }
+    }
     if (warp == 0 && lane < na) {
         const int i = base + lane;
         const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
@@ -307,18 +467,10 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
         sV[lane][2] = vz;
         if (do_j2) jump_prep(s, p, js, lane, i, vx, vy, vz);
     }
-    if (threadIdx.x == 0) js.next = 0;
     __syncthreads();
     if (do_j2) {
         poisson_phase(s, p, js, base, na, step - 1, BOUNCE_STREAM_J2);
-        for (;;) {
-            int a = 0;
-            if (lane == 0) a = atomicAdd(&js.next, 1);
-            a = __shfl_sync(0xffffffffu, a, 0);
-            if (a >= na) break;
-            jump_chain(s, p, js, cur, a, base + a, step - 1, BOUNCE_STREAM_J2);
-        }
-        __syncthreads();
+        jump_phase(s, p, js, ps, cur, base, na, step - 1, BOUNCE_STREAM_J2);
     }
     if (warp == 0 && lane < na) {
         const int i = base + lane;
@@ -349,18 +501,10 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
         sV[lane][2] = vz;
         if (do_j1) jump_prep(s, p, js, lane, i, vx, vy, vz);
     }
-    if (threadIdx.x == 0) js.next = 0;
     __syncthreads();
     if (do_j1) {
         poisson_phase(s, p, js, base, na, step, BOUNCE_STREAM_J1);
-        for (;;) {
-            int a = 0;
-            if (lane == 0) a = atomicAdd(&js.next, 1);
-            a = __shfl_sync(0xffffffffu, a, 0);
-            if (a >= na) break;
-            jump_chain(s, p, js, cur, a, base + a, step, BOUNCE_STREAM_J1);
-        }
-        __syncthreads();
+        jump_phase(s, p, js, ps, cur, base, na, step, BOUNCE_STREAM_J1);
     }
     if (warp == 0 && lane < na) {
         const int i = base + lane;
@@ -422,12 +566,12 @@ __global__ void __launch_bounds__(NW * 32, 4) k_step(DevSys s, Params p, int var
 __global__ void __launch_bounds__(NW * 32) k_jump_half(DevSys s, Params p, int cur, long long step, int stream_id,
                                                       int* Mout, int* Aout) {
     __shared__ JumpSmem js;
+    __shared__ PropSmem ps;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = blockIdx.x * BOUNCE_GROUP;
     const int na = min(BOUNCE_GROUP, s.n - base);
     if (threadIdx.x == 0) {
         js.cnt[0] = js.cnt[1] = js.cnt[2] = 0ull;
-        js.next = 0;
     }
     for (int k = threadIdx.x; k < 129; k += blockDim.x) js.inv[k] = k ? __frcp_rn((float)k) : 0.f;
     if (warp == 0 && lane < na) {
@@ -436,14 +580,7 @@ __global__ void __launch_bounds__(NW * 32) k_jump_half(DevSys s, Params p, int c
     }
     __syncthreads();
     poisson_phase(s, p, js, base, na, step, (uint32_t)stream_id);
-    for (;;) {
-        int a = 0;
-        if (lane == 0) a = atomicAdd(&js.next, 1);
-        a = __shfl_sync(0xffffffffu, a, 0);
-        if (a >= na) break;
-        jump_chain(s, p, js, cur, a, base + a, step, (uint32_t)stream_id);
-    }
-    __syncthreads();
+    jump_phase(s, p, js, ps, cur, base, na, step, (uint32_t)stream_id);
     if (warp == 0 && lane < na) {
         const int i = base + lane;
         s.vx[i] += (double)js.dv[lane][0];
