@@ -12,6 +12,14 @@ Method: a dense grid of 10^6 points on [r', R] (R = r_c, or r'' + 60 A with no
 cutoff), then a bounded scalar refinement around the best grid point, then a
 relative pad of 1e-6 so that round-off never makes the bound too small.
 
+Per-type-pair bounds (Sec. V: the bound L may depend on the types of the two
+particles).  pair_weights turns the table into the two-stage partner choice:
+the type b of the partner is drawn with probability proportional to
+n_ib Lq_ab, then the partner uniformly among the n_ib candidates of that
+type.  Lq_ab = ceil(2^16 L_ab / L*_a) + 1 is an integer weight (0 where
+L_ab = 0) so that the choice is exact integer arithmetic, and the bound it
+stands for, Lt_ab = (Lq_ab L*_a) 2^-16 >= L_ab, is used in the acceptance.
+
 Pins: closed form k |q_a q_b| / r''^2 for an indicator chi and bare Coulomb,
 and a brute-force check that lambda <= lambda* on random pairs
 (tests/test_oracle_bounds.py).
@@ -71,3 +79,21 @@ def bound_table(charge, typ, n_types, lj_sigma, lj_eps, p):
                     best = max(best, sup_chi_dW(qa, qb, lj_sigma[a, b], lj_eps[a, b], p))
             L[a, b] = best * (1.0 + PAD)
     return L, L.max(axis=1)
+
+
+QBITS = 16
+
+
+def pair_weights(L, Lstar):
+    """(Lq, Lt): integer weights of the two-stage partner choice and the
+    bounds they stand for, Lt_ab = (Lq_ab L*_a) 2^-16 >= L_ab."""
+    L = np.asarray(L, dtype=np.float64)
+    T = L.shape[0]
+    Lq = np.zeros((T, T), dtype=np.int64)
+    Lt = np.zeros((T, T))
+    for a in range(T):
+        for b in range(T):
+            if L[a, b] > 0.0:
+                Lq[a, b] = int(math.ceil(L[a, b] / Lstar[a] * float(1 << QBITS))) + 1
+                Lt[a, b] = (float(Lq[a, b]) * Lstar[a]) * 2.0 ** -QBITS
+    return Lq, Lt

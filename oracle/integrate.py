@@ -17,7 +17,9 @@ test is U ||v_i|| L < v_i . F_ij (beta cancels).
 Readings of the paper used here (all listed in the design notes):
   * F_0 = bonded + (1 - chi) part of every pair term; F_ij = chi W' d/r.
   * friction coefficient is mass-independent: c1 = exp(-gamma delta).
-  * L is the per-type row maximum L*_{t_i} (oracle.bounds).
+  * L is the per-type row maximum L*_{t_i} (oracle.bounds), or, with
+    per-type-pair bounds, Lt_{t_i t_j} with the two-stage partner choice
+    (jump_half, oracle.bounds.pair_weights).
   * Random numbers: Philox4x32-10 keyed by the run seed with counter
     (slot, atom, step, stream); stream 1 for the J after the first B,
     stream 2 for the J before the last B, stream 0 for O.  Proposal k
@@ -69,19 +71,64 @@ def o_step(v, mass, temperature, gamma, dt, seed, step, atoms=None):
     return c1 * v + sd[:, None] * g
 
 
-def jump_half(q, v, row_list, topo, p, Lstar_row, beta, dt, seed, step, stream, record=False):
+def typed_rows(row_list, typ, n_types):
+    """Candidate rows regrouped by partner type: segment b holds the members of
+    type b in ascending index, segments in increasing b; and the counts n_ib."""
+    typ = np.asarray(typ)
+    out = []
+    counts = np.zeros((len(row_list), n_types), dtype=np.int64)
+    for i, r in enumerate(row_list):
+        r = np.asarray(r, dtype=np.int64)
+        segs = [r[typ[r] == b] for b in range(n_types)]
+        out.append(np.concatenate(segs) if segs else r)
+        counts[i] = [len(x) for x in segs]
+    return out, counts
+
+
+def two_stage_pick(t, C, S, Lq_a):
+    """Position in the type-grouped row of the candidate that weight unit t
+    (0 <= t < W) falls on: segment b with C_b <= t < C_{b+1}, then
+    (t - C_b) // Lq_ab within it.  C: (m, T+1) cumulative weights, S: (m, T+1)
+    segment starts, Lq_a: (m, T) weights of the atoms' types."""
+    t = np.asarray(t, dtype=np.int64)
+    b = (C[:, 1:] <= t[:, None]).sum(1)
+    rows = np.arange(len(t))
+    return S[rows, b] + (t - C[rows, b]) // Lq_a[rows, b]
+
+
+def jump_half(q, v, row_list, topo, p, Lstar_row, beta, dt, seed, step, stream, record=False, pair_bounds=None):
     """The jump step J over a half step dt/2 for every atom (Sec. IV.B).
 
+    pair_bounds = None: one bound L*_{t_i} for every candidate, J uniform over
+    the row.  pair_bounds = (Lq, Lt) (oracle.bounds.pair_weights): two-stage
+    choice over the type-grouped row (typed_rows) -- the weight of a candidate
+    of type b is Lq_ab, the Poisson mean is beta ||v|| (delta/2) L*_a W_i 2^-16
+    with W_i = sum_b n_ib Lq_ab, and the acceptance bound is Lt_ab.
+    Proposal k: t = floor(x0 W_i / 2^32); segment b with C_b <= t < C_{b+1}
+    (C_b = sum_{c<b} n_ic Lq_ac); J = (start of segment b) + (t - C_b) // Lq_ab.
+
     Returns the new velocities and, if record, a dict of per-proposal arrays
-    (atom, k, J, j, U, ratio = max(0, v.F)/(||v|| L*), accepted)."""
+    (atom, k, J, j, U, ratio = max(0, v.F)/(||v|| L), accepted)."""
     n = q.shape[0]
     v = np.array(v, dtype=np.float64, copy=True)
+    if pair_bounds is not None:
+        Lq, Lt = pair_bounds
+        T = Lq.shape[0]
+        row_list, counts = typed_rows(row_list, topo.type, T)
+        wq = counts * Lq[topo.type]                      # n_ib Lq_ab
+        W = wq.sum(1)
+        C = np.concatenate([np.zeros((n, 1), np.int64), np.cumsum(wq, 1)], 1)
+        S = np.concatenate([np.zeros((n, 1), np.int64), np.cumsum(counts, 1)], 1)
+        assert np.all(W < 2 ** 32)
     nrow = np.array([len(r) for r in row_list], dtype=np.int64)
     offs = np.concatenate([[0], np.cumsum(nrow)])
     flat = np.concatenate(row_list) if n else np.zeros(0, np.int64)
     s = np.sqrt((v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1]) + v[:, 2] * v[:, 2])
     Ls = Lstar_row[topo.type]
-    mu = ((((beta * s) * Ls) * nrow) * dt) * 0.5
+    if pair_bounds is None:
+        mu = ((((beta * s) * Ls) * nrow) * dt) * 0.5
+    else:
+        mu = ((((beta * s) * Ls) * (W * 2.0 ** -16)) * dt) * 0.5
     atoms = np.arange(n)
     M = poisson.counts(mu, atoms, seed, step, stream)
     rec = {k: [] for k in ('atom', 'k', 'J', 'j', 'U', 'ratio', 'accepted')} if record else None
@@ -89,19 +136,23 @@ def jump_half(q, v, row_list, topo, p, Lstar_row, beta, dt, seed, step, stream, 
     for k in range(1, kmax + 1):
         act = np.nonzero(M >= k)[0]
         x = philox.draw(seed, k, act, step, stream)
-        J = philox.index_below(x[0], nrow[act])
+        if pair_bounds is None:
+            J = philox.index_below(x[0], nrow[act])
+        else:
+            J = two_stage_pick(philox.index_below(x[0], W[act]), C[act], S[act], Lq[topo.type[act]])
         j = flat[offs[act] + J]
         U = philox.u53(x[1], x[2])
         ti, tj = topo.type[act], topo.type[j]
+        Lb = Ls[act] if pair_bounds is None else Lt[ti, tj]
         G = pair_gradient_one(q[act], q[j], topo.charge[act], topo.charge[j],
                               p.lj_sigma[ti, tj], p.lj_eps[ti, tj], p, part="long")
         va = v[act]
         a = (va[:, 0] * G[:, 0] + va[:, 1] * G[:, 1]) + va[:, 2] * G[:, 2]
-        thr = (U * s[act]) * Ls[act]
+        thr = (U * s[act]) * Lb
         acc = thr < a
         if record:
             with np.errstate(divide='ignore', invalid='ignore'):
-                ratio = np.where(s[act] > 0, np.maximum(a, 0.0) / (s[act] * Ls[act]), 0.0)
+                ratio = np.where(s[act] > 0, np.maximum(a, 0.0) / (s[act] * Lb), 0.0)
             for key, val in (('atom', act), ('k', np.full(len(act), k)), ('J', J), ('j', j), ('U', U),
                              ('ratio', ratio), ('accepted', acc)):
                 rec[key].append(val)
@@ -122,7 +173,8 @@ def jump_half(q, v, row_list, topo, p, Lstar_row, beta, dt, seed, step, stream, 
 class OracleMD:
     """Plain FP64 BAOAB / BOUNCE integrator over one system."""
 
-    def __init__(self, q, v, topo, p, *, dt=1.0, gamma=0.001, temperature=300.0, seed=0, skin=1.0, step=0):
+    def __init__(self, q, v, topo, p, *, dt=1.0, gamma=0.001, temperature=300.0, seed=0, skin=1.0, step=0,
+                 pair_bounds=False):
         self.q = np.array(q, dtype=np.float64)
         self.v = np.array(v, dtype=np.float64)
         self.topo = topo
@@ -139,9 +191,10 @@ class OracleMD:
         self.rebuilds = 0
         self.proposals = 0
         self.accepts = 0
-        from .bounds import bound_table
+        from .bounds import bound_table, pair_weights
         T = int(max(topo.type.max() + 1, p.lj_sigma.shape[0]))
         self.L, self.Lstar = bound_table(topo.charge, topo.type, T, p.lj_sigma, p.lj_eps, p)
+        self.pair_bounds = pair_weights(self.L, self.Lstar) if pair_bounds else None
 
     @property
     def r_list(self):
@@ -217,7 +270,8 @@ class OracleMD:
 
     def jump(self, stream, record=False):
         self.v, rec = jump_half(self.q, self.v, self.row_list, self.topo, self.p, self.Lstar, self.beta,
-                                self.dt, self.seed, self.step_index, stream, record=True)
+                                self.dt, self.seed, self.step_index, stream, record=True,
+                                pair_bounds=self.pair_bounds)
         self.proposals += int(rec['M'].sum())
         self.accepts += int(rec['accepted'].sum()) if len(rec['accepted']) else 0
         return rec if record else None
