@@ -693,8 +693,9 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     int dev = c->cfg.device, optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t words = (size_t)(n + 31) / 32;
-    // per warp: the bitmap (rounded to 16 bytes) and 3 x 128 ints of cell-row runs
-    const size_t per_warp = (words * 4 + 15) / 16 * 16 + 3 * 128 * 4;
+    // per warp: the long- and short-row bitmaps (each rounded to 16 bytes) and
+    // 3 x 128 ints of cell-row runs
+    const size_t per_warp = 2 * ((words * 4 + 15) / 16 * 16) + 3 * 128 * 4;
     if (per_warp > (size_t)optin) return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for the row builder bitmap");
     c->bitmap_warps = (int)std::min<size_t>(8, (size_t)optin / per_warp);
     c->bitmap_bytes = per_warp * c->bitmap_warps;

@@ -3,13 +3,14 @@
 // interacting with i).  Row of atom i: every atom j of another molecule with
 // r_ij^2 < r_list^2 (FP64, minimum image), in ascending j.
 //
-// GPU design: a cell grid of edge > r_list (counting sort: count, scan,
-// scatter), then one warp per atom scans the 27 neighbour cells, screens each
-// candidate in FP32 from the split positions and settles the few candidates
-// near r_list exactly in FP64.  Accepted candidates set a bit in a per-warp
-// bitmap over all atom indices in shared memory; reading the bitmap back in
-// word order yields the row already in ascending order (no sort), and
-// duplicate visits of a cell (grids narrower than 3 cells) are harmless.
+// GPU design: a cell grid of edge >= r_list / 3 (counting sort: count, scan,
+// scatter), then one warp per atom scans the cells that meet its r_list
+// sphere, screens each candidate in FP32 from the high position parts and
+// settles the few candidates near r_list exactly in FP64.  Accepted
+// candidates set a bit in a per-warp bitmap over all atom indices in shared
+// memory (a second bitmap marks the short-row members, r < r_off + skin);
+// reading a bitmap back in word order yields the row already in ascending
+// order (no sort), and duplicate visits of a cell are harmless.
 // Every kernel returns at once unless a rebuild is pending (the step kernel
 // raises the flag when an atom has moved more than skin/2 since the last
 // build), so the sequence can sit in a captured CUDA graph.  Three launches:
@@ -134,18 +135,53 @@ __device__ __forceinline__ bool image_ambiguous(const Params& p, float4 hi, floa
     return fabsf(fx - 0.5f) < 1e-4f || fabsf(fy - 0.5f) < 1e-4f || fabsf(fz - 0.5f) < 1e-4f;
 }
 
+// Writes the set bits of a warp's bitmap, in ascending order, as indices to
+// row[0 .. cap) and returns their count (which may exceed cap).  Passes of 32
+// words: a prefix of their popcounts, then the warp expands the non-empty
+// words one at a time, lane b writing bit b, so neighbouring indices (dense
+// words) cost one step per word and the stores are contiguous.
+__device__ int expand_bitmap(const uint32_t* bm, int nwords, int* row, int cap) {
+    const int lane = threadIdx.x & 31;
+    int total = 0;
+    for (int w0 = 0; w0 < nwords; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t bits = w < nwords ? bm[w] : 0u;
+        const int c = __popc(bits);
+        int x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int excl = total + x - c;
+        uint32_t nz = __ballot_sync(0xffffffffu, bits != 0u);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const uint32_t b = __shfl_sync(0xffffffffu, bits, src);
+            const int at = __shfl_sync(0xffffffffu, excl, src);
+            if (b & (1u << lane)) {
+                const int pos = at + __popc(b & ((1u << lane) - 1u));
+                if (pos < cap) row[pos] = ((w0 + src) << 5) + lane;
+            }
+        }
+        total += __shfl_sync(0xffffffffu, x, 31);
+    }
+    return total;
+}
+
 __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_per_warp) {
     if (!pending(s, force)) return;
     extern __shared__ uint32_t smem_bm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int nwords = (s.n + 31) >> 5;
-    uint32_t* bm = smem_bm + (size_t)warp * words_per_warp;
+    uint32_t* bm = smem_bm + (size_t)warp * words_per_warp;  // long-row bitmap
+    uint32_t* bs = bm + ((nwords + 3) & ~3);                   // short-row bitmap
     const int cur = (int)((*s.step_base + step_off) & 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
     for (int i = blockIdx.x * wpb + warp; i < s.n; i += gridDim.x * wpb) {
-        for (int w = lane; w < nwords; w += 32) bm[w] = 0u;
+        for (int w = lane; w < nwords; w += 32) bm[w] = bs[w] = 0u;
         __syncwarp();
-        const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
+        const float4 hi = s.phi[cur][i];
         const int mi = s.mol[i];
         // unclamped cell coordinates of atom i
         const float fx = p.periodic ? hi.x * s.ihx : (hi.x - s.ox) * s.ihx;
@@ -280,57 +316,19 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
             if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
             else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
             else in = in_list_fp64(s, p, cur, i, j);
-            if (in) atomicOr(&bm[j >> 5], 1u << (j & 31));
+            if (in) {
+                atomicOr(&bm[j >> 5], 1u << (j & 31));
+                // short rows: r < r_off + skin (rshort2 carries a 1e-4 margin)
+                if (r2 < p.rshort2) atomicOr(&bs[j >> 5], 1u << (j & 31));
+            }
         }
         __syncwarp();
-        // bitmap -> ascending row
-        int total = 0;
-        int* row = s.rows + (size_t)i * s.cap;
-        for (int w0 = 0; w0 < nwords; w0 += 32) {
-            const int w = w0 + lane;
-            uint32_t bits = w < nwords ? bm[w] : 0u;
-            const int c = __popc(bits);
-            int x = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            int pos = total + x - c;
-            while (bits) {
-                const int t = __ffs(bits) - 1;
-                if (pos < s.cap) row[pos] = (w << 5) + t;
-                ++pos;
-                bits &= bits - 1u;
-            }
-            total += __shfl_sync(0xffffffffu, x, 31);
-        }
+        // bitmaps -> ascending rows
+        const int total = expand_bitmap(bm, nwords, s.rows + (size_t)i * s.cap, s.cap);
+        const int ns = p.rshort2 < INFINITY ? expand_bitmap(bs, nwords, s.srows + (size_t)i * s.caps, s.caps) : 0;
         if (lane == 0) {
             s.nlong[i] = min(total, s.cap);
             if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
-        }
-        __syncwarp();
-        // short rows: the members of the (ascending) row with r < r_off + skin
-        // (none when F_0 reads the long rows, rshort2 = +inf)
-        const int nl = min(total, s.cap);
-        int ns = 0;
-        int* srow = s.srows + (size_t)i * s.caps;
-        for (int k0 = 0; p.rshort2 < INFINITY && k0 < nl; k0 += 32) {
-            const int k = k0 + lane;
-            bool keep = false;
-            int j = 0;
-            if (k < nl) {
-                j = row[k];
-                const float3 d = pair_disp(p, hi, lo, s.phi[cur][j], s.plo[cur][j]);
-                keep = (d.x * d.x + d.y * d.y + d.z * d.z) < p.rshort2;
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int pos = ns + __popc(m & ((1u << lane) - 1u));
-                if (pos < s.caps) srow[pos] = j;
-            }
-            ns += __popc(m);
-        }
-        if (lane == 0) {
             s.nshort[i] = min(ns, s.caps);
             if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
             s.refx[i] = s.qx[cur][i];
