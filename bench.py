@@ -186,8 +186,12 @@ def our_arm(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
     windows = [WINDOW] * (args.steps // WINDOW) + ([args.steps % WINDOW] if args.steps % WINDOW else [])
     res = {}
-    for name, integ in (("bounce", bounce.BOUNCE), ("baoab", bounce.BAOAB)):
-        ctx = bounce.from_system(s, seed=7 + rank, **cfg)
+    # "bounce": per-type-pair bounds with the two-stage partner choice;
+    # "bounce_rowmax": one bound per atom type, partner uniform over the row
+    arms = (("bounce", bounce.BOUNCE, True), ("baoab", bounce.BAOAB, False),
+            ("bounce_rowmax", bounce.BOUNCE, False))
+    for name, integ, pb in arms:
+        ctx = bounce.from_system(s, seed=7 + rank, pair_bounds=pb, **cfg)
         ctx.set_state(q0, v0, step=0)
         if args.warmup:
             ctx.run(args.warmup, integ, stream=sh)
@@ -272,13 +276,18 @@ def our_arm(args):
         "vs_baseline": None,
         "dtype": "f32 pair math, f64 integration",
         "data": "synthetic: seeded lattice water droplet, BAOAB pre-equilibrated at 300 K",
-        "config": {"workload": "BOUNCE, 4096-molecule flexible-water droplet (12288 atoms), r_c 12 A, cell list, "
+        "config": {"workload": "BOUNCE (per-type-pair bounds), 4096-molecule flexible-water droplet (12288 atoms), r_c 12 A, "
+                               "cell list, "
                                "switch 4-5 A, 1 fs, friction 1/ps",
                    "atoms": n_atoms, "windows_of_steps": WINDOW, "l2": "flushed before each timed window",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "baoab": {"value": round(baoab_value, 4), "unit": "ns/day", "ms_per_step": round(t_a * 1e3 / steps, 5),
                   "pair_evals_per_s": pe_a},
         "bounce_pair_evals_per_s": pe_b,
+        "bounce_rowmax_bounds": {
+            "value": round(ws * ns_per_day(steps, _max_over_ranks(res["bounce_rowmax"]["ms"] / 1e3, ws, device)), 4),
+            "unit": "ns/day",
+            "proposals_per_atom_step": res["bounce_rowmax"]["energies"]["proposals"] / (steps * n_atoms)},
         "speedup_vs_own_baoab": round(value / baoab_value, 4),
         "proposals_per_atom_step": b["energies"]["proposals"] / (steps * n_atoms),
         "accepts_per_atom_step": b["energies"]["accepts"] / (steps * n_atoms),
@@ -331,11 +340,13 @@ def oracle_sample_step(md, sample):
         full_rows[i] = r[a]
     vs = v.copy()
     vs[sample] -= (h * ACCEL / t.mass[sample])[:, None] * g0()
-    vs, _ = jump_half(q, vs, full_rows, t, p, md.Lstar, md.beta, md.dt, md.seed, md.step_index, philox.STREAM_J1)
+    vs, _ = jump_half(q, vs, full_rows, t, p, md.Lstar, md.beta, md.dt, md.seed, md.step_index, philox.STREAM_J1,
+                      pair_bounds=md.pair_bounds)
     q[sample] += h * vs[sample]
     vs[sample] = o_step(vs[sample], t.mass[sample], md.T, md.gamma, md.dt, md.seed, md.step_index, atoms=sample)
     q[sample] += h * vs[sample]
-    vs, _ = jump_half(q, vs, full_rows, t, p, md.Lstar, md.beta, md.dt, md.seed, md.step_index, philox.STREAM_J2)
+    vs, _ = jump_half(q, vs, full_rows, t, p, md.Lstar, md.beta, md.dt, md.seed, md.step_index, philox.STREAM_J2,
+                      pair_bounds=md.pair_bounds)
     vs[sample] -= (h * ACCEL / t.mass[sample])[:, None] * g0()
     md.v = vs
     md.step_index += 1
@@ -346,7 +357,7 @@ def cpu_baseline(s, steps=3, every=8):
     sample: `steps` BOUNCE steps of every `every`-th atom; time scaled."""
     from oracle.integrate import OracleMD
     topo, p = _oracle_setup(s)
-    md = OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN)
+    md = OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN, pair_bounds=True)
     sample = np.arange(0, s.n_atoms, every)
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -365,7 +376,7 @@ def reference_arm(args):
     from oracle.integrate import OracleMD
     s = water_droplet(N_SIDE, seed=0)
     topo, p = _oracle_setup(s)
-    md = OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN)
+    md = OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN, pair_bounds=True)
     every = 8
     sample = np.arange(0, s.n_atoms, every)
     for _ in range(args.warmup):
@@ -382,7 +393,8 @@ def reference_arm(args):
         "value": round(val, 8), "unit": "ns/day", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded lattice water droplet",
-        "config": {"workload": "BOUNCE, 4096-molecule flexible-water droplet (12288 atoms), r_c 12 A, cell list, "
+        "config": {"workload": "BOUNCE (per-type-pair bounds), 4096-molecule flexible-water droplet (12288 atoms), r_c 12 A, "
+                               "cell list, "
                                "switch 4-5 A, 1 fs, friction 1/ps", "atoms": s.n_atoms},
         "cpu_baseline": {"value": round(val, 8), "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": sample_txt},
         "e2e": {"value": round(val, 8), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

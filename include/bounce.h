@@ -88,6 +88,16 @@ typedef struct bounce_config {
     int32_t jump_coulomb;  /* 1: Coulomb is split by chi like LJ (Sec. V droplets);
                             * 0: Coulomb wholly in F_0, only LJ on jumps
                             * (the first example of Sec. IV) (1)                 */
+    int32_t pair_bounds;   /* 1: one bound per type pair (Sec. V: L may depend on
+                            * the types of both particles) with a two-stage
+                            * partner choice: type b with probability
+                            * proportional to n_ib Lq_ab (Lq_ab =
+                            * ceil(2^16 L_ab / L*_a) + 1, 0 where L_ab = 0),
+                            * then uniform within the type; acceptance bound
+                            * Lt_ab = Lq_ab L*_a 2^-16.  Rows are then grouped
+                            * by partner type (ascending inside each group).
+                            * Needs max_neighbors < 65535.  0: one bound L*_a
+                            * per atom type, partner uniform over the row (0)  */
 } bounce_config;
 
 /* Energies and counters (bounce_get_energies). */

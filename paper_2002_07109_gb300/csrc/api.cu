@@ -353,6 +353,21 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     const double rs = g.r_off + g.skin;
     p.rshort2 = (g.jump_coulomb && std::isfinite(rs) && rs < rl) ? (float)(rs * rs * (1.0 + 1e-4)) : INFINITY;
     p.coul_jump = g.jump_coulomb ? 1 : 0;
+    p.typed = g.pair_bounds ? 1 : 0;
+    p.n_types = T;
+    for (int k = 0; k < BOUNCE_MAXT * BOUNCE_MAXT; ++k) {
+        p.lq[k] = 0u;
+        p.lt_d[k] = 0.0;
+    }
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const double L = c->L[a * T + b];
+            if (L > 0.0) {
+                const double q = std::ceil(L / c->Lstar[a] * 65536.0) + 1.0;
+                p.lq[a * BOUNCE_MAXT + b] = (uint32_t)q;
+                p.lt_d[a * BOUNCE_MAXT + b] = (q * c->Lstar[a]) * (1.0 / 65536.0);
+            }
+        }
     for (int a = 0; a < BOUNCE_MAXT; ++a) {
         p.Lstar_d[a] = c->Lstar[a];
         p.Lstar_f[a] = (float)c->Lstar[a];
@@ -553,6 +568,8 @@ int bounce_create(bounce_ctx** out, const bounce_config* cfg) {
         cfg->ewald_beta < 0)
         return BOUNCE_ERR_INVALID_ARG;
     if (cfg->periodic && !(cfg->box[0] > 0 && cfg->box[1] > 0 && cfg->box[2] > 0)) return BOUNCE_ERR_INVALID_ARG;
+    // two-stage choice: the row weight n_i * 65537 must fit 32 bits
+    if (cfg->pair_bounds && cfg->max_neighbors >= 65535) return BOUNCE_ERR_UNSUPPORTED;
     c = new bounce_ctx();
     c->cfg = *cfg;
     cudaError_t e = cudaSetDevice(cfg->device);
@@ -646,9 +663,10 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
         (r = dalloc(c, &dmol, n)) || (r = dalloc(c, &boff, n + 1)) ||
         (r = dalloc(c, &bidx, c->bt_idx.size())) || (r = dalloc(c, &bpar, c->bt_par.size())) ||
         (r = dalloc(c, &s.nlong, n)) || (r = dalloc(c, &s.rows, (size_t)n * s.cap)) ||
-        (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, distinct_short ? (size_t)n * s.caps : 1)) ||
+        (r = dalloc(c, &s.nseg, (size_t)n * BOUNCE_MAXT)) || (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, distinct_short ? (size_t)n * s.caps : 1)) ||
         (r = dalloc(c, &s.refx, n)) || (r = dalloc(c, &s.refy, n)) || (r = dalloc(c, &s.refz, n)) ||
         (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.cell_phi, n)) || (r = dalloc(c, &s.cell_mol, n)) ||
+        (r = dalloc(c, &s.cell_type, n)) ||
         (r = dalloc(c, &s.done_ctr, 2)) ||
         (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
         (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 2048)))
@@ -693,9 +711,11 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     int dev = c->cfg.device, optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t words = (size_t)(n + 31) / 32;
-    // per warp: the long- and short-row bitmaps (each rounded to 16 bytes) and
-    // 3 x 128 ints of cell-row runs
-    const size_t per_warp = 2 * ((words * 4 + 15) / 16 * 16) + 3 * 128 * 4;
+    // per warp: the long-row bitmaps (one per partner type with per-type-pair
+    // bounds), the short-row bitmap (each rounded to 16 bytes) and 3 x 128
+    // ints of cell-row runs
+    const size_t nbm = (c->cfg.pair_bounds ? (size_t)c->n_types : 1) + 1;
+    const size_t per_warp = nbm * ((words * 4 + 15) / 16 * 16) + 3 * 128 * 4;
     if (per_warp > (size_t)optin) return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for the row builder bitmap");
     c->bitmap_warps = (int)std::min<size_t>(8, (size_t)optin / per_warp);
     c->bitmap_bytes = per_warp * c->bitmap_warps;

@@ -47,6 +47,7 @@ struct DevSys {
     int* nlong;
     int* rows;
     int cap;
+    int* nseg;      // [n][BOUNCE_MAXT] candidates of each type in the row (typed rows)
     int* nshort;
     int* srows;
     int caps;
@@ -61,6 +62,7 @@ struct DevSys {
     float4* cell_phi;  // high position parts in cell order (coalesced candidate reads)
     unsigned int* done_ctr;  // [2] finished-CTA counters of the rebuild kernels (zero between launches)
     int* cell_mol;     // molecule ids in cell order
+    int* cell_type;    // atom types in cell order
     int ncx, ncy, ncz;
     float ox, oy, oz;        // grid origin (droplets)
     float ihx, ihy, ihz;     // inverse cell edges
@@ -115,6 +117,10 @@ struct Params {
     float rshort2;               // short-row threshold
     float rcull;                 // r_list with a safety margin for cell culling (+inf = all)
     int coul_jump;               // 1: Coulomb is switched by chi like LJ; 0: Coulomb wholly in F_0
+    int typed;                   // per-type-pair bounds with the two-stage partner choice
+    int n_types;
+    uint32_t lq[BOUNCE_MAXT * BOUNCE_MAXT];  // integer weights Lq_ab of the partner types
+    double lt_d[BOUNCE_MAXT * BOUNCE_MAXT];  // their bounds Lt_ab = Lq_ab L*_a 2^-16
     float Lstar_f[BOUNCE_MAXT];
     double Lstar_d[BOUNCE_MAXT];
     double beta;

@@ -8,7 +8,8 @@
 // sphere, screens each candidate in FP32 from the high position parts and
 // settles the few candidates near r_list exactly in FP64.  Accepted
 // candidates set a bit in a per-warp bitmap over all atom indices in shared
-// memory (a second bitmap marks the short-row members, r < r_off + skin);
+// memory (one per partner type with per-type-pair bounds, then a bitmap of
+// the short-row members, r < r_off + skin);
 // reading a bitmap back in word order yields the row already in ascending
 // order (no sort), and duplicate visits of a cell are harmless.
 // Every kernel returns at once unless a rebuild is pending (the step kernel
@@ -116,6 +117,7 @@ __global__ void k_cells_scatter(DevSys s, Params p, int step_off, int force) {
         s.cell_atoms[pos] = i;
         s.cell_phi[pos] = hi;
         s.cell_mol[pos] = s.mol[i];
+        s.cell_type[pos] = s.type[i];
     }
 }
 
@@ -136,7 +138,8 @@ __device__ __forceinline__ bool image_ambiguous(const Params& p, float4 hi, floa
 }
 
 // Writes the set bits of a warp's bitmap, in ascending order, as indices to
-// row[0 .. cap) and returns their count (which may exceed cap).  Passes of 32
+// row[0 .. cap) and returns their count (which may exceed cap; cap may be
+// zero or negative, then nothing is written).  Passes of 32
 // words: a prefix of their popcounts, then the warp expands the non-empty
 // words one at a time, lane b writing bit b, so neighbouring indices (dense
 // words) cost one step per word and the stores are contiguous.
@@ -174,12 +177,15 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
     extern __shared__ uint32_t smem_bm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int nwords = (s.n + 31) >> 5;
-    uint32_t* bm = smem_bm + (size_t)warp * words_per_warp;  // long-row bitmap
-    uint32_t* bs = bm + ((nwords + 3) & ~3);                   // short-row bitmap
+    // long-row bitmaps (one per partner type with per-type-pair bounds), then
+    // the short-row bitmap
+    const int wr = (nwords + 3) & ~3, nbm = p.typed ? p.n_types : 1;
+    uint32_t* bm = smem_bm + (size_t)warp * words_per_warp;
+    uint32_t* bs = bm + (size_t)nbm * wr;
     const int cur = (int)((*s.step_base + step_off) & 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
     for (int i = blockIdx.x * wpb + warp; i < s.n; i += gridDim.x * wpb) {
-        for (int w = lane; w < nwords; w += 32) bm[w] = bs[w] = 0u;
+        for (int w = lane; w < (nbm + 1) * wr; w += 32) bm[w] = 0u;
         __syncwarp();
         const float4 hi = s.phi[cur][i];
         const int mi = s.mol[i];
@@ -317,14 +323,22 @@ __global__ void k_rows(DevSys s, Params p, int step_off, int force, int words_pe
             else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
             else in = in_list_fp64(s, p, cur, i, j);
             if (in) {
-                atomicOr(&bm[j >> 5], 1u << (j & 31));
+                uint32_t* bt = p.typed ? bm + (size_t)s.cell_type[idx] * wr : bm;
+                atomicOr(&bt[j >> 5], 1u << (j & 31));
                 // short rows: r < r_off + skin (rshort2 carries a 1e-4 margin)
                 if (r2 < p.rshort2) atomicOr(&bs[j >> 5], 1u << (j & 31));
             }
         }
         __syncwarp();
         // bitmaps -> ascending rows
-        const int total = expand_bitmap(bm, nwords, s.rows + (size_t)i * s.cap, s.cap);
+        // (typed rows: the type groups one after the other, group sizes to nseg)
+        int total = 0;
+        for (int t = 0; t < nbm; ++t) {
+            const int c = expand_bitmap(bm + (size_t)t * wr, nwords, s.rows + (size_t)i * s.cap + total,
+                                        s.cap - total);
+            if (p.typed && lane == 0) s.nseg[(size_t)i * BOUNCE_MAXT + t] = c;
+            total += c;
+        }
         const int ns = p.rshort2 < INFINITY ? expand_bitmap(bs, nwords, s.srows + (size_t)i * s.caps, s.caps) : 0;
         if (lane == 0) {
             s.nlong[i] = min(total, s.cap);
@@ -352,27 +366,33 @@ __global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
         const int r = s.rep_of[i], b = s.rep_off[r], e = s.rep_off[r + 1], mi = s.mol[i];
         int* row = s.rows + (size_t)i * s.cap;
         int total = 0;
-        for (int j0 = b; j0 < e; j0 += 32) {
-            const int j = j0 + lane;
-            const bool keep = j < e && s.mol[j] != mi;
-            const uint32_t m = __ballot_sync(0xffffffffu, keep);
-            const int pos = total + __popc(m & ((1u << lane) - 1u));
-            if (keep && pos < s.cap) row[pos] = j;
-            total += __popc(m);
+        const int ngroups = p.typed ? p.n_types : 1;
+        for (int tb = 0; tb < ngroups; ++tb) {  // typed rows: one pass per partner type
+            const int before = total;
+            for (int j0 = b; j0 < e; j0 += 32) {
+                const int j = j0 + lane;
+                const bool keep = j < e && s.mol[j] != mi && (!p.typed || s.type[j] == tb);
+                const uint32_t m = __ballot_sync(0xffffffffu, keep);
+                const int pos = total + __popc(m & ((1u << lane) - 1u));
+                if (keep && pos < s.cap) row[pos] = j;
+                total += __popc(m);
+            }
+            if (p.typed && lane == 0) s.nseg[(size_t)i * BOUNCE_MAXT + tb] = total - before;
         }
         __syncwarp();
-        const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
+        // short rows: ascending over the replica with the same high-part
+        // screen as the cell-list builder (independent of the long row's order)
+        const float4 hi = s.phi[cur][i];
         const int nl = min(total, s.cap);
         int ns = 0;
         int* srow = s.srows + (size_t)i * s.caps;
-        for (int k0 = 0; p.rshort2 < INFINITY && k0 < nl; k0 += 32) {
-            const int k = k0 + lane;
+        for (int j0 = b; p.rshort2 < INFINITY && j0 < e; j0 += 32) {
+            const int j = j0 + lane;
             bool keep = false;
-            int j = 0;
-            if (k < nl) {
-                j = row[k];
-                const float3 d = pair_disp(p, hi, lo, s.phi[cur][j], s.plo[cur][j]);
-                keep = (d.x * d.x + d.y * d.y + d.z * d.z) < p.rshort2;
+            if (j < e && s.mol[j] != mi) {
+                const float4 hj = s.phi[cur][j];
+                const float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
+                keep = dx * dx + dy * dy + dz * dz < p.rshort2;
             }
             const uint32_t m = __ballot_sync(0xffffffffu, keep);
             if (keep) {

@@ -36,6 +36,7 @@ constexpr int FU = 2;  // proposals per thread in flight in the jump phase
 struct JumpSmem {
     double s[BOUNCE_GROUP];       // ||v|| (FP64)
     float sl[BOUNCE_GROUP];       // ||v|| L* (FP32)
+    float slt[BOUNCE_GROUP][BOUNCE_MAXT];  // ||v|| times the bound of each partner type (FP32)
     float vf[BOUNCE_GROUP][3];    // FP32 velocity at the start of the chain
     float dv[BOUNCE_GROUP][3];    // accumulated jump increment
     float muc[BOUNCE_GROUP];      // Poisson chunk mean (FP32)
@@ -53,8 +54,21 @@ __device__ __forceinline__ void jump_prep(const DevSys& s, const Params& p, Jump
     const double sp = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
     const int t = s.type[i];
     const double Ls = p.Lstar_d[t];
-    const int n = s.nlong[i];
-    double mu = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(p.beta, sp), Ls), (double)n), p.dt), 0.5);
+    // candidates: n_i, or with per-type-pair bounds the row weight W_i 2^-16
+    // (W_i = sum_b n_ib Lq_ab, exact in FP64)
+    double n;
+    if (p.typed) {
+        uint32_t W = 0u;
+        for (int b = 0; b < BOUNCE_MAXT; ++b) {
+            const double lt = p.lt_d[t * BOUNCE_MAXT + b];
+            W += (uint32_t)s.nseg[(size_t)i * BOUNCE_MAXT + b] * p.lq[t * BOUNCE_MAXT + b];
+            js.slt[a][b] = __double2float_rn(__dmul_rn(sp, lt));
+        }
+        n = __dmul_rn((double)W, 1.52587890625e-05);
+    } else {
+        n = (double)s.nlong[i];
+    }
+    double mu = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(p.beta, sp), Ls), n), p.dt), 0.5);
     if (!(mu <= 1e6)) {  // a blown-up state: report instead of drawing millions of proposals
         atomicOr(s.err, BERR_RATE);
         mu = 0.0;
@@ -67,6 +81,7 @@ __device__ __forceinline__ void jump_prep(const DevSys& s, const Params& p, Jump
     }
     js.s[a] = sp;
     js.sl[a] = __double2float_rn(__dmul_rn(sp, Ls));
+    if (!p.typed) js.slt[a][0] = js.sl[a];
     js.vf[a][0] = __double2float_rn(vx);
     js.vf[a][1] = __double2float_rn(vy);
     js.vf[a][2] = __double2float_rn(vz);
@@ -137,6 +152,8 @@ struct PropSmem {
     int P[BOUNCE_GROUP + 1];       // prefix of the proposal counts M of the CTA's atoms
     float4 ahi[BOUNCE_GROUP], alo[BOUNCE_GROUP];  // the atoms' split positions at q_n
     int an[BOUNCE_GROUP];          // their candidate-row lengths
+    uint32_t acum[BOUNCE_GROUP][BOUNCE_MAXT + 1];  // typed rows: cumulative weights C_b (C_T = W_i)
+    int ast[BOUNCE_GROUP][BOUNCE_MAXT];    // typed rows: start of each type group
     int next;                      // next atom to take in the chain pass
 };
 
@@ -183,6 +200,19 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
         ps.ahi[a] = s.phi[cur][i];
         ps.alo[a] = s.plo[cur][i];
         ps.an[a] = s.nlong[i];
+        if (p.typed) {
+            const int ta = s.type[i];
+            uint32_t c = 0u;
+            int st = 0;
+            for (int b = 0; b < BOUNCE_MAXT; ++b) {
+                const int nb = s.nseg[(size_t)i * BOUNCE_MAXT + b];
+                ps.acum[a][b] = c;
+                ps.ast[a][b] = st;
+                c += (uint32_t)nb * p.lq[ta * BOUNCE_MAXT + b];
+                st += nb;
+            }
+            ps.acum[a][BOUNCE_MAXT] = c;
+        }
     }
     __syncthreads();
     const int tot = ps.P[na];
@@ -200,9 +230,21 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                     const int g = c0 + t;
                     ow[u] = owner_of(ps, na, g);
                     const uint4 x = rng_atom(s, p, (uint32_t)(g - ps.P[ow[u]] + 1), base + ow[u], step, stream);
+                    uint32_t bsel = 0u;
+                    if (p.typed) {
+                        // two-stage choice: weight unit tg of W_i; its type group b is the
+                        // last with C_b <= tg (never an empty group); its member (tg - C_b) / Lq_ab
+                        const int a = ow[u], ta = type_of(ps.alo[a]);
+                        const uint32_t tg = __umulhi(x.x, ps.acum[a][BOUNCE_MAXT]);
+#pragma unroll
+                        for (int b = 1; b < BOUNCE_MAXT; ++b)
+                            if (ps.acum[a][b] <= tg) bsel = (uint32_t)b;
+                        jj[u] = ps.ast[a][bsel] + (int)((tg - ps.acum[a][bsel]) / p.lq[ta * BOUNCE_MAXT + bsel]);
+                    } else {
+                        jj[u] = (int)__umulhi(x.x, (uint32_t)ps.an[ow[u]]);
+                    }
                     ps.x1[t] = x.y;
-                    ps.x2[t] = x.z;
-                    jj[u] = (int)__umulhi(x.x, (uint32_t)ps.an[ow[u]]);
+                    ps.x2[t] = (x.z & ~63u) | bsel;  // u53 uses only the top 26 bits of x2
                 }
             }
 #pragma unroll
@@ -246,15 +288,15 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
             if (a >= na) break;
             const int lo = max(ps.P[a], c0), hi = min(ps.P[a + 1], c0 + cn);
             if (lo >= hi) continue;
-            const float sl = js.sl[a];
-            const double sp = js.s[a], Ls = p.Lstar_d[s.type[base + a]];
+            const int ti = s.type[base + a];
+            const double sp = js.s[a];
             float vx = js.vf[a][0], vy = js.vf[a][1], vz = js.vf[a][2];
             float dvx = js.dv[a][0], dvy = js.dv[a][1], dvz = js.dv[a][2];
             int nacc = js.nacc[a];
             for (int gb = lo; gb < hi; gb += 32) {
                 const int t = gb - c0 + lane;
                 const bool act = gb + lane < hi;
-                float gx = 0.f, gy = 0.f, gz = 0.f, uf = 1.f;
+                float gx = 0.f, gy = 0.f, gz = 0.f, uf = 1.f, sl = 0.f;
                 uint32_t x1 = 0, x2 = 0;
                 if (act) {
                     gx = ps.gx[t];
@@ -263,6 +305,7 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                     x1 = ps.x1[t];
                     x2 = ps.x2[t];
                     uf = u24(x1);
+                    sl = js.slt[a][x2 & 3u];  // ||v|| times the bound of the partner's type
                 }
                 int start = 0;
                 while (true) {
@@ -273,7 +316,10 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                     int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
                     const bool live = act && lane >= start;
                     if (__any_sync(0xffffffffu, live && dec == 2)) {
-                        if (live && dec == 2) dec = exact_decision(vx, vy, vz, gx, gy, gz, x1, x2, sp, Ls);
+                        if (live && dec == 2) {
+                            const double Ls = p.typed ? p.lt_d[ti * BOUNCE_MAXT + (x2 & 3u)] : p.Lstar_d[ti];
+                            dec = exact_decision(vx, vy, vz, gx, gy, gz, x1, x2, sp, Ls);
+                        }
                     }
                     const uint32_t acc = __ballot_sync(0xffffffffu, live && dec == 1);
                     const int f = acc ? __ffs(acc) - 1 : 32;
