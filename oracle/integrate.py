@@ -325,11 +325,37 @@ class OracleMD:
             self.step_bounce(with_recip=False, bonded_only=extended)
         self.kick(g_out(), H)
 
-    def run(self, n, integrator="bounce", respa_m=2):
+    def block_bounce_respa1(self, m=4, m2=3):
+        """One outer step Delta_out = m2 m delta of BOUNCE-RESPA1 (Sec. V, the
+        RESPA1 splitting): kick with G_recip over Delta_out/2; m2 intermediate
+        steps, each a kick with the short-range pair part over m delta/2, m
+        BJAOAJB steps whose F_0 holds only the bonded terms, and the same kick
+        again; the reciprocal kick again."""
+        H_out = 0.5 * m2 * m * self.dt
+        H_mid = 0.5 * m * self.dt
+
+        def g_mid():
+            self.ensure_rows()
+            return self.grad_short_pairs()
+
+        self.kick(self.recip()[1], H_out)
+        for _ in range(m2):
+            self.kick(g_mid(), H_mid)
+            for _ in range(m):
+                self.step_bounce(with_recip=False, bonded_only=True)
+            self.kick(g_mid(), H_mid)
+        self.kick(self.recip()[1], H_out)
+
+    def run(self, n, integrator="bounce", respa_m=2, respa_m2=3):
         if integrator in ("bounce_respa", "bounce_respa_ext"):
             assert n % respa_m == 0
             for _ in range(n // respa_m):
                 self.block_bounce_respa(respa_m, extended=integrator == "bounce_respa_ext")
+            return
+        if integrator == "bounce_respa1":
+            assert n % (respa_m * respa_m2) == 0
+            for _ in range(n // (respa_m * respa_m2)):
+                self.block_bounce_respa1(respa_m, respa_m2)
             return
         for _ in range(n):
             if integrator == "bounce":

@@ -121,3 +121,36 @@ def test_extended_respa_with_one_inner_step_is_baoab():
     a.run(12, "baoab")
     b.run(12, "bounce_respa_ext", respa_m=1)
     assert np.allclose(a.q, b.q, rtol=0, atol=1e-10) and np.allclose(a.v, b.v, rtol=0, atol=1e-12)
+
+
+def test_respa1_with_one_intermediate_step_is_extended_respa():
+    """With m2 = 1 the intermediate and outer kicks act at the same positions,
+    so BOUNCE-RESPA1 is the extended BOUNCE-RESPA (up to the rounding of
+    adding two kicks instead of their sum); with m = m2 = 1 it is BAOAB."""
+    a = _respa_setup(0.25)
+    b = _respa_setup(0.25)
+    a.run(12, "bounce_respa_ext", respa_m=2)
+    b.run(12, "bounce_respa1", respa_m=2, respa_m2=1)
+    assert np.allclose(a.q, b.q, rtol=0, atol=1e-10) and np.allclose(a.v, b.v, rtol=0, atol=1e-12)
+    c = _respa_setup(0.25)
+    d = _respa_setup(0.25)
+    c.run(8, "baoab")
+    d.run(8, "bounce_respa1", respa_m=1, respa_m2=1)
+    assert np.allclose(c.q, d.q, rtol=0, atol=1e-10) and np.allclose(c.v, d.v, rtol=0, atol=1e-12)
+
+
+def test_respa1_is_second_order():
+    """Energy error of BOUNCE-RESPA1 (m = 2, m2 = 2, no jump part, no
+    friction) falls by about 4 when delta halves."""
+    dev = []
+    for dt in (0.25, 0.125):
+        md = _respa_setup(dt)
+        e0 = md.energies()
+        t0 = e0["pot"] + e0["kin"]
+        worst = 0.0
+        for _ in range(4):
+            md.run(int(round(2.0 / dt)) * 4, "bounce_respa1", respa_m=2, respa_m2=2)
+            e = md.energies()
+            worst = max(worst, abs(e["pot"] + e["kin"] - t0))
+        dev.append(worst)
+    assert 2.5 < dev[0] / dev[1] < 6.0, dev
