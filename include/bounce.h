@@ -54,6 +54,13 @@ extern "C" {
                                * around every block of m BJAOAJB steps (Sec. V) */
 #define BOUNCE_BOUNCE_RESPA_EXT 3 /* extended split (Sec. V): the outer kicks add the
                                    * short-range pair part; inner F_0 = bonded only */
+#define BOUNCE_BOUNCE_RESPA1 4 /* three levels (Sec. V, RESPA1 splitting): the
+                                * reciprocal kick over Delta_out/2 =
+                                * respa_m2 respa_m delta/2 around respa_m2
+                                * intermediate steps; each kicks with the
+                                * short-range pair part over respa_m delta/2
+                                * around respa_m BJAOAJB steps with a
+                                * bonded-only F_0 */
 
 /* Gradient parts (bounce_compute_gradient). */
 #define BOUNCE_GRAD_FULL 0  /* dE_pot/dq: all pairs within r_c + bonded     */
@@ -84,7 +91,7 @@ typedef struct bounce_config {
     int32_t device;        /* CUDA device ordinal (0)                            */
     int32_t pme_grid[3];   /* SPME grid K1 K2 K3; 0 = no reciprocal part (0)     */
     int32_t pme_order;     /* SPME B-spline order, 3..8 (5)                      */
-    int32_t respa_m;       /* inner steps per BOUNCE-RESPA outer step (2)        */
+    int32_t respa_m;       /* inner steps per BOUNCE-RESPA outer step, 1..8 (2)  */
     int32_t jump_coulomb;  /* 1: Coulomb is split by chi like LJ (Sec. V droplets);
                             * 0: Coulomb wholly in F_0, only LJ on jumps
                             * (the first example of Sec. IV) (1)                 */
@@ -98,6 +105,8 @@ typedef struct bounce_config {
                             * by partner type (ascending inside each group).
                             * Needs max_neighbors < 65535.  0: one bound L*_a
                             * per atom type, partner uniform over the row (0)  */
+    int32_t respa_m2;      /* intermediate steps per BOUNCE-RESPA1 outer step,
+                            * 1..8 (3)                                           */
 } bounce_config;
 
 /* Energies and counters (bounce_get_energies). */
@@ -152,11 +161,13 @@ int bounce_set_state(bounce_ctx* ctx, const double* q, const double* v, int64_t 
 int bounce_get_state(bounce_ctx* ctx, double* q, double* v, int32_t where, void* stream);
 
 /* Advance n_steps full steps of the integrator (BOUNCE_BAOAB,
- * BOUNCE_BOUNCE or BOUNCE_BOUNCE_RESPA); the returned state is after the
- * last B half-kick.  With an SPME grid set, the reciprocal gradient is part
- * of the full gradient (BAOAB) or of F_0 (BOUNCE, Sec. V basic BOUNCE);
- * BOUNCE_BOUNCE_RESPA needs the grid; both RESPA integrators need a step
- * counter and n_steps that are multiples of respa_m (else INVALID_ARG).  All
+ * BOUNCE_BOUNCE, BOUNCE_BOUNCE_RESPA, BOUNCE_BOUNCE_RESPA_EXT or
+ * BOUNCE_BOUNCE_RESPA1); the returned state is after the last B half-kick.
+ * With an SPME grid set, the reciprocal gradient is part of the full
+ * gradient (BAOAB) or of F_0 (BOUNCE, Sec. V basic BOUNCE);
+ * BOUNCE_BOUNCE_RESPA needs the grid; the RESPA integrators need a step
+ * counter and n_steps that are multiples of respa_m (respa_m respa_m2 for
+ * RESPA1) (else INVALID_ARG).  All
  * work stays on the device; the call does not synchronise `stream` except
  * to report row overflows, which it checks once at the end.
  * Errors: STATE, LIST_OVERFLOW (a row exceeded max_neighbors; the state is

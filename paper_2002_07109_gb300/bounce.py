@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "NONFINITE", -4: "LIST_OVERFLOW", -5: "STATE", -6: "UNSUPPORTED"}
 HOST, DEVICE = 0, 1
-BAOAB, BOUNCE, BOUNCE_RESPA, BOUNCE_RESPA_EXT = 0, 1, 2, 3
+BAOAB, BOUNCE, BOUNCE_RESPA, BOUNCE_RESPA_EXT, BOUNCE_RESPA1 = 0, 1, 2, 3, 4
 GRAD_FULL, GRAD_SHORT, GRAD_LONG, GRAD_RECIP = 0, 1, 2, 3
 MAX_TYPES = 4
 
@@ -37,7 +37,7 @@ class bounce_config(C.Structure):
                 ("box", C.c_double * 3), ("max_neighbors", C.c_int32), ("max_short", C.c_int32),
                 ("device", C.c_int32), ("pme_grid", C.c_int32 * 3), ("pme_order", C.c_int32),
                 ("respa_m", C.c_int32), ("jump_coulomb", C.c_int32),
-                ("pair_bounds", C.c_int32)]
+                ("pair_bounds", C.c_int32), ("respa_m2", C.c_int32)]
 
 
 class bounce_energies(C.Structure):
@@ -109,7 +109,7 @@ class Context:
 
     def __init__(self, *, dt=1.0, gamma=0.001, temperature=300.0, seed=0, r_on=4.0, r_off=5.0, r_cut=math.inf,
                  skin=1.0, ewald_beta=0.0, box=None, max_neighbors=2048, max_short=256, device=0, pme_grid=None,
-                 pme_order=5, respa_m=2, jump_coulomb=True, pair_bounds=False):
+                 pme_order=5, respa_m=2, jump_coulomb=True, pair_bounds=False, respa_m2=3):
         cfg = bounce_config()
         bounce_config_default(C.byref(cfg))
         cfg.dt_fs, cfg.gamma_per_fs, cfg.temperature_K, cfg.seed = dt, gamma, temperature, seed
@@ -123,6 +123,7 @@ class Context:
         cfg.pme_order, cfg.respa_m = pme_order, respa_m
         cfg.jump_coulomb = 1 if jump_coulomb else 0
         cfg.pair_bounds = 1 if pair_bounds else 0
+        cfg.respa_m2 = respa_m2
         self.cfg = cfg
         h = C.c_void_p()
         r = bounce_create(C.byref(h), C.byref(cfg))

@@ -66,7 +66,7 @@ struct bounce_ctx {
     size_t bitmap_bytes = 0;
     int ncell_alloc = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[4][8] = {};   // [integrator][RESPA phase of the chunk's first step]
+    cudaGraphExec_t graph[5][64] = {};  // [integrator][RESPA phase of the chunk's first step]
     long long cur_step = 0;              // host mirror of the device step counter
     bool has_pme = false;
     DevPme pme{};
@@ -484,6 +484,19 @@ void plan(const bounce_ctx* c, int integ, int variant, long long step, bool& pme
         }
         return;
     }
+    if (integ == BOUNCE_BOUNCE_RESPA1) {
+        // kicks that meet at one boundary act at the same positions: the
+        // short-range kick of the intermediate level and the reciprocal kick
+        // of the outer level are applied together
+        const int m = c->cfg.respa_m, m2 = c->cfg.respa_m2;
+        const double w = variant == 1 ? 1.0 : 0.5;
+        if (step % m == 0) hout = w * m * dt;
+        if (step % ((long long)m * m2) == 0 && c->has_pme) {
+            pme = true;
+            hr = w * m * m2 * dt;
+        }
+        return;
+    }
     if (c->has_pme) {
         pme = true;
         hr = hk;
@@ -499,8 +512,16 @@ void boundary(bounce_ctx* c, int integ, int variant, int off, long long step, cu
     launch_step(c->ds, c->pp, integ, variant, off, hr, hout, st);
 }
 
+// Steps after which the kick pattern of the integrator repeats.
+int respa_period(const bounce_ctx* c, int integ) {
+    if (integ == BOUNCE_BOUNCE_RESPA || integ == BOUNCE_BOUNCE_RESPA_EXT) return c->cfg.respa_m;
+    if (integ == BOUNCE_BOUNCE_RESPA1) return c->cfg.respa_m * c->cfg.respa_m2;
+    return 1;
+}
+
 // Graph of CHUNK body steps whose first step index is congruent to `phase`
-// modulo respa_m (the RESPA block boundaries inside a chunk depend on it).
+// modulo the integrator's period (the RESPA block boundaries inside a chunk
+// depend on it).
 int ensure_graph(bounce_ctx* c, int integ, int phase) {
     if (c->graph[integ][phase]) return BOUNCE_OK;
     cudaStream_t st = c->cap_stream;
@@ -516,8 +537,13 @@ int ensure_graph(bounce_ctx* c, int integ, int phase) {
 }
 
 int check_run_args(bounce_ctx* c, int64_t n_steps, int32_t integ) {
-    if (n_steps < 0 || integ < BOUNCE_BAOAB || integ > BOUNCE_BOUNCE_RESPA_EXT)
+    if (n_steps < 0 || integ < BOUNCE_BAOAB || integ > BOUNCE_BOUNCE_RESPA1)
         return fail(c, BOUNCE_ERR_INVALID_ARG, "bad run arguments");
+    if (integ == BOUNCE_BOUNCE_RESPA1) {
+        const long long P = (long long)c->cfg.respa_m * c->cfg.respa_m2;
+        if (n_steps % P != 0 || c->cur_step % P != 0)
+            return fail(c, BOUNCE_ERR_INVALID_ARG, "BOUNCE-RESPA1 runs whole outer steps (multiples of respa_m respa_m2)");
+    }
     if (integ == BOUNCE_BOUNCE_RESPA || integ == BOUNCE_BOUNCE_RESPA_EXT) {
         const int m = c->cfg.respa_m;
         if (integ == BOUNCE_BOUNCE_RESPA && !c->has_pme)
@@ -557,6 +583,7 @@ void bounce_config_default(bounce_config* cfg) {
     cfg->pme_order = 5;
     cfg->respa_m = 2;
     cfg->jump_coulomb = 1;
+    cfg->respa_m2 = 3;
 }
 
 int bounce_create(bounce_ctx** out, const bounce_config* cfg) {
@@ -568,6 +595,7 @@ int bounce_create(bounce_ctx** out, const bounce_config* cfg) {
         cfg->ewald_beta < 0)
         return BOUNCE_ERR_INVALID_ARG;
     if (cfg->periodic && !(cfg->box[0] > 0 && cfg->box[1] > 0 && cfg->box[2] > 0)) return BOUNCE_ERR_INVALID_ARG;
+    if (cfg->respa_m < 1 || cfg->respa_m > 8 || cfg->respa_m2 < 1 || cfg->respa_m2 > 8) return BOUNCE_ERR_INVALID_ARG;
     // two-stage choice: the row weight n_i * 65537 must fit 32 bits
     if (cfg->pair_bounds && cfg->max_neighbors >= 65535) return BOUNCE_ERR_UNSUPPORTED;
     c = new bounce_ctx();
@@ -839,7 +867,7 @@ int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
     if (n_steps == 0) return BOUNCE_OK;
     cudaSetDevice(c->cfg.device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int m = c->cfg.respa_m > 0 ? c->cfg.respa_m : 1;
+    const int m = respa_period(c, integ);
     long long s0 = c->cur_step;
     // head: B/2 [J] A O A at the current step
     boundary(c, integ, 0, 0, s0, st);

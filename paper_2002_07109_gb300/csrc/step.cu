@@ -662,7 +662,7 @@ __global__ void k_advance(DevSys s, long long by) { *const_cast<long long*>(s.st
 void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
                  double hout, cudaStream_t st) {
     const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
-    const int ext = integrator == 3 ? 1 : 0;
+    const int ext = integrator >= 3 ? 1 : 0;  // extended RESPA and RESPA1: bonded-only F_0
     if (integrator != 0) k_step<1><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr, ext, hout);
     else k_step<0><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr, 0, 0.0);
 }

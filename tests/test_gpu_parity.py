@@ -366,3 +366,37 @@ def test_extended_respa_droplet_block():
     assert ok.mean() > 0.99, ok.mean()
     assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["box_pme", "droplet_cutoff"])
+def test_respa1_outer_step(case):
+    """BOUNCE-RESPA1 (m = 2 inner, m2 = 3 intermediate steps): one outer step
+    of 6 BJAOAJB steps against the oracle; the droplet has no reciprocal part."""
+    if case == "box_pme":
+        s, ctx, md = _setup_pme(perturb=0.0)
+        kscale = _kick_scale(md, "short", True)
+    else:
+        s, ctx, md = _setup(case)
+        kscale = _kick_scale(md, "short", False)
+    ctx.set_state(md.q, md.v, step=12)
+    md.step_index = 12
+    ctx.run(6, bounce.BOUNCE_RESPA1)
+    md.run(6, "bounce_respa1", respa_m=2, respa_m2=3)
+    q, v = ctx.get_state()
+    dv = np.linalg.norm(v - md.v, axis=1)
+    ok = dv / (np.linalg.norm(md.v, axis=1) + 6 * kscale) < TOL
+    # a near tie in any of the 12 jump half-steps may flip one atom's chain
+    assert ok.mean() > 0.99, ok.mean()
+    assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
+    ctx.close()
+
+
+def test_respa1_rejects_partial_outer_steps():
+    s, ctx, md = _setup("droplet_cutoff")
+    ctx.set_state(md.q, md.v, step=12)
+    with pytest.raises(bounce.BounceError):
+        ctx.run(4, bounce.BOUNCE_RESPA1)
+    ctx.set_state(md.q, md.v, step=8)
+    with pytest.raises(bounce.BounceError):
+        ctx.run(6, bounce.BOUNCE_RESPA1)
+    ctx.close()
