@@ -303,12 +303,61 @@ def our_arm(args):
         "gpu_launches": b["launches"],
         "clocks": clk,
     }
+    line["long_run"] = long_run(s, q0, v0, cfg, rank, stream, sh)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(s)
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def long_run(s, q0, v0, cfg, rank, stream, sh, n_steps=1000, chunk=100):
+    """Graph-captured runs of n_steps from the equilibrated state (after 64
+    warm-up steps), for the matched-observables comparison: BAOAB; BOUNCE
+    with the LJ part on the jumps and Coulomb in F_0 (per-type-pair bounds);
+    BOUNCE with Coulomb and LJ on the jumps (the headline split), which heats
+    and is reported with the step at which it stopped.  Each: ns/day over the
+    chunks timed with CUDA events, and the means of the potential energy per
+    molecule and of the temperature sampled after every chunk."""
+    import torch
+    from paper_2002_07109_gb300 import bounce
+    n_mol = s.n_atoms // 3
+    out = {}
+    arms = (("baoab", bounce.BAOAB, dict(pair_bounds=False)),
+            ("bounce_lj_jumps", bounce.BOUNCE, dict(pair_bounds=True, jump_coulomb=False)),
+            ("bounce_coulomb_lj_jumps", bounce.BOUNCE, dict(pair_bounds=True)))
+    for name, integ, extra in arms:
+        ctx = bounce.from_system(s, seed=11 + rank, **cfg, **extra)
+        ctx.set_state(q0, v0, step=0)
+        ms, pe, T, done, err = 0.0, [], [], 0, None
+        try:
+            ctx.run(64, integ, stream=sh)
+            torch.cuda.synchronize()
+            ctx.reset_counters(stream=sh)
+            for _ in range(n_steps // chunk):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.run(chunk, integ, stream=sh)
+                b.record(stream)
+                b.synchronize()
+                ms += a.elapsed_time(b)
+                done += chunk
+                e = ctx.energies(stream=sh)
+                pe.append(e["potential"] / n_mol)
+                T.append(e["temperature"])
+        except Exception as ex:  # a blown-up state is reported, not timed
+            err = str(ex).split("(")[0].strip()
+        ctx.close()
+        r = {"steps": done}
+        if done:
+            r.update({"ns_per_day": round(ns_per_day(done, ms / 1e3), 2), "pe_per_molecule": round(float(np.mean(pe)), 4),
+                      "temperature_K": round(float(np.mean(T)), 1)})
+        if err:
+            r["stopped"] = err
+        out[name] = r
+    return out
 
 
 def _oracle_setup(s):

@@ -246,38 +246,44 @@ __device__ __forceinline__ float rsqrt_nr(float r2) {
     return y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
-// W'(r) / r of one pair (Coulomb or Ewald direct + LJ), r2 < rc2 assumed.
-__device__ __forceinline__ float pair_dW_over_r(const Params& p, float r2, float qq, int tp) {
+// Coulomb (or Ewald direct) part wc and LJ part wl of W'(r) / r of one pair, r2 < rc2 assumed.
+__device__ __forceinline__ void pair_dW_parts(const Params& p, float r2, float qq, int tp, float& wc, float& wl) {
     float ir = rsqrt_nr(r2);
     float ir2 = ir * ir;
-    float w;
     if (p.ebeta > 0.f) {
         float r = r2 * ir;
         float br = p.ebeta * r;
-        w = -qq * (erfcf(br) * ir2 + p.e2b_sqrtpi * __expf(-br * br) * ir) * ir;
+        wc = -qq * (erfcf(br) * ir2 + p.e2b_sqrtpi * __expf(-br * br) * ir) * ir;
     } else {
-        w = -qq * ir2 * ir;
+        wc = -qq * ir2 * ir;
     }
+    wl = 0.f;
     float c12 = p.c12[tp];
     if (c12 != 0.f) {
         float ir6 = ir2 * ir2 * ir2;
-        w -= (12.f * c12 * ir6 - 6.f * p.c6[tp]) * ir6 * ir2;
+        wl = -((12.f * c12 * ir6 - 6.f * p.c6[tp]) * ir6 * ir2);
     }
-    return w;
+}
+
+// W'(r) / r of one pair (Coulomb or Ewald direct + LJ), r2 < rc2 assumed.
+__device__ __forceinline__ float pair_dW_over_r(const Params& p, float r2, float qq, int tp) {
+    float wc, wl;
+    pair_dW_parts(p, r2, qq, tp, wc, wl);
+    return wc + wl;
 }
 
 // W'/r split into the part switched by chi (sw) and the part that always
 // stays in F_0 (fixed): (all, 0), or (LJ, Coulomb) when Coulomb is kept out
-// of the jumps.
+// of the jumps.  One evaluation of the pair terms either way.
 __device__ __forceinline__ void pair_dW_split(const Params& p, float r2, float qq, int tp, float& sw, float& fixed) {
-    const float all = pair_dW_over_r(p, r2, qq, tp);
+    float wc, wl;
+    pair_dW_parts(p, r2, qq, tp, wc, wl);
     if (p.coul_jump) {
-        sw = all;
+        sw = wc + wl;
         fixed = 0.f;
     } else {
-        const float lj = pair_dW_over_r(p, r2, 0.f, tp);
-        sw = lj;
-        fixed = all - lj;
+        sw = wl;
+        fixed = wc;
     }
 }
 
