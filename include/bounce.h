@@ -153,8 +153,11 @@ int bounce_set_topology(bounce_ctx* ctx, int32_t n_atoms, const int32_t* type, c
 int bounce_set_lj(bounce_ctx* ctx, int32_t n_types, const double* sigma, const double* eps);
 
 /* Positions q[n,3] and velocities v[n,3] (A, A/fs); resets the step counter
- * to `step` (the Philox step index of the next step) and forces a row
- * rebuild.  Errors: INVALID_ARG, NONFINITE, STATE (no topology). */
+ * to `step` (the Philox step index of the next step).  The candidate rows are
+ * rebuilt at the next launch if this is the first state of the topology (or
+ * of a replica layout) or if an atom lies more than skin/2 from its position
+ * at the last row build -- the test a run applies every step; otherwise the
+ * rows are kept.  Errors: INVALID_ARG, NONFINITE, STATE (no topology). */
 int bounce_set_state(bounce_ctx* ctx, const double* q, const double* v, int64_t step, int32_t where, void* stream);
 
 /* Copy the current state out (q, v may be NULL to skip). */

@@ -68,6 +68,7 @@ struct bounce_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[5][64] = {};  // [integrator][RESPA phase of the chunk's first step]
     long long cur_step = 0;              // host mirror of the device step counter
+    bool rows_valid = false;             // rows were requested for this topology and replica layout
     bool has_pme = false;
     DevPme pme{};
     double* diff_part = nullptr;   // [NPAR n + NPAR] parameter partials and sums of the pair backward
@@ -626,6 +627,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     free_all(c);
     c->ncell_alloc = 0;
     c->have_topo = c->have_lj = c->have_state = false;
+    c->rows_valid = false;
     c->n = n;
     c->type.assign(type, type + n);
     c->mol.assign(molecule, molecule + n);
@@ -821,8 +823,16 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
     long long st0 = step;
     CU(cudaMemcpyAsync(c->d_step, &st0, sizeof(long long), cudaMemcpyHostToDevice, st));
     launch_pack_positions(s, c->pp, cur, st);
-    const int one = 1;
-    CU(cudaMemcpyAsync(s.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    // rows stay valid while every atom is within skin/2 of where they were
+    // built (the same test as during a run); otherwise the next launch
+    // rebuilds them
+    if (c->rows_valid) {
+        launch_flag_moved(s, c->pp, cur, st);
+    } else {
+        const int one = 1;
+        CU(cudaMemcpyAsync(s.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+        c->rows_valid = true;
+    }
     CU(cudaMemsetAsync(s.err, 0, sizeof(int), st));
     CU(cudaStreamSynchronize(st));
     c->step0 = step;
@@ -1183,6 +1193,7 @@ int bounce_set_replicas(bounce_ctx* c, int32_t n_rep, const int32_t* off, const 
     c->ds.rep_off = doff;
     c->ds.rep_key = dkey;
     drop_graphs(c);
+    c->rows_valid = false;
     return BOUNCE_OK;
 }
 

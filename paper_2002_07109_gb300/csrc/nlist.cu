@@ -415,7 +415,18 @@ __global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
     if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
 }
 
+__global__ void k_flag_moved(DevSys s, Params p, int cur) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        const double ex = s.qx[cur][i] - s.refx[i], ey = s.qy[cur][i] - s.refy[i], ez = s.qz[cur][i] - s.refz[i];
+        if (ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+    }
+}
+
 }  // namespace
+
+void launch_flag_moved(const DevSys& s, const Params& p, int cur, cudaStream_t st) {
+    k_flag_moved<<<(s.n + 255) / 256, 256, 0, st>>>(s, p, cur);
+}
 
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
                     cudaStream_t st) {

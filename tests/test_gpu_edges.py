@@ -112,3 +112,27 @@ def test_bad_inputs_are_refused():
     with pytest.raises(bounce.BounceError, match="INVALID_ARG"):
         ctx.set_topology(bad, s.mass, s.charge, s.molecule)
     ctx.close()
+
+
+def test_set_state_keeps_valid_rows():
+    """A new state within skin/2 of the last row build keeps the rows (no
+    rebuild counted); one atom moved further forces a rebuild, and the rows
+    then match the oracle's rows at the new positions."""
+    from oracle.neighbors import rows as oracle_rows
+    s = water_droplet_molecules(300, seed=2)
+    ctx = bounce.from_system(s, seed=1, r_on=4.0, r_off=5.0, r_cut=9.0, skin=1.0)
+    ctx.set_state(s.q, s.v, step=0)
+    ctx.rows()
+    n0 = ctx.energies()["rebuilds"]
+    q1 = s.q + 0.2
+    ctx.set_state(q1, s.v, step=0)
+    ctx.rows()
+    assert ctx.energies()["rebuilds"] == n0
+    q2 = q1.copy()
+    q2[5] += np.array([0.6, 0.0, 0.0])
+    ctx.set_state(q2, s.v, step=0)
+    got = ctx.rows()
+    assert ctx.energies()["rebuilds"] == n0 + 1
+    ref = oracle_rows(q2, s.molecule, 10.0)
+    assert all(np.array_equal(a, b) for a, b in zip(got, ref))
+    ctx.close()
