@@ -358,6 +358,8 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     p.n_types = T;
     for (int k = 0; k < BOUNCE_MAXT * BOUNCE_MAXT; ++k) {
         p.lq[k] = 0u;
+        p.lq_m[k] = 0u;
+        p.lq_s[k] = 0u;
         p.lt_d[k] = 0.0;
     }
     for (int a = 0; a < T; ++a)
@@ -367,6 +369,13 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
                 const double q = std::ceil(L / c->Lstar[a] * 65536.0) + 1.0;
                 p.lq[a * BOUNCE_MAXT + b] = (uint32_t)q;
                 p.lt_d[a * BOUNCE_MAXT + b] = (q * c->Lstar[a]) * (1.0 / 65536.0);
+                // division by the invariant d = Lq_ab >= 2 (Granlund and Montgomery 1994, Fig. 4.1):
+                // l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, x / d = (t + ((x - t) >> 1)) >> (l - 1)
+                const uint64_t d = (uint64_t)q;
+                int l = 0;
+                while ((1ull << l) < d) ++l;
+                p.lq_m[a * BOUNCE_MAXT + b] = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+                p.lq_s[a * BOUNCE_MAXT + b] = (uint32_t)(l - 1);
             }
         }
     for (int a = 0; a < BOUNCE_MAXT; ++a) {

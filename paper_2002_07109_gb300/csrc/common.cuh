@@ -120,6 +120,8 @@ struct Params {
     int typed;                   // per-type-pair bounds with the two-stage partner choice
     int n_types;
     uint32_t lq[BOUNCE_MAXT * BOUNCE_MAXT];  // integer weights Lq_ab of the partner types
+    uint32_t lq_m[BOUNCE_MAXT * BOUNCE_MAXT];  // x / Lq_ab = (t + ((x - t) >> 1)) >> lq_s, t = umulhi(lq_m, x)
+    uint32_t lq_s[BOUNCE_MAXT * BOUNCE_MAXT];  //   (Granlund-Montgomery division by an invariant integer)
     double lt_d[BOUNCE_MAXT * BOUNCE_MAXT];  // their bounds Lt_ab = Lq_ab L*_a 2^-16
     float Lstar_f[BOUNCE_MAXT];
     double Lstar_d[BOUNCE_MAXT];
@@ -246,12 +248,14 @@ __device__ __forceinline__ float rsqrt_nr(float r2) {
     return y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
-// Coulomb (or Ewald direct) part wc and LJ part wl of W'(r) / r of one pair, r2 < rc2 assumed.
-__device__ __forceinline__ void pair_dW_parts(const Params& p, float r2, float qq, int tp, float& wc, float& wl) {
+// Coulomb (or Ewald direct) part wc and LJ part wl of W'(r) / r of one pair,
+// r2 < rc2 assumed; r = r2 / sqrt(r2) from the same reciprocal square root.
+__device__ __forceinline__ void pair_dW_parts(const Params& p, float r2, float qq, int tp, float& wc, float& wl,
+                                              float& r) {
     float ir = rsqrt_nr(r2);
     float ir2 = ir * ir;
+    r = r2 * ir;
     if (p.ebeta > 0.f) {
-        float r = r2 * ir;
         float br = p.ebeta * r;
         wc = -qq * (erfcf(br) * ir2 + p.e2b_sqrtpi * __expf(-br * br) * ir) * ir;
     } else {
@@ -267,17 +271,18 @@ __device__ __forceinline__ void pair_dW_parts(const Params& p, float r2, float q
 
 // W'(r) / r of one pair (Coulomb or Ewald direct + LJ), r2 < rc2 assumed.
 __device__ __forceinline__ float pair_dW_over_r(const Params& p, float r2, float qq, int tp) {
-    float wc, wl;
-    pair_dW_parts(p, r2, qq, tp, wc, wl);
+    float wc, wl, r;
+    pair_dW_parts(p, r2, qq, tp, wc, wl, r);
     return wc + wl;
 }
 
 // W'/r split into the part switched by chi (sw) and the part that always
 // stays in F_0 (fixed): (all, 0), or (LJ, Coulomb) when Coulomb is kept out
-// of the jumps.  One evaluation of the pair terms either way.
-__device__ __forceinline__ void pair_dW_split(const Params& p, float r2, float qq, int tp, float& sw, float& fixed) {
+// of the jumps.  One evaluation of the pair terms either way; r as above.
+__device__ __forceinline__ void pair_dW_split(const Params& p, float r2, float qq, int tp, float& sw, float& fixed,
+                                              float& r) {
     float wc, wl;
-    pair_dW_parts(p, r2, qq, tp, wc, wl);
+    pair_dW_parts(p, r2, qq, tp, wc, wl, r);
     if (p.coul_jump) {
         sw = wc + wl;
         fixed = 0.f;

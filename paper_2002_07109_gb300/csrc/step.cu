@@ -239,7 +239,9 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
 #pragma unroll
                         for (int b = 1; b < BOUNCE_MAXT; ++b)
                             if (ps.acum[a][b] <= tg) bsel = (uint32_t)b;
-                        jj[u] = ps.ast[a][bsel] + (int)((tg - ps.acum[a][bsel]) / p.lq[ta * BOUNCE_MAXT + bsel]);
+                        const uint32_t x = tg - ps.acum[a][bsel], ab = ta * BOUNCE_MAXT + bsel;
+                        const uint32_t th = __umulhi(p.lq_m[ab], x);
+                        jj[u] = ps.ast[a][bsel] + (int)((th + ((x - th) >> 1)) >> p.lq_s[ab]);  // x / Lq_ab
                     } else {
                         jj[u] = (int)__umulhi(x.x, (uint32_t)ps.an[ow[u]]);
                     }
@@ -266,10 +268,10 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                 const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
                 float gx = 0.f, gy = 0.f, gz = 0.f;
                 if (inside_cut(s, p, cur, base + ow[u], jj[u], r2)) {
-                    float sw, fixed;
+                    float sw, fixed, r;
                     pair_dW_split(p, r2, p.kcoul * hi.w * hj[u].w, type_of(lo) * BOUNCE_MAXT + type_of(lj[u]), sw,
-                                  fixed);
-                    const float w = chi_of(p, sqrtf(r2)) * sw;
+                                  fixed, r);
+                    const float w = chi_of(p, r) * sw;
                     gx = w * d.x;
                     gy = w * d.y;
                     gz = w * d.z;
@@ -290,13 +292,14 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
             if (lo >= hi) continue;
             const int ti = s.type[base + a];
             const double sp = js.s[a];
+            const float sp_f = __double2float_rn(sp);
             float vx = js.vf[a][0], vy = js.vf[a][1], vz = js.vf[a][2];
             float dvx = js.dv[a][0], dvy = js.dv[a][1], dvz = js.dv[a][2];
             int nacc = js.nacc[a];
             for (int gb = lo; gb < hi; gb += 32) {
                 const int t = gb - c0 + lane;
                 const bool act = gb + lane < hi;
-                float gx = 0.f, gy = 0.f, gz = 0.f, uf = 1.f, sl = 0.f;
+                float gx = 0.f, gy = 0.f, gz = 0.f, thr = 0.f, err = 0.f, sl = 0.f;
                 uint32_t x1 = 0, x2 = 0;
                 if (act) {
                     gx = ps.gx[t];
@@ -304,15 +307,17 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                     gz = ps.gz[t];
                     x1 = ps.x1[t];
                     x2 = ps.x2[t];
-                    uf = u24(x1);
                     sl = js.slt[a][x2 & 3u];  // ||v|| times the bound of the partner's type
+                    thr = u24(x1) * sl;
+                    // FP32 decision error: |fl(v.F) - v.F| <= 4e-6 sum_c |v_c F_c| <= 4e-6 ||v|| ||F||
+                    // (the chain's FP32 ||v|| stays within 1e-4 of the FP64 one, reflections keep it);
+                    // U and ||v|| L within 2.4e-7 ||v|| L.  Fixed along the chain.
+                    err = 4e-6f * (thr + 1.0001f * sp_f * sqrtf(gx * gx + gy * gy + gz * gz)) + 2.4e-7f * sl;
                 }
                 int start = 0;
                 while (true) {
-                    // decide with the current velocity: accept iff U ||v|| L* < v . F
+                    // decide with the current velocity: accept iff U ||v|| L < v . F
                     const float af = vx * gx + vy * gy + vz * gz;
-                    const float thr = uf * sl;
-                    const float err = 4e-6f * (thr + fabsf(vx * gx) + fabsf(vy * gy) + fabsf(vz * gz)) + 2.4e-7f * sl;
                     int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
                     const bool live = act && lane >= start;
                     if (__any_sync(0xffffffffu, live && dec == 2)) {
@@ -330,7 +335,7 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                                 fz = __shfl_sync(0xffffffffu, gz, f);
                     const float aa = vx * fx + vy * fy + vz * fz;
                     const float ff = fx * fx + fy * fy + fz * fz;
-                    const float coef = (aa + aa) / ff;
+                    const float coef = __fdividef(aa + aa, ff);
                     vx -= coef * fx;
                     vy -= coef * fy;
                     vz -= coef * fz;
@@ -396,11 +401,11 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
             const float3 d = pair_disp(p, hi, lo, hj[u], lj[u]);
             const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
             if (inside_cut(s, p, cur, i, j[u], r2)) {
-                float sw, fixed;
-                pair_dW_split(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]), sw, fixed);
+                float sw, fixed, r;
+                pair_dW_split(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]), sw, fixed, r);
                 float w = sw + fixed;
                 if (part != 0 && part != 5) {
-                    const float c = chi_of(p, sqrtf(r2));
+                    const float c = chi_of(p, r);
                     w = part == 2 ? sw * c : sw * (1.f - c) + fixed;
                 }
                 gx += w * d.x;
