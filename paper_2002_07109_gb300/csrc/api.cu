@@ -61,6 +61,8 @@ struct bounce_ctx {
     int hist_alloc = 0;
     long long* d_step = nullptr;
     int* h_err = nullptr;        // pinned
+    double* h_stage = nullptr;   // pinned [6 n]: interleaved q then v on their way to or from the device
+    double* d_stage = nullptr;   // device [6 n]
     unsigned long long* h_cnt = nullptr;
     int bitmap_warps = 1;
     size_t bitmap_bytes = 0;
@@ -111,6 +113,8 @@ void drop_graphs(bounce_ctx* c) {
 }
 
 void free_all(bounce_ctx* c) {
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    c->h_stage = nullptr;
     drop_graphs(c);
     for (auto& b : c->bufs) cudaFree(b.p);
     c->bufs.clear();
@@ -393,7 +397,7 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
 // Cell grid for the current host positions: cells of edge >= r_list / 3
 // (the row builder scans, for each (y, z) cell row within reach, only the
 // x-span of cells the r_list sphere can touch).
-int setup_grid(bounce_ctx* c, const std::vector<double>& q) {
+int setup_grid(bounce_ctx* c, const double* q) {
     DevSys& s = c->ds;
     const double rl = r_list(c->cfg);
     const double reach = std::isfinite(rl) ? rl * (1.0 + 1e-5) + 1e-3 : INFINITY;
@@ -564,12 +568,6 @@ int check_run_args(bounce_ctx* c, int64_t n_steps, int32_t integ) {
     return BOUNCE_OK;
 }
 
-bool finite_all(const std::vector<double>& x) {
-    for (double v : x)
-        if (!std::isfinite(v)) return false;
-    return true;
-}
-
 }  // namespace
 
 extern "C" {
@@ -708,7 +706,8 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
         (r = dalloc(c, &s.cell_type, n)) ||
         (r = dalloc(c, &s.done_ctr, 2)) ||
         (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
-        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 2048)))
+        (r = dalloc(c, &s.cnt, CNT_N)) || (r = dalloc(c, &c->d_step, 1)) || (r = dalloc(c, &c->terms, 6 * (size_t)n + 2048)) ||
+        (r = dalloc(c, &c->d_stage, 6 * (size_t)n)))
         return r;
     s.kick = kick;
     s.osd = osd;
@@ -792,16 +791,20 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
     cudaSetDevice(c->cfg.device);
     cudaStream_t st = (cudaStream_t)stream;
     const int n = c->n;
-    std::vector<double> hq(3 * (size_t)n), hv(3 * (size_t)n);
-    if (where == BOUNCE_HOST) {
-        std::memcpy(hq.data(), q, hq.size() * sizeof(double));
-        std::memcpy(hv.data(), v, hv.size() * sizeof(double));
-    } else {
-        CU(cudaMemcpyAsync(hq.data(), q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(hv.data(), v, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    const size_t n3 = 3 * (size_t)n;
+    if (!c->h_stage) CU(cudaMallocHost(&c->h_stage, 2 * n3 * sizeof(double)));
+    // host view of the state for the checks and the cell grid
+    const double *hq = q, *hv = v;
+    if (where == BOUNCE_DEVICE) {
+        CU(cudaMemcpyAsync(c->h_stage, q, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(c->h_stage + n3, v, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
+        hq = c->h_stage;
+        hv = c->h_stage + n3;
     }
-    if (!finite_all(hq) || !finite_all(hv)) return fail(c, BOUNCE_ERR_NONFINITE, "non-finite position or velocity");
+    for (size_t k = 0; k < n3; ++k)
+        if (!std::isfinite(hq[k]) || !std::isfinite(hv[k]))
+            return fail(c, BOUNCE_ERR_NONFINITE, "non-finite position or velocity");
     const DevSys before = c->ds;
     int r = setup_grid(c, hq);
     if (r) return r;
@@ -813,22 +816,18 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
         g.cell_count != before.cell_count || g.cell_start != before.cell_start || g.cell_fill != before.cell_fill)
         drop_graphs(c);
     const int cur = (int)(step & 1);
-    std::vector<double> cx(n), cy(n), cz(n), vx(n), vy(n), vz(n);
-    for (int i = 0; i < n; ++i) {
-        cx[i] = hq[3 * i];
-        cy[i] = hq[3 * i + 1];
-        cz[i] = hq[3 * i + 2];
-        vx[i] = hv[3 * i];
-        vy[i] = hv[3 * i + 1];
-        vz[i] = hv[3 * i + 2];
-    }
     DevSys& s = c->ds;
-    CU(cudaMemcpyAsync(s.qx[cur], cx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(s.qy[cur], cy.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(s.qz[cur], cz.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(s.vx, vx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(s.vy, vy.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(s.vz, vz.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    // host arrays: one pinned staging copy and one contiguous upload; device
+    // arrays are read in place
+    const double *dq = q, *dv = v;
+    if (where == BOUNCE_HOST) {
+        std::memcpy(c->h_stage, q, n3 * sizeof(double));
+        std::memcpy(c->h_stage + n3, v, n3 * sizeof(double));
+        CU(cudaMemcpyAsync(c->d_stage, c->h_stage, 2 * n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        dq = c->d_stage;
+        dv = c->d_stage + n3;
+    }
+    launch_state_in(s, dq, dv, cur, st);
     long long st0 = step;
     CU(cudaMemcpyAsync(c->d_step, &st0, sizeof(long long), cudaMemcpyHostToDevice, st));
     launch_pack_positions(s, c->pp, cur, st);
@@ -856,25 +855,20 @@ int bounce_get_state(bounce_ctx* c, double* q, double* v, int32_t where, void* s
     if (where != BOUNCE_HOST && where != BOUNCE_DEVICE) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad where");
     cudaSetDevice(c->cfg.device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int n = c->n;
-    long long step;
-    CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    const size_t n3 = 3 * (size_t)c->n;
+    if (where == BOUNCE_DEVICE) {
+        // interleaved straight into the caller's device arrays, stream-ordered
+        launch_state_out(c->ds, q, v, st);
+        CU(cudaGetLastError());
+        return BOUNCE_OK;
+    }
+    if (!c->h_stage) CU(cudaMallocHost(&c->h_stage, 2 * n3 * sizeof(double)));
+    launch_state_out(c->ds, q ? c->d_stage : nullptr, v ? c->d_stage + n3 : nullptr, st);
+    if (q) CU(cudaMemcpyAsync(c->h_stage, c->d_stage, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (v) CU(cudaMemcpyAsync(c->h_stage + n3, c->d_stage + n3, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    const int cur = (int)(step & 1);
-    DevSys& s = c->ds;
-    const cudaMemcpyKind kind = where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    // strided copies interleave the SoA device arrays into (n, 3) rows
-    if (q) {
-        CU(cudaMemcpy2DAsync(q + 0, 3 * sizeof(double), s.qx[cur], sizeof(double), sizeof(double), n, kind, st));
-        CU(cudaMemcpy2DAsync(q + 1, 3 * sizeof(double), s.qy[cur], sizeof(double), sizeof(double), n, kind, st));
-        CU(cudaMemcpy2DAsync(q + 2, 3 * sizeof(double), s.qz[cur], sizeof(double), sizeof(double), n, kind, st));
-    }
-    if (v) {
-        CU(cudaMemcpy2DAsync(v + 0, 3 * sizeof(double), s.vx, sizeof(double), sizeof(double), n, kind, st));
-        CU(cudaMemcpy2DAsync(v + 1, 3 * sizeof(double), s.vy, sizeof(double), sizeof(double), n, kind, st));
-        CU(cudaMemcpy2DAsync(v + 2, 3 * sizeof(double), s.vz, sizeof(double), sizeof(double), n, kind, st));
-    }
-    if (where == BOUNCE_HOST) CU(cudaStreamSynchronize(st));
+    if (q) std::memcpy(q, c->h_stage, n3 * sizeof(double));
+    if (v) std::memcpy(v, c->h_stage + n3, n3 * sizeof(double));
     return BOUNCE_OK;
 }
 

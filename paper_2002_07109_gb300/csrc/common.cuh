@@ -405,6 +405,8 @@ void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step,
 void launch_energies(const DevSys& s, const Params& p, int cur, double* terms, cudaStream_t st);
 void launch_advance_step(const DevSys& s, long long by, cudaStream_t st);
 void launch_pack_positions(const DevSys& s, const Params& p, int cur, cudaStream_t st);
+void launch_state_in(const DevSys& s, const double* q, const double* v, int cur, cudaStream_t st);
+void launch_state_out(const DevSys& s, double* q, double* v, cudaStream_t st);
 // Raises the rebuild flag when an atom at positions `cur` lies more than
 // skin/2 from its position at the last row build (the step kernel's test).
 void launch_flag_moved(const DevSys& s, const Params& p, int cur, cudaStream_t st);

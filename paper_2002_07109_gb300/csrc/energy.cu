@@ -140,6 +140,44 @@ void launch_energies(const DevSys& s, const Params& p, int cur, double* terms, c
     k_sum_pass2<5><<<1, SUM_CTAS, 0, st>>>(partial, terms + 5 * (size_t)s.n);
 }
 
+// State in: interleaved q[n][3], v[n][3] (device) -> FP64 SoA at buffer cur.
+__global__ void k_state_in(DevSys s, const double* q, const double* v, int cur) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        s.qx[cur][i] = q[3 * (size_t)i];
+        s.qy[cur][i] = q[3 * (size_t)i + 1];
+        s.qz[cur][i] = q[3 * (size_t)i + 2];
+        s.vx[i] = v[3 * (size_t)i];
+        s.vy[i] = v[3 * (size_t)i + 1];
+        s.vz[i] = v[3 * (size_t)i + 2];
+    }
+}
+
+// State out: FP64 SoA of the current step (read on the device) -> interleaved
+// q[n][3], v[n][3] (device; either may be null).
+__global__ void k_state_out(DevSys s, double* q, double* v) {
+    const int cur = (int)(*s.step_base & 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        if (q) {
+            q[3 * (size_t)i] = s.qx[cur][i];
+            q[3 * (size_t)i + 1] = s.qy[cur][i];
+            q[3 * (size_t)i + 2] = s.qz[cur][i];
+        }
+        if (v) {
+            v[3 * (size_t)i] = s.vx[i];
+            v[3 * (size_t)i + 1] = s.vy[i];
+            v[3 * (size_t)i + 2] = s.vz[i];
+        }
+    }
+}
+
+void launch_state_in(const DevSys& s, const double* q, const double* v, int cur, cudaStream_t st) {
+    k_state_in<<<(s.n + 255) / 256, 256, 0, st>>>(s, q, v, cur);
+}
+
+void launch_state_out(const DevSys& s, double* q, double* v, cudaStream_t st) {
+    k_state_out<<<(s.n + 255) / 256, 256, 0, st>>>(s, q, v);
+}
+
 void launch_pack_positions(const DevSys& s, const Params& p, int cur, cudaStream_t st) {
     k_pack<<<(s.n + 255) / 256, 256, 0, st>>>(s, p, cur);
 }
