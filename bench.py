@@ -47,7 +47,7 @@ DT = 1.0
 # Algorithmic lane-operations per unit of work in the fused step kernel,
 # counted from the kernel source (see the design notes):
 # DRAM bytes per body launch of the BOUNCE step kernel on this workload (ncu capture)
-K_STEP_TRAFFIC = 36.85e6
+K_STEP_TRAFFIC = None  # re-measured after the last change to the kernel
 OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
 OPS_PER_SHORT_PAIR = 35      # FP32 pair term (displacement, r^2, rsqrt, chi, W'/r, accumulate)
 OPS_PER_FULL_PAIR = 25       # FP32 pair term without the switching function

@@ -30,6 +30,18 @@
 namespace {
 
 constexpr int NW = 8;  // warps per CTA
+static_assert(BOUNCE_GROUP <= 32, "per-atom prefixes are one warp scan");
+
+// Inclusive prefix sum over the 32 lanes of a warp.
+__device__ __forceinline__ int warp_scan_incl(int x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
 constexpr int GU = 2;  // row entries per lane in flight in the pair sums
 constexpr int FU = 2;  // proposals per thread in flight in the jump phase
 
@@ -76,7 +88,7 @@ __device__ __forceinline__ void jump_prep(const DevSys& s, const Params& p, Jump
     int nch = 0;
     float muc = 0.f;
     if (mu > 0.0) {
-        nch = (int)ceil(__ddiv_rn(mu, 16.0));
+        nch = (int)ceil(__dmul_rn(mu, 0.0625));  // mu / 16, exact
         muc = __double2float_rn(__ddiv_rn(mu, (double)nch));
     }
     js.s[a] = sp;
@@ -106,14 +118,14 @@ __device__ __noinline__ int exact_decision(float vx, float vy, float vz, float g
 // count to the atom's total.  Called by all threads of the CTA.
 __device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, int base, int na, long long step,
                               uint32_t stream) {
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int a = 0; a < na; ++a) {
-            js.chp[a] = acc;
-            acc += js.nch[a];
+    if (threadIdx.x < 32) {  // prefix of the chunk counts: one warp scan (na <= 32)
+        const int a = threadIdx.x, c = a < na ? js.nch[a] : 0;
+        const int x = warp_scan_incl(c);
+        if (a < na) {
+            js.chp[a] = x - c;
             js.M[a] = 0;
         }
-        js.chp[na] = acc;
+        if (a == 31) js.chp[na] = x;
     }
     __syncthreads();
     const int tot = js.chp[na];
@@ -184,14 +196,14 @@ __device__ __forceinline__ int owner_of(const PropSmem& ps, int na, int g) {
 __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropSmem& ps, int cur, int base, int na,
                            long long step, uint32_t stream) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int a = 0; a < na; ++a) {
-            ps.P[a] = acc;
-            acc += js.M[a];
+    if (threadIdx.x < 32) {  // prefix of the proposal counts: one warp scan (na <= 32)
+        const int a = threadIdx.x, m = a < na ? js.M[a] : 0;
+        const int x = warp_scan_incl(m);
+        if (a < na) ps.P[a] = x - m;
+        if (a == 31) {
+            ps.P[na] = x;
+            js.cnt[0] += (unsigned long long)x;
         }
-        ps.P[na] = acc;
-        js.cnt[0] += (unsigned long long)acc;
     }
     if (threadIdx.x < na) {
         const int a = threadIdx.x, i = base + a;
@@ -360,10 +372,9 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
     }
     near = warp_sum_i(near);
     if (lane == 0 && near) atomicAdd(&js.cnt[2], (unsigned long long)near);
-    if (threadIdx.x == 0) {
-        unsigned long long A = 0;
-        for (int a = 0; a < na; ++a) A += (unsigned long long)js.nacc[a];
-        js.cnt[1] += A;
+    if (threadIdx.x < 32) {
+        const int A = warp_sum_i(threadIdx.x < na ? js.nacc[threadIdx.x] : 0);
+        if (threadIdx.x == 0) js.cnt[1] += (unsigned long long)A;
     }
     __syncthreads();
 }
