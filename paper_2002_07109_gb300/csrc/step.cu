@@ -311,7 +311,7 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
             for (int gb = lo; gb < hi; gb += 32) {
                 const int t = gb - c0 + lane;
                 const bool act = gb + lane < hi;
-                float gx = 0.f, gy = 0.f, gz = 0.f, thr = 0.f, err = 0.f, sl = 0.f;
+                float gx = 0.f, gy = 0.f, gz = 0.f, g2 = 1.f, thr = 0.f, hi = 0.f, lo = 0.f, tie = 0.f;
                 uint32_t x1 = 0, x2 = 0;
                 if (act) {
                     gx = ps.gx[t];
@@ -319,18 +319,22 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                     gz = ps.gz[t];
                     x1 = ps.x1[t];
                     x2 = ps.x2[t];
-                    sl = js.slt[a][x2 & 3u];  // ||v|| times the bound of the partner's type
+                    const float sl = js.slt[a][x2 & 3u];  // ||v|| times the bound of the partner's type
                     thr = u24(x1) * sl;
+                    g2 = gx * gx + gy * gy + gz * gz;
                     // FP32 decision error: |fl(v.F) - v.F| <= 4e-6 sum_c |v_c F_c| <= 4e-6 ||v|| ||F||
                     // (the chain's FP32 ||v|| stays within 1e-4 of the FP64 one, reflections keep it);
                     // U and ||v|| L within 2.4e-7 ||v|| L.  Fixed along the chain.
-                    err = 4e-6f * (thr + 1.0001f * sp_f * sqrtf(gx * gx + gy * gy + gz * gz)) + 2.4e-7f * sl;
+                    const float err = 4e-6f * (thr + 1.0001f * sp_f * sqrtf(g2)) + 2.4e-7f * sl;
+                    hi = thr + err;
+                    lo = thr - err;
+                    tie = 1e-6f * sl;
                 }
                 int start = 0;
                 while (true) {
                     // decide with the current velocity: accept iff U ||v|| L < v . F
                     const float af = vx * gx + vy * gy + vz * gz;
-                    int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
+                    int dec = (hi < af) ? 1 : ((lo > af) ? 0 : 2);
                     const bool live = act && lane >= start;
                     if (__any_sync(0xffffffffu, live && dec == 2)) {
                         if (live && dec == 2) {
@@ -341,12 +345,12 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                     const uint32_t acc = __ballot_sync(0xffffffffu, live && dec == 1);
                     const int f = acc ? __ffs(acc) - 1 : 32;
                     // near ties among the decisions that stand (lanes start..f)
-                    if (live && lane <= f && fabsf(thr - af) < 1e-6f * sl) ++near;
+                    if (live && lane <= f && fabsf(thr - af) < tie) ++near;
                     if (!acc) break;
+                    // reflect on the accepted proposal: its v.F and ||F||^2 from its lane
                     const float fx = __shfl_sync(0xffffffffu, gx, f), fy = __shfl_sync(0xffffffffu, gy, f),
                                 fz = __shfl_sync(0xffffffffu, gz, f);
-                    const float aa = vx * fx + vy * fy + vz * fz;
-                    const float ff = fx * fx + fy * fy + fz * fz;
+                    const float aa = __shfl_sync(0xffffffffu, af, f), ff = __shfl_sync(0xffffffffu, g2, f);
                     const float coef = __fdividef(aa + aa, ff);
                     vx -= coef * fx;
                     vy -= coef * fy;
