@@ -48,3 +48,33 @@ def test_replica_arguments_are_checked():
     with pytest.raises(bounce.BounceError):
         b.set_replicas(np.array([0, sysb.n_atoms - 3]), [1])          # does not cover all atoms
     b.close()
+
+
+def test_full_size_batch_sampled():
+    """The 256-replica batch (64-1,024 molecules each, seeded sizes, one seed
+    per replica) at full size: one BOUNCE step of the whole batch in shared
+    launches; three sampled replicas run alone reproduce their part bit for
+    bit."""
+    from paper_2002_07109_gb300.water import replica_sizes
+    sizes = replica_sizes(256, 64, 1024, seed=0)
+    reps = [water_droplet_molecules(int(n), seed=r) for r, n in enumerate(sizes)]
+    seeds = [1000 + r for r in range(len(reps))]
+    sysb, off = concat_systems(reps)
+    cfg = dict(r_on=4.0, r_off=5.0, max_neighbors=3 * int(sizes.max()), pair_bounds=True)
+    b = bounce.from_system(sysb, seed=1, **cfg)
+    b.set_replicas(off, seeds)
+    b.set_state(sysb.q, sysb.v, step=0)
+    b.run(1, bounce.BOUNCE)
+    qb, vb = b.get_state()
+    eb = b.energies()
+    b.close()
+    assert eb["proposals"] > 100 * sysb.n_atoms
+    for r in (0, int(np.argmax(sizes)), len(reps) - 1):
+        s = reps[r]
+        c = bounce.from_system(s, seed=seeds[r], **cfg)
+        c.set_state(s.q + np.array([r * 500.0, 0.0, 0.0]), s.v, step=0)
+        c.run(1, bounce.BOUNCE)
+        q, v = c.get_state()
+        c.close()
+        assert np.array_equal(qb[off[r]:off[r + 1]], q), r
+        assert np.array_equal(vb[off[r]:off[r + 1]], v), r
