@@ -400,3 +400,42 @@ def test_respa1_rejects_partial_outer_steps():
     with pytest.raises(bounce.BounceError):
         ctx.run(6, bounce.BOUNCE_RESPA1)
     ctx.close()
+
+
+def test_full_size_box_pme_sampled():
+    """The 32,768-molecule periodic box (98,304 atoms, edge 99.3 A): Ewald
+    direct erfc (beta 0.35) within 9 A, SPME 96^3 of order 5, per-type-pair
+    bounds.  Rows, the F_0 gradient and the reciprocal gradient (SPME plus the
+    same-molecule removal) on a sample of atoms against the oracle."""
+    from oracle import ewald
+    from oracle.forcefield import (pair_gradients, bonded_gradients, pair_gradient_magnitudes,
+                                   bonded_gradient_magnitudes)
+    from oracle.neighbors import to_pairs
+    s = water_box(32, seed=0)
+    cfg = dict(r_on=4.0, r_off=5.0, r_cut=9.0, skin=1.0, ewald_beta=0.35, pme_grid=(96, 96, 96), pme_order=5,
+               max_neighbors=1024, pair_bounds=True)
+    ctx = bounce.from_system(s, seed=1, **cfg)
+    ctx.set_state(s.q, s.v, step=0)
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(s.n_atoms, 120, replace=False))
+    ref_rows = oracle_rows(s.q, s.molecule, 10.0, s.box, atoms=sample)
+    got = ctx.rows()
+    from oracle.integrate import typed_rows
+    ref_typed, _ = typed_rows(ref_rows, s.type, 2)
+    for a, i in enumerate(sample):
+        assert np.array_equal(got[i], ref_typed[a]), i
+    p = Params(r_on=4.0, r_off=5.0, r_cut=9.0, ewald_beta=0.35, box=s.box, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps,
+               pme_grid=(96, 96, 96), pme_order=5)
+    ii, jj = to_pairs(ref_rows, sample)
+    g = ctx.gradient(bounce.GRAD_SHORT)
+    ref = pair_gradients(s.q, s.charge, s.type, ii, jj, p, "short") + bonded_gradients(
+        s.q, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0, s.box)
+    scale = pair_gradient_magnitudes(s.q, s.charge, s.type, ii, jj, p, "short") + bonded_gradient_magnitudes(
+        s.q, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0, s.box)
+    _check_sum(g[sample], ref[sample], scale[sample])
+    gr = ctx.gradient(bounce.GRAD_RECIP)
+    _, g_rec = ewald.spme_recip(s.q, s.charge, s.box, 0.35, (96, 96, 96), 5)
+    _, g_exc = ewald.exclusion(s.q, s.charge, ewald.molecule_pairs(s.molecule), 0.35, s.box)
+    sc = np.linalg.norm(g_rec, axis=1) + np.linalg.norm(g_exc, axis=1)
+    _check_sum(gr[sample], (g_rec + g_exc)[sample], sc[sample])
+    ctx.close()
