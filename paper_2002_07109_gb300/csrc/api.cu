@@ -749,14 +749,26 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     int dev = c->cfg.device, optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t words = (size_t)(n + 31) / 32;
-    // per warp: the long-row bitmaps (one per partner type with per-type-pair
-    // bounds), the short-row bitmap (each rounded to 16 bytes) and 3 x 128
-    // ints of cell-row runs
+    // Row builder.  Per warp of the warp-per-atom kernel: the long-row
+    // bitmaps (one per partner type with per-type-pair bounds) and the
+    // short-row bitmap, each rounded to 16 bytes, and 3 x 128 ints of
+    // cell-row runs.  When that exceeds 8 KB (large systems: the bitmaps span
+    // all atoms) the CTA-per-atom kernel runs instead, with one such set per
+    // CTA plus a touched flag per 32-word group, a count per (bitmap, group)
+    // and the list of touched groups.
     const size_t nbm = (c->cfg.pair_bounds ? (size_t)c->n_types : 1) + 1;
-    const size_t per_warp = nbm * ((words * 4 + 15) / 16 * 16) + 3 * 128 * 4;
-    if (per_warp > (size_t)optin) return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for the row builder bitmap");
-    c->bitmap_warps = (int)std::min<size_t>(8, (size_t)optin / per_warp);
-    c->bitmap_bytes = per_warp * c->bitmap_warps;
+    const size_t per_warp = nbm * ((words + 3) / 4 * 16) + 3 * 128 * 4;
+    const size_t groups = (words + 31) / 32;
+    const size_t per_cta = nbm * ((words + 3) / 4 * 16) + (groups + 15) / 16 * 16 + (nbm * groups + 3) / 4 * 16 +
+                           (groups + 3) / 4 * 16 + 3 * 128 * 4;
+    if (per_warp <= 8192) {
+        c->bitmap_warps = 8;
+        c->bitmap_bytes = per_warp * 8;
+    } else {
+        if (per_cta > (size_t)optin) return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for the row builder bitmap");
+        c->bitmap_warps = 0;
+        c->bitmap_bytes = per_cta;
+    }
     nlist_set_smem_limit(c->bitmap_bytes);
     c->have_topo = true;
     return BOUNCE_OK;

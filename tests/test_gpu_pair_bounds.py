@@ -138,3 +138,22 @@ def test_typed_rows_need_short_enough_rows():
     s = water_droplet(2, seed=0)
     with pytest.raises(bounce.BounceError):
         bounce.from_system(s, pair_bounds=True, max_neighbors=70000)
+
+
+@pytest.mark.parametrize("n_mol, typed", [(7000, True), (9000, False)])
+def test_rows_large_system(n_mol, typed):
+    """21,000 / 27,000 atoms: the row builder's CTA-per-atom path (its bitmaps
+    over all atoms exceed the warp-per-atom budget), with and without
+    per-type-pair bounds; every row bit-exact."""
+    from oracle.neighbors import rows_cell_list
+    s = water_droplet_molecules(n_mol, seed=3)
+    ctx = bounce.from_system(s, seed=2, pair_bounds=typed, r_on=4.0, r_off=5.0, r_cut=9.0, skin=1.0)
+    ctx.set_state(s.q, s.v, step=0)
+    got = ctx.rows()
+    ref = rows_cell_list(s.q, s.molecule, 10.0)
+    if typed:
+        ref, _ = typed_rows(ref, s.type, 2)
+    assert len(got) == len(ref)
+    for i, (a, b) in enumerate(zip(got, ref)):
+        assert np.array_equal(a, b), i
+    ctx.close()
