@@ -308,6 +308,7 @@ def our_arm(args):
         "clocks": clk,
     }
     line["long_run"] = long_run(s, q0, v0, cfg, rank, stream, sh)
+    line["pbc_box"] = pbc_box(rank, stream, sh)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(s)
         print(json.dumps(line))
@@ -358,6 +359,68 @@ def long_run(s, q0, v0, cfg, rank, stream, sh, n_steps=1000, chunk=100):
         if done:
             r.update({"ns_per_day": round(ns_per_day(done, ms / 1e3), 2), "pe_per_molecule": round(float(np.mean(pe)), 4),
                       "temperature_K": round(float(np.mean(T)), 1)})
+        if err:
+            r["stopped"] = err
+        out[name] = r
+    return out
+
+
+def pbc_box(rank, stream, sh, n_steps=960, chunk=48):
+    """The periodic box of 32,768 water molecules (98,304 atoms, edge 99.3 A):
+    Ewald direct erfc (beta 0.35) and LJ within 9 A, SPME 96^3 of order 5,
+    jumps beyond a 7.5-8.5 A switch (per-type-pair bounds), 1 fs, friction
+    1/ps.  From a BAOAB-equilibrated state, graph-captured runs of n_steps
+    after one warm-up chunk: BAOAB (SPME every step), BOUNCE-RESPA (SPME on
+    the 2 fs outer step) and BOUNCE-RESPA1 (short-range pairs on 2 fs, SPME on
+    6 fs).  ns/day over the chunks (CUDA events), and the means of the
+    potential energy per molecule and of the temperature after every chunk."""
+    import torch
+    from paper_2002_07109_gb300 import bounce
+    from paper_2002_07109_gb300.water import water_box
+    s = water_box(32, seed=rank)
+    n_mol = s.n_atoms // 3
+    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=1.0, dt=1.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
+               pme_order=5, max_neighbors=1024, max_short=640, device=torch.cuda.current_device())
+    eq = bounce.from_system(s, seed=500 + rank, gamma=0.05, **cfg)
+    eq.set_state(s.q, s.v)
+    eq.run(600, bounce.BAOAB, stream=sh)
+    q0, v0 = eq.get_state(stream=sh)
+    eq.close()
+    out = {"workload": "32,768-molecule periodic water box (98,304 atoms), erfc beta 0.35, r_c 9 A, SPME 96^3 order 5, "
+                       "switch 7.5-8.5 A, 1 fs, friction 1/ps"}
+    arms = (("baoab", bounce.BAOAB, dict(pair_bounds=False)),
+            ("bounce_respa", bounce.BOUNCE_RESPA, dict(pair_bounds=True, respa_m=2)),
+            ("bounce_respa1", bounce.BOUNCE_RESPA1, dict(pair_bounds=True, respa_m=2, respa_m2=3)))
+    for name, integ, extra in arms:
+        ctx = bounce.from_system(s, seed=21 + rank, **cfg, **extra)
+        ctx.set_state(q0, v0, step=0)
+        ms, pe, T, done, err = 0.0, [], [], 0, None
+        try:
+            ctx.run(chunk, integ, stream=sh)
+            torch.cuda.synchronize()
+            ctx.reset_counters(stream=sh)
+            for _ in range(n_steps // chunk):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.run(chunk, integ, stream=sh)
+                b.record(stream)
+                b.synchronize()
+                ms += a.elapsed_time(b)
+                done += chunk
+                e = ctx.energies(stream=sh)
+                pe.append(e["potential"] / n_mol)
+                T.append(e["temperature"])
+            props = ctx.energies(stream=sh)["proposals"]
+        except Exception as ex:  # a blown-up state is reported, not timed
+            err = str(ex).split("(")[0].strip()
+        ctx.close()
+        r = {"steps": done}
+        if done:
+            r.update({"ns_per_day": round(ns_per_day(done, ms / 1e3), 2), "pe_per_molecule": round(float(np.mean(pe)), 4),
+                      "temperature_K": round(float(np.mean(T)), 1)})
+            if integ != bounce.BAOAB and err is None:
+                r["proposals_per_atom_step"] = round(props / (done * s.n_atoms), 4)
         if err:
             r["stopped"] = err
         out[name] = r
