@@ -44,10 +44,12 @@ WINDOW = 5
 N_SIDE = 16                  # 16^3 = 4096 molecules
 R_CUT, R_ON, R_OFF, SKIN = 12.0, 4.0, 5.0, 1.0
 DT = 1.0
+# DRAM bytes (read + write) of one body launch of the BOUNCE step kernel with
+# per-type-pair bounds on the 12,288-atom lattice droplet (82 proposals per
+# atom-step; the timed windows run ~85): one ncu capture of the current kernel
+K_STEP_TRAFFIC = 36794368 + 30464
 # Algorithmic lane-operations per unit of work in the fused step kernel,
-# counted from the kernel source (see the design notes):
-# DRAM bytes per body launch of the BOUNCE step kernel on this workload (ncu capture)
-K_STEP_TRAFFIC = None  # re-measured after the last change to the kernel
+# counted from the kernel source:
 OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
 OPS_PER_SHORT_PAIR = 35      # FP32 pair term (displacement, r^2, rsqrt, chi, W'/r, accumulate)
 OPS_PER_FULL_PAIR = 25       # FP32 pair term without the switching function
@@ -299,7 +301,7 @@ def our_arm(args):
         "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / peak, 4), "traffic": K_STEP_TRAFFIC,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one body launch of "
-                                       "k_step<BOUNCE> on this droplet (per-type-pair bounds)",
+                                       "k_step<BOUNCE> on the same-size lattice droplet (per-type-pair bounds)",
                      "kernel": "k_step<BOUNCE> (fused F_0 + 2 jump half-steps + B A O A)",
                      "baoab_kernel_frac": round(ach_a / peak, 4)},
         "e2e": {"value": round(e2e_val, 4), "unit": "ns/day", "h2d_bytes_per_step": h2d * len(windows) // steps,
