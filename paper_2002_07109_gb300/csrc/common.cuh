@@ -293,6 +293,36 @@ __device__ __forceinline__ void pair_dW_split(const Params& p, float r2, float q
 }
 
 // Switching function chi(r) (quintic smoothstep on [r', r'']).
+__device__ __forceinline__ float chi_of(const Params& p, float r);
+
+// W'/r of the F_0 share of one pair: (1 - chi) times the switched part plus
+// the fixed part (pair_dW_split).  The switched part, LJ included, is not
+// evaluated at or beyond r'', where 1 - chi = 0; the result equals
+// sw (1 - chi) + fixed there too.
+__device__ __forceinline__ float pair_dW_f0(const Params& p, float r2, float qq, int tp) {
+    const float ir = rsqrt_nr(r2);
+    const float ir2 = ir * ir;
+    const float r = r2 * ir;
+    float wc;
+    if (p.ebeta > 0.f) {
+        const float br = p.ebeta * r;
+        wc = -qq * (erfcf(br) * ir2 + p.e2b_sqrtpi * __expf(-br * br) * ir) * ir;
+    } else {
+        wc = -qq * ir2 * ir;
+    }
+    const float fixed = p.coul_jump ? 0.f : wc;
+    if (!(r < p.r_off)) return fixed;
+    float wl = 0.f;
+    const float c12 = p.c12[tp];
+    if (c12 != 0.f) {
+        const float ir6 = ir2 * ir2 * ir2;
+        wl = -((12.f * c12 * ir6 - 6.f * p.c6[tp]) * ir6 * ir2);
+    }
+    const float sw = p.coul_jump ? wc + wl : wl;
+    return sw * (1.f - chi_of(p, r)) + fixed;
+}
+
+// Switching function chi(r) (quintic smoothstep on [r', r''])
 __device__ __forceinline__ float chi_of(const Params& p, float r) {
     if (p.chi_step) return r >= p.r_off ? 1.f : 0.f;
     float s = fminf(fmaxf((r - p.r_on) * p.inv_span, 0.f), 1.f);

@@ -89,7 +89,7 @@ __device__ __forceinline__ void jump_prep(const DevSys& s, const Params& p, Jump
     float muc = 0.f;
     if (mu > 0.0) {
         nch = (int)ceil(__dmul_rn(mu, 0.0625));  // mu / 16, exact
-        muc = __double2float_rn(__ddiv_rn(mu, (double)nch));
+        muc = __double2float_rn(nch == 1 ? mu : __ddiv_rn(mu, (double)nch));
     }
     js.s[a] = sp;
     js.sl[a] = __double2float_rn(__dmul_rn(sp, Ls));
@@ -196,19 +196,23 @@ __device__ __forceinline__ int owner_of(const PropSmem& ps, int na, int g) {
 __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropSmem& ps, int cur, int base, int na,
                            long long step, uint32_t stream) {
     const int lane = threadIdx.x & 31;
+    int any = 0;  // the CTA has proposals (warp 0 knows it from the scan)
     if (threadIdx.x < 32) {  // prefix of the proposal counts: one warp scan (na <= 32)
         const int a = threadIdx.x, m = a < na ? js.M[a] : 0;
         const int x = warp_scan_incl(m);
+        any = __shfl_sync(0xffffffffu, x, 31) > 0;
         if (a < na) ps.P[a] = x - m;
         if (a == 31) {
             ps.P[na] = x;
             js.cnt[0] += (unsigned long long)x;
         }
+        if (a < na) {
+            js.nacc[a] = 0;
+            js.dv[a][0] = js.dv[a][1] = js.dv[a][2] = 0.f;
+        }
     }
-    if (threadIdx.x < na) {
+    if (threadIdx.x < na && any) {
         const int a = threadIdx.x, i = base + a;
-        js.nacc[a] = 0;
-        js.dv[a][0] = js.dv[a][1] = js.dv[a][2] = 0.f;
         ps.ahi[a] = s.phi[cur][i];
         ps.alo[a] = s.plo[cur][i];
         ps.an[a] = s.nlong[i];
@@ -228,6 +232,7 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
     }
     __syncthreads();
     const int tot = ps.P[na];
+    if (tot == 0) return;  // no proposals: the velocity increments stay zero
     int near = 0;
     for (int c0 = 0; c0 < tot; c0 += PC) {
         const int cn = min(PC, tot - c0);
@@ -416,12 +421,13 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
             const float3 d = pair_disp(p, hi, lo, hj[u], lj[u]);
             const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
             if (inside_cut(s, p, cur, i, j[u], r2)) {
-                float sw, fixed, r;
-                pair_dW_split(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]), sw, fixed, r);
-                float w = sw + fixed;
-                if (part != 0 && part != 5) {
-                    const float c = chi_of(p, r);
-                    w = part == 2 ? sw * c : sw * (1.f - c) + fixed;
+                float w;
+                if (part == 1 || part == 3) {
+                    w = pair_dW_f0(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]));
+                } else {
+                    float sw, fixed, r;
+                    pair_dW_split(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]), sw, fixed, r);
+                    w = part == 2 ? sw * chi_of(p, r) : sw + fixed;
                 }
                 gx += w * d.x;
                 gy += w * d.y;
