@@ -63,9 +63,10 @@ WORKLOAD = ("BOUNCE (LJ beyond the 4-5 A switch on jumps with per-type-pair boun
 N_SIDE = 16                  # 16^3 = 4096 molecules
 R_CUT, R_ON, R_OFF, SKIN = 12.0, 4.0, 5.0, 1.0
 DT = 1.0
-# DRAM bytes (read + write) of one body launch of the BOUNCE step kernel on
-# this droplet and split (ncu)
-K_STEP_TRAFFIC = None
+# DRAM bytes (read + write) of one body launch of the BOUNCE step kernel with
+# this split on the same-size droplet at its lattice start (ncu, cold caches;
+# ~670 row entries per atom there, ~920 after equilibration)
+K_STEP_TRAFFIC = 36363008 + 14080
 # Algorithmic lane-operations per unit of work in the fused step kernel,
 # counted from the kernel source:
 OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
@@ -346,7 +347,7 @@ def our_arm(args):
         "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / peak, 4), "traffic": K_STEP_TRAFFIC,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one body launch of "
-                                       "k_step<BOUNCE> on this droplet and split",
+                                       "k_step<BOUNCE> with this split on the same-size lattice droplet",
                      "kernel": "k_step<BOUNCE> (fused F_0 + 2 jump half-steps + B A O A)",
                      "baoab_kernel_frac": round(ach_a / peak, 4)},
         "e2e": {"value": round(e2e_val, 4), "unit": "ns/day", "h2d_bytes_per_step": h2d * b["windows"] // steps,
