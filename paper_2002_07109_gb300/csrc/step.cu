@@ -42,7 +42,6 @@ __device__ __forceinline__ int warp_scan_incl(int x) {
     }
     return x;
 }
-constexpr int GU = 2;  // row entries per lane in flight in the pair sums
 constexpr int FU = 2;  // proposals per thread in flight in the jump phase
 
 struct JumpSmem {
@@ -401,39 +400,42 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
     const int n = part == 4 ? 0 : (shortrows ? s.nshort[i] : s.nlong[i]);
     const int* row = shortrows ? s.srows + (size_t)i * s.caps : s.rows + (size_t)i * s.cap;
     float gx = 0.f, gy = 0.f, gz = 0.f;
-    // GU row entries per lane per pass: their index and position loads are
-    // issued back to back before any is used; each lane still adds its pairs
-    // in row order.
-    for (int k0 = lane; k0 < n; k0 += GU * 32) {
-        int j[GU];
-        float4 hj[GU], lj[GU];
-#pragma unroll
-        for (int u = 0; u < GU; ++u) j[u] = k0 + 32 * u < n ? row[k0 + 32 * u] : -1;
-#pragma unroll
-        for (int u = 0; u < GU; ++u)
-            if (j[u] >= 0) {
-                hj[u] = s.phi[cur][j[u]];
-                lj[u] = s.plo[cur][j[u]];
-            }
-#pragma unroll
-        for (int u = 0; u < GU; ++u) {
-            if (j[u] < 0) continue;
-            const float3 d = pair_disp(p, hi, lo, hj[u], lj[u]);
-            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-            if (inside_cut(s, p, cur, i, j[u], r2)) {
-                float w;
-                if (part == 1 || part == 3) {
-                    w = pair_dW_f0(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]));
-                } else {
-                    float sw, fixed, r;
-                    pair_dW_split(p, r2, p.kcoul * qi * hj[u].w, ti * BOUNCE_MAXT + type_of(lj[u]), sw, fixed, r);
-                    w = part == 2 ? sw * chi_of(p, r) : sw + fixed;
-                }
-                gx += w * d.x;
-                gy += w * d.y;
-                gz += w * d.z;
-            }
+    // software pipeline over the lane's row entries lane, lane + 32, ...: the
+    // index two entries ahead and the position one entry ahead are in flight
+    // while an entry is evaluated; each lane adds its pairs in row order
+    int jc = lane < n ? row[lane] : -1;
+    int jn = lane + 32 < n ? row[lane + 32] : -1;
+    float4 hc = make_float4(0.f, 0.f, 0.f, 0.f), lc = hc;
+    if (jc >= 0) {
+        hc = s.phi[cur][jc];
+        lc = s.plo[cur][jc];
+    }
+    for (int k0 = lane; k0 < n; k0 += 32) {
+        const int jnn = k0 + 64 < n ? __ldg(row + k0 + 64) : -1;
+        float4 hn = hc, ln = lc;
+        if (jn >= 0) {
+            hn = s.phi[cur][jn];
+            ln = s.plo[cur][jn];
         }
+        const float3 d = pair_disp(p, hi, lo, hc, lc);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        if (inside_cut(s, p, cur, i, jc, r2)) {
+            float w;
+            if (part == 1 || part == 3) {
+                w = pair_dW_f0(p, r2, p.kcoul * qi * hc.w, ti * BOUNCE_MAXT + type_of(lc));
+            } else {
+                float sw, fixed, r;
+                pair_dW_split(p, r2, p.kcoul * qi * hc.w, ti * BOUNCE_MAXT + type_of(lc), sw, fixed, r);
+                w = part == 2 ? sw * chi_of(p, r) : sw + fixed;
+            }
+            gx += w * d.x;
+            gy += w * d.y;
+            gz += w * d.z;
+        }
+        jc = jn;
+        jn = jnn;
+        hc = hn;
+        lc = ln;
     }
     if (part == 0 || part == 1 || part == 4) {
         for (int t = s.bt_off[i] + lane; t < s.bt_off[i + 1]; t += 32) {
