@@ -111,12 +111,45 @@ __device__ __noinline__ int exact_decision(float vx, float vy, float vz, float g
     return td < ad ? 1 : 0;
 }
 
+// Poisson(mu_c) by sequential search of the FP32 CDF with uniform u (same
+// operations as poisson_invert_f32); inv[k] = 1/k.
+__device__ __forceinline__ int poisson_chunk(float u, float mu_c, const float* inv) {
+    float pk = expneg_f32(mu_c), cdf = pk;
+    int k = 0;
+    while (u > cdf && k < 128) {
+        ++k;
+        const float q = __fmul_rn(__fmul_rn(pk, mu_c), inv[k]);
+        const float cn = __fadd_rn(cdf, q);
+        if (cn == cdf) break;
+        pk = q;
+        cdf = cn;
+    }
+    return k;
+}
+
 // Poisson counts of the CTA's atoms (one half step): every thread takes
 // whole chunks (chunk c of atom a inverts Poisson(mu_c) with the uniform of
 // Philox slot 0x80000000 | c), one chunk per thread at a time, and adds its
 // count to the atom's total.  Called by all threads of the CTA.
 __device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, int base, int na, long long step,
                               uint32_t stream) {
+    // every atom with at most one chunk (mu <= 16, the usual case): lane a of
+    // warp 0 inverts atom a's chunk, and the prefix scan of jump_phase (same
+    // warp) follows without a CTA barrier.  Every warp takes this decision
+    // from the chunk counts, which a barrier has published.
+    const int lane = threadIdx.x & 31;
+    if (__all_sync(0xffffffffu, lane >= na || js.nch[lane] <= 1)) {
+        if (threadIdx.x < na) {
+            int k = 0;
+            if (js.nch[lane] == 1) {
+                const uint4 x = rng_atom(s, p, BOUNCE_POISSON_SLOT, base + lane, step, stream);
+                k = poisson_chunk(u24(x.x), js.muc[lane], js.inv);
+            }
+            js.M[lane] = k;
+        }
+        __syncwarp();
+        return;
+    }
     if (threadIdx.x < 32) {  // prefix of the chunk counts: one warp scan (na <= 32)
         const int a = threadIdx.x, c = a < na ? js.nch[a] : 0;
         const int x = warp_scan_incl(c);
@@ -137,19 +170,7 @@ __device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, in
         }
         const int c = t - js.chp[lo];
         const uint4 x = rng_atom(s, p, BOUNCE_POISSON_SLOT | (uint32_t)c, base + lo, step, stream);
-        // sequential search of the FP32 CDF (same operations as poisson_invert_f32)
-        const float u = u24(x.x), mu_c = js.muc[lo];
-        float pk = expneg_f32(mu_c), cdf = pk;
-        int k = 0;
-        while (u > cdf && k < 128) {
-            ++k;
-            const float q = __fmul_rn(__fmul_rn(pk, mu_c), js.inv[k]);
-            const float cn = __fadd_rn(cdf, q);
-            if (cn == cdf) break;
-            pk = q;
-            cdf = cn;
-        }
-        atomicAdd(&js.M[lo], k);
+        atomicAdd(&js.M[lo], poisson_chunk(u24(x.x), js.muc[lo], js.inv));
     }
     __syncthreads();
 }
@@ -165,7 +186,9 @@ struct PropSmem {
     int an[BOUNCE_GROUP];          // their candidate-row lengths
     uint32_t acum[BOUNCE_GROUP][BOUNCE_MAXT + 1];  // typed rows: cumulative weights C_b (C_T = W_i)
     int ast[BOUNCE_GROUP][BOUNCE_MAXT];    // typed rows: start of each type group
-    int next;                      // next atom to take in the chain pass
+    int alist[BOUNCE_GROUP];       // atoms with proposals in the pass
+    int nlist;
+    int next;                      // next entry of alist to take in the chain pass
 };
 
 // Flattened proposal g of the CTA -> (atom a, slot k = g - P[a] + 1).
@@ -297,15 +320,24 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
                 ps.gz[t] = gz;
             }
         }
-        if (threadIdx.x == 0) ps.next = 0;
+        if (threadIdx.x < 32) {  // the atoms with proposals in this pass, in order
+            const int a = threadIdx.x;
+            const bool has = a < na && max(ps.P[a], c0) < min(ps.P[a + 1], c0 + cn);
+            const unsigned b = __ballot_sync(0xffffffffu, has);
+            if (has) ps.alist[__popc(b & ((1u << a) - 1u))] = a;
+            if (a == 0) {
+                ps.nlist = __popc(b);
+                ps.next = 0;
+            }
+        }
         __syncthreads();
         for (;;) {
-            int a = 0;
-            if (lane == 0) a = atomicAdd(&ps.next, 1);
-            a = __shfl_sync(0xffffffffu, a, 0);
-            if (a >= na) break;
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&ps.next, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= ps.nlist) break;
+            const int a = ps.alist[k];
             const int lo = max(ps.P[a], c0), hi = min(ps.P[a + 1], c0 + cn);
-            if (lo >= hi) continue;
             const int ti = s.type[base + a];
             const double sp = js.s[a];
             const float sp_f = __double2float_rn(sp);
