@@ -422,6 +422,33 @@ __device__ __forceinline__ float3 bonded_grad(const Params& p, const DevSys& s, 
     return g;
 }
 
+// Programmatic dependent launch of the per-step kernel chain (row-rebuild
+// gates, step kernel, step counter): a kernel launched with launch_chained
+// may be scheduled while its predecessor in the stream still runs.  It waits
+// here until the predecessor has completed and its writes are visible, before
+// reading anything, and then lets its own successor be scheduled.  Without a
+// programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Launchers implemented in the .cu files.
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
                     cudaStream_t st);

@@ -27,7 +27,12 @@ namespace {
 constexpr int RANGE_MAX = 128;  // cell-row runs per atom (<= 2 (2*3+1)^2 = 98)
 constexpr int ROWS_NT = 256;    // threads per CTA of the row builder
 
-__device__ __forceinline__ bool pending(const DevSys& s, int force) { return force || *s.rebuild; }
+// Entry of a gated rebuild kernel: after its predecessor in the chain, is a
+// rebuild due (or forced)?
+__device__ __forceinline__ bool pending(const DevSys& s, int force) {
+    chain_enter();
+    return force || *s.rebuild;
+}
 
 __device__ __forceinline__ void cell_of(const DevSys& s, const Params& p, float4 hi, int& cx, int& cy, int& cz) {
     if (p.periodic) {
@@ -636,20 +641,21 @@ void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, 
     const int f = force ? 1 : 0;
     if (s.rep_of) {
         const int wpb = 8;
-        k_rows_batch<<<(s.n + wpb - 1) / wpb, wpb * 32, 0, st>>>(s, p, step_off, f);
+        launch_chained(k_rows_batch, (s.n + wpb - 1) / wpb, wpb * 32, 0, st, s, p, step_off, f);
         return;
     }
     const int tb = 1024;
     const int gb = (s.n + tb - 1) / tb;
-    k_cells_count<<<gb, tb, 0, st>>>(s, p, step_off, f);
-    k_cells_scatter<<<gb, tb, 0, st>>>(s, p, step_off, f);
-    if (bitmap_warps > 0) {  // warp per atom
+    launch_chained(k_cells_count, gb, tb, 0, st, s, p, step_off, f);
+    launch_chained(k_cells_scatter, gb, tb, 0, st, s, p, step_off, f);
+    if (bitmap_warps > 0) {  // warp per atom, a grid-stride loop over one wave of CTAs
         const int words = (int)(bitmap_bytes / 4 / bitmap_warps);
-        const int blocks = (s.n + bitmap_warps - 1) / bitmap_warps;
-        k_rows_warp<<<blocks, bitmap_warps * 32, bitmap_bytes, st>>>(s, p, step_off, f, words);
+        const int per_sm = std::max(1, std::min(8, (int)((227u << 10) / std::max<size_t>(bitmap_bytes, 1))));
+        const int blocks = std::min((s.n + bitmap_warps - 1) / bitmap_warps, 152 * per_sm);
+        launch_chained(k_rows_warp, blocks, bitmap_warps * 32, bitmap_bytes, st, s, p, step_off, f, words);
     } else {  // CTA per atom, a grid-stride loop over a GPU-filling grid (an idle launch stays small)
         const int blocks = std::min(s.n, 152 * 8);
-        k_rows_cta<<<blocks, ROWS_NT, bitmap_bytes, st>>>(s, p, step_off, f);
+        launch_chained(k_rows_cta, blocks, ROWS_NT, bitmap_bytes, st, s, p, step_off, f);
     }
 }
 

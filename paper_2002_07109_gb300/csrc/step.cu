@@ -498,6 +498,7 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
     __shared__ PropSmem ps;
     __shared__ int sBoff[BOUNCE_GROUP + 1];
     __shared__ unsigned long long sPairs;
+    chain_enter();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = blockIdx.x * BOUNCE_GROUP;
     const int na = min(BOUNCE_GROUP, s.n - base);
@@ -715,7 +716,10 @@ __global__ void k_gradient(DevSys s, Params p, int part, int cur, double* out) {
     }
 }
 
-__global__ void k_advance(DevSys s, long long by) { *const_cast<long long*>(s.step_base) += by; }
+__global__ void k_advance(DevSys s, long long by) {
+    chain_enter();
+    *const_cast<long long*>(s.step_base) += by;
+}
 
 }  // namespace
 
@@ -723,8 +727,8 @@ void launch_step(const DevSys& s, const Params& p, int integrator, int variant, 
                  double hout, cudaStream_t st) {
     const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
     const int ext = integrator >= 3 ? 1 : 0;  // extended RESPA and RESPA1: bonded-only F_0
-    if (integrator != 0) k_step<1><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr, ext, hout);
-    else k_step<0><<<blocks, NW * 32, 0, st>>>(s, p, variant, step_off, hr, 0, 0.0);
+    if (integrator != 0) launch_chained(k_step<1>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, ext, hout);
+    else launch_chained(k_step<0>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, 0, 0.0);
 }
 
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,
@@ -738,4 +742,6 @@ void launch_gradient(const DevSys& s, const Params& p, int part, int cur, double
     k_gradient<<<(s.n + wpb - 1) / wpb, wpb * 32, 0, st>>>(s, p, part, cur, out);
 }
 
-void launch_advance_step(const DevSys& s, long long by, cudaStream_t st) { k_advance<<<1, 1, 0, st>>>(s, by); }
+void launch_advance_step(const DevSys& s, long long by, cudaStream_t st) {
+    launch_chained(k_advance, 1, 1, 0, st, s, by);
+}
