@@ -68,7 +68,7 @@ DT = 1.0
 # DRAM bytes (read + write) of one body launch of the BOUNCE step kernel with
 # this split on the same-size droplet at its lattice start (ncu, cold caches;
 # ~670 row entries per atom there, ~920 after equilibration)
-K_STEP_TRAFFIC = None
+K_STEP_TRAFFIC = 36164352 + 4096
 # Algorithmic lane-operations per unit of work in the fused step kernel,
 # counted from the kernel source:
 OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
@@ -467,7 +467,7 @@ def matched_observables(s, q0, v0, cfg, rank, stream, sh, n_eq=5000, n_blocks=50
 def pbc_box(rank, stream, sh, n_steps=960, chunk=48):
     """The periodic box of 32,768 water molecules (98,304 atoms, edge 99.3 A):
     Ewald direct erfc (beta 0.35) and LJ within 9 A, SPME 96^3 of order 5,
-    jumps beyond a 7.5-8.5 A switch (per-type-pair bounds), 1 fs, friction
+    jumps beyond a 7.5-8.5 A switch (one bound per atom type), 1 fs, friction
     1/ps.  From a BAOAB-equilibrated state, graph-captured runs of n_steps
     after one warm-up chunk: BAOAB (SPME every step), BOUNCE-RESPA (SPME on
     the 2 fs outer step) and BOUNCE-RESPA1 (short-range pairs on 2 fs, SPME on
@@ -488,8 +488,8 @@ def pbc_box(rank, stream, sh, n_steps=960, chunk=48):
     out = {"workload": "32,768-molecule periodic water box (98,304 atoms), erfc beta 0.35, r_c 9 A, SPME 96^3 order 5, "
                        "switch 7.5-8.5 A, 1 fs, friction 1/ps"}
     arms = (("baoab", bounce.BAOAB, dict(pair_bounds=False)),
-            ("bounce_respa", bounce.BOUNCE_RESPA, dict(pair_bounds=True, respa_m=2)),
-            ("bounce_respa1", bounce.BOUNCE_RESPA1, dict(pair_bounds=True, respa_m=2, respa_m2=3)))
+            ("bounce_respa", bounce.BOUNCE_RESPA, dict(pair_bounds=False, respa_m=2)),
+            ("bounce_respa1", bounce.BOUNCE_RESPA1, dict(pair_bounds=False, respa_m=2, respa_m2=3)))
     for name, integ, extra in arms:
         ctx = bounce.from_system(s, seed=21 + rank, **cfg, **extra)
         ctx.set_state(q0, v0, step=0)
