@@ -266,35 +266,60 @@ __device__ int candidate_runs(const DevSys& s, const Params& p, float4 hi, int* 
 
 // Writes the set bits of a warp's bitmap, in ascending order, as indices to
 // row[0 .. cap) and returns their count (which may exceed cap; cap may be
-// zero or negative, then nothing is written).  Passes of 32
-// words: a prefix of their popcounts, then the warp expands the non-empty
-// words one at a time, lane b writing bit b, so neighbouring indices (dense
-// words) cost one step per word and the stores are contiguous.
+// zero or negative, then nothing is written).  Passes of 32 words: a prefix
+// of their popcounts, then the pass's set bits are spread over the lanes,
+// 32 at a time: output k of the pass finds its word by a shuffle search over
+// the prefix and its bit by a popcount halving search, so the stores are
+// contiguous and the cost
+// follows the number of set bits, not of non-empty words.  Empty passes cost
+// one load and a vote.
+// Position of the set bit of rank r (0-based, r < popc(b)) in b.
+__device__ __forceinline__ int select_bit(uint32_t b, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int half = 16; half > 0; half >>= 1) {
+        const int c = __popc(b & ((1u << half) - 1u));
+        if (r >= c) {
+            r -= c;
+            b >>= half;
+            pos += half;
+        }
+    }
+    return pos;
+}
+
 __device__ int expand_bitmap(const uint32_t* bm, int nwords, int* row, int cap) {
     const int lane = threadIdx.x & 31;
     int total = 0;
     for (int w0 = 0; w0 < nwords; w0 += 32) {
         const int w = w0 + lane;
         const uint32_t bits = w < nwords ? bm[w] : 0u;
+        if (!__any_sync(0xffffffffu, bits != 0u)) continue;
         const int c = __popc(bits);
         int x = c;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        const int excl = total + x - c;
-        uint32_t nz = __ballot_sync(0xffffffffu, bits != 0u);
-        while (nz) {
-            const int src = __ffs(nz) - 1;
-            nz &= nz - 1u;
-            const uint32_t b = __shfl_sync(0xffffffffu, bits, src);
-            const int at = __shfl_sync(0xffffffffu, excl, src);
-            if (b & (1u << lane)) {
-                const int pos = at + __popc(b & ((1u << lane) - 1u));
-                if (pos < cap) row[pos] = ((w0 + src) << 5) + lane;
+        const int excl = x - c;  // set bits of this pass before word w
+        const int tc = __shfl_sync(0xffffffffu, x, 31);
+        for (int k0 = 0; k0 < tc; k0 += 32) {
+            const int k = k0 + lane;
+            // last lane l with excl_l <= k (the words of lanes before it hold fewer than k + 1 bits)
+            int l = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, excl, l + step);
+                if (e <= k) l += step;
+            }
+            const uint32_t b = __shfl_sync(0xffffffffu, bits, l);
+            const int r = k - __shfl_sync(0xffffffffu, excl, l);
+            if (k < tc) {
+                const int pos = total + k;
+                if (pos < cap) row[pos] = ((w0 + l) << 5) + select_bit(b, r);
             }
         }
-        total += __shfl_sync(0xffffffffu, x, 31);
+        total += tc;
     }
     return total;
 }
