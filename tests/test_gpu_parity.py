@@ -229,7 +229,8 @@ def test_multi_step_trajectory_tracks_oracle():
 
 def test_full_size_droplet_sampled():
     """4096-molecule droplet with a 12 A cutoff (the benchmark workload):
-    rows, gradients and a jump half-step on a sample of atoms."""
+    rows and full gradients on a sample of atoms (the whole step is in
+    test_full_size_droplet_steps)."""
     s = water_droplet(16, seed=0)
     cfg = dict(r_on=4.0, r_off=5.0, r_cut=12.0, skin=1.0)
     ctx = bounce.from_system(s, seed=1, **cfg)
@@ -251,6 +252,59 @@ def test_full_size_droplet_sampled():
     scale = pair_gradient_magnitudes(s.q, s.charge, s.type, ii, jj, p, "full") + bonded_gradient_magnitudes(
         s.q, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0)
     _check_sum(g[sample], ref[sample], scale[sample])
+    ctx.close()
+
+
+@pytest.mark.parametrize("split, n_steps", [("lj_jumps_rowmax", 3), ("coulomb_jumps_typed", 1)])
+def test_full_size_droplet_steps(split, n_steps):
+    """The benchmark workload at full size (4096-molecule droplet, r_c 12 A)
+    through the launches the benchmark times: run(n) is the step kernel's
+    head, body and tail launches.  Every atom against the oracle's n
+    B J A O A J B steps.  lj_jumps_rowmax is the benchmark's split (LJ on the
+    jumps, Coulomb in F_0, one bound per atom type); coulomb_jumps_typed the
+    paper's droplet split with per-type-pair bounds (~1 M proposals per
+    step).  Atoms with a near tie, and every atom of their rows, are left out
+    of the comparison (a tie may flip one decision).  Positions are compared
+    per distance travelled, velocities per their magnitude (at least a tenth
+    of the rms speed) and per step (the per-step errors of the n steps add
+    up), both at 1e-5."""
+    s = water_droplet(16, seed=0)
+    lj_only = split == "lj_jumps_rowmax"
+    typed = not lj_only
+    cfg = dict(r_on=4.0, r_off=5.0, r_cut=12.0, skin=1.0, jump_coulomb=not lj_only, pair_bounds=typed)
+    ctx = bounce.from_system(s, seed=7, **cfg)
+    ctx.set_state(s.q, s.v, step=11)
+    p = Params(r_on=4.0, r_off=5.0, r_cut=12.0, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps, coulomb_jumps=not lj_only)
+    md = OracleMD(s.q, s.v, _topo(s), p, seed=7, skin=1.0, step=11, pair_bounds=typed)
+    ctx.run(n_steps, bounce.BOUNCE)
+    tie_atoms = set()
+    path = np.zeros(s.n_atoms)  # distance each atom travels, step by step
+    for _ in range(n_steps):
+        md.ensure_rows()
+        q_prev = md.q.copy()
+        for r in md.step_bounce(record=True):
+            tie_atoms.update(r["atom"][np.abs(r["U"] - r["ratio"]) < 1e-6].tolist())
+        path += np.linalg.norm(md.q - q_prev, axis=1)
+    keep = np.ones(s.n_atoms, bool)
+    for i in tie_atoms:
+        keep[i] = False
+        keep[md.row_list[i]] = False
+    q, v = ctx.get_state()
+    # position error per distance travelled (the per-step relative error does not grow with the steps)
+    dq = np.linalg.norm(q - md.q, axis=1) / np.maximum(path, 1e-6)
+    assert keep.sum() > 0.75 * s.n_atoms
+    assert dq[keep].max() < TOL, dq[keep].max()
+    # velocity error per step (the per-step errors add up over the n steps),
+    # relative to |v| or a tenth of the rms speed: among 12,288 atoms some are
+    # nearly at rest, where the ~1e-8 A/fs absolute error of the FP32 kicks
+    # would dominate any relative measure
+    rms = math.sqrt((md.v ** 2).sum(1).mean())
+    dv = (np.linalg.norm(v - md.v, axis=1) / np.maximum(np.linalg.norm(md.v, axis=1), 0.1 * rms))[keep].max()
+    dv /= n_steps
+    assert dv < TOL, dv
+    if not tie_atoms:
+        assert ctx.energies()["proposals"] == md.proposals
+    assert md.proposals > (1000 if lj_only else 500000)
     ctx.close()
 
 
