@@ -65,10 +65,10 @@ WORKLOAD = ("BOUNCE (LJ beyond the 4-5 A switch on jumps, Coulomb in F_0), "
 N_SIDE = 16                  # 16^3 = 4096 molecules
 R_CUT, R_ON, R_OFF, SKIN = 12.0, 4.0, 5.0, 1.0
 DT = 1.0
-# DRAM bytes (read + write) of one body launch of the BOUNCE step kernel with
-# this split on the same-size droplet at its lattice start (ncu, cold caches;
-# ~670 row entries per atom there, ~920 after equilibration)
-K_STEP_TRAFFIC = 36164352 + 4096
+# DRAM bytes (read + write) of one body step (pair-sum kernel + step kernel)
+# with this split on the same-size droplet at its lattice start (ncu, cold
+# caches; ~670 row entries per atom there, ~920 after equilibration)
+K_STEP_TRAFFIC = (34263040 + 4096) + (2804736 + 0)  # k_pairs + k_step<BOUNCE>
 # Algorithmic lane-operations per unit of work in the fused step kernel,
 # counted from the kernel source:
 OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
@@ -348,9 +348,11 @@ def our_arm(args):
             rowmax_bounds=hot("bounce_coulomb_jumps_rowmax")),
         "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / peak, 4), "traffic": K_STEP_TRAFFIC,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one body launch of "
-                                       "k_step<BOUNCE> with this split on the same-size lattice droplet",
-                     "kernel": "k_step<BOUNCE> (fused F_0 + 2 jump half-steps + B A O A)",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, the k_pairs and "
+                                       "k_step<BOUNCE> launches of one body step with this split on the "
+                                       "same-size lattice droplet",
+                     "kernel": "k_pairs + k_step<BOUNCE> (F_0 pair sums; bonded terms, 2 jump half-steps, "
+                               "B A O A)",
                      "baoab_kernel_frac": round(ach_a / peak, 4)},
         "e2e": {"value": round(e2e_val, 4), "unit": "ns/day", "h2d_bytes_per_step": h2d * b["windows"] // steps,
                 "d2h_bytes_per_step": h2d * b["windows"] // steps},

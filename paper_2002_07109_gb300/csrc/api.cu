@@ -703,6 +703,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
         (r = dalloc(c, &s.nseg, (size_t)n * BOUNCE_MAXT)) || (r = dalloc(c, &s.nshort, n)) || (r = dalloc(c, &s.srows, distinct_short ? (size_t)n * s.caps : 1)) ||
         (r = dalloc(c, &s.refx, n)) || (r = dalloc(c, &s.refy, n)) || (r = dalloc(c, &s.refz, n)) ||
         (r = dalloc(c, &s.cell_atoms, n)) || (r = dalloc(c, &s.cell_phi, n)) || (r = dalloc(c, &s.cell_mol, n)) ||
+        (r = dalloc(c, &s.g0, n)) ||
         (r = dalloc(c, &s.cell_type, n)) ||
         (r = dalloc(c, &s.done_ctr, 2)) ||
         (r = dalloc(c, &s.rebuild, 1)) || (r = dalloc(c, &s.err, 1)) ||
@@ -958,15 +959,18 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
 int64_t bounce_run_launch_count(const bounce_ctx* c, int64_t n, int32_t integ) {
     if (!c || n <= 0) return 0;
     // gated row-rebuild kernels (cells count + scan, scatter, rows + flag clear;
-    // one kernel for a batch of replicas) + the fused step kernel
+    // one kernel for a batch of replicas) + the fused step kernel, and the
+    // pair-sum kernel wherever the boundary has pair sums over the long rows
     const int64_t per_boundary = (c->ds.rep_of ? 1 : 3) + 1;
+    const bool ext = integ >= BOUNCE_BOUNCE_RESPA_EXT;
+    const bool short_f0 = integ != BOUNCE_BAOAB && c->pp.rshort2 < INFINITY;
     const int64_t pme_launches = 10; // spread, load, 3 + 3 transforms, convolve, gather
     int64_t total = 2;               // step-counter updates after the head and the bodies
     for (int64_t k = 0; k <= n; ++k) {
         bool pme;
         double hr, hout;
         plan(c, integ, k == 0 ? 0 : (k == n ? 2 : 1), c->cur_step + k, pme, hr, hout);
-        total += per_boundary + (pme ? pme_launches : 0);
+        total += per_boundary + (pme ? pme_launches : 0) + (((ext && hout == 0.0) || short_f0) ? 0 : 1);
     }
     total += (n - 1) / CHUNK;        // one counter update per replayed graph chunk
     return total;

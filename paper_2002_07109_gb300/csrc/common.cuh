@@ -60,6 +60,7 @@ struct DevSys {
     int* cell_fill;
     int* cell_atoms;
     float4* cell_phi;  // high position parts in cell order (coalesced candidate reads)
+    float4* g0;        // pair-sum gradient of each atom from k_pairs (x, y, z; w = row entries, int bits)
     unsigned int* done_ctr;  // [2] finished-CTA counters of the rebuild kernels (zero between launches)
     int* cell_mol;     // molecule ids in cell order
     int* cell_type;    // atom types in cell order

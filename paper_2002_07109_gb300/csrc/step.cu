@@ -490,7 +490,7 @@ __device__ float3 atom_gradient(const DevSys& s, const Params& p, int cur, int i
 // boundaries, 0 elsewhere, where the pair sums are skipped).
 template <int BOUNCE>
 __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int variant, int step_off, double hr,
-                                                     int ext, double hout) {
+                                                     int ext, double hout, int pre) {
     __shared__ float sG[BOUNCE_GROUP][3];
     __shared__ float sGp[BOUNCE_GROUP][3];
     __shared__ double sV[BOUNCE_GROUP][3];
@@ -516,8 +516,21 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
         for (int k = threadIdx.x; k < 129; k += blockDim.x) js.inv[k] = k ? __frcp_rn((float)k) : 0.f;
     if (threadIdx.x <= na) sBoff[threadIdx.x] = s.bt_off[base + threadIdx.x];
     __syncthreads();
-    // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n: pair sums, warps over atoms
-    for (int a = warp; a < na; a += NW) {
+    // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n: pair sums, either
+    // read from k_pairs (pre) or here, warps over atoms
+    if (pre && threadIdx.x < na) {
+        const float4 g = s.g0[base + threadIdx.x];
+        const int a = threadIdx.x;
+        const bool to_out = ext != 0;
+        sG[a][0] = to_out ? 0.f : g.x;
+        sG[a][1] = to_out ? 0.f : g.y;
+        sG[a][2] = to_out ? 0.f : g.z;
+        sGp[a][0] = to_out ? g.x : 0.f;
+        sGp[a][1] = to_out ? g.y : 0.f;
+        sGp[a][2] = to_out ? g.z : 0.f;
+        atomicAdd(&sPairs, (unsigned long long)__float_as_int(g.w));
+    }
+    for (int a = pre ? na : warp; a < na; a += NW) {
         int np = 0, np2 = 0;
         float3 g = make_float3(0.f, 0.f, 0.f), gp = g;
         if (!ext) g = atom_gradient(s, p, cur, base + a, BOUNCE ? 3 : 5, np);
@@ -716,6 +729,21 @@ __global__ void k_gradient(DevSys s, Params p, int part, int cur, double* out) {
     }
 }
 
+// Pair sums of part `part` (atom_gradient) for every atom, one warp per
+// atom, for the step kernel to read: a separate kernel with few registers
+// keeps many more warps in flight on the partners' position gathers than the
+// fused step kernel can.
+__global__ void __launch_bounds__(256, 4) k_pairs(DevSys s, Params p, int step_off, int part) {
+    chain_enter();
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= s.n) return;
+    const int cur = (int)((*s.step_base + step_off) & 1);
+    int np = 0;
+    const float3 g = atom_gradient(s, p, cur, i, part, np);
+    if (lane == 0) s.g0[i] = make_float4(g.x, g.y, g.z, __int_as_float(np));
+}
+
 __global__ void k_advance(DevSys s, long long by) {
     chain_enter();
     *const_cast<long long*>(s.step_base) += by;
@@ -727,8 +755,15 @@ void launch_step(const DevSys& s, const Params& p, int integrator, int variant, 
                  double hout, cudaStream_t st) {
     const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
     const int ext = integrator >= 3 ? 1 : 0;  // extended RESPA and RESPA1: bonded-only F_0
-    if (integrator != 0) launch_chained(k_step<1>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, ext, hout);
-    else launch_chained(k_step<0>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, 0, 0.0);
+    // pair sums over the long candidate rows in their own kernel; short rows
+    // (Coulomb on the jumps) stay in the step kernel, and so does a boundary
+    // without pair sums (the extended splits between outer kicks)
+    const bool short_f0 = integrator != 0 && p.rshort2 < INFINITY;
+    const int pre = ((ext && hout == 0.0) || short_f0) ? 0 : 1;
+    if (pre) launch_chained(k_pairs, (s.n + 7) / 8, 256, 0, st, s, p, step_off, integrator != 0 ? 3 : 5);
+    if (integrator != 0)
+        launch_chained(k_step<1>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, ext, hout, pre);
+    else launch_chained(k_step<0>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, 0, 0.0, pre);
 }
 
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,
