@@ -471,9 +471,9 @@ def pbc_box(rank, stream, sh, n_steps=960, chunk=48):
     Ewald direct erfc (beta 0.35) and LJ within 9 A, SPME 96^3 of order 5,
     jumps beyond a 7.5-8.5 A switch (one bound per atom type), 1 fs, friction
     1/ps.  From a BAOAB-equilibrated state, graph-captured runs of n_steps
-    after one warm-up chunk: BAOAB (SPME every step), BOUNCE-RESPA (SPME on
-    the 2 fs outer step) and BOUNCE-RESPA1 (short-range pairs on 2 fs, SPME on
-    6 fs).  ns/day over the chunks (CUDA events), and the means of the
+    after one warm-up chunk: BAOAB (SPME every step), BOUNCE (SPME every
+    step), BOUNCE-RESPA (SPME on the 2 fs outer step) and BOUNCE-RESPA1
+    (short-range pairs on 2 fs, SPME on 6 fs).  ns/day over the chunks (CUDA events), and the means of the
     potential energy per molecule and of the temperature after every chunk."""
     import torch
     from paper_2002_07109_gb300 import bounce
@@ -490,6 +490,7 @@ def pbc_box(rank, stream, sh, n_steps=960, chunk=48):
     out = {"workload": "32,768-molecule periodic water box (98,304 atoms), erfc beta 0.35, r_c 9 A, SPME 96^3 order 5, "
                        "switch 7.5-8.5 A, 1 fs, friction 1/ps"}
     arms = (("baoab", bounce.BAOAB, dict(pair_bounds=False)),
+            ("bounce", bounce.BOUNCE, dict(pair_bounds=False)),
             ("bounce_respa", bounce.BOUNCE_RESPA, dict(pair_bounds=False, respa_m=2)),
             ("bounce_respa1", bounce.BOUNCE_RESPA1, dict(pair_bounds=False, respa_m=2, respa_m2=3)))
     for name, integ, extra in arms:
