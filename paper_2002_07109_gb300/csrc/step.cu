@@ -132,7 +132,7 @@ __device__ __forceinline__ int poisson_chunk(float u, float mu_c, const float* i
 // Philox slot 0x80000000 | c), one chunk per thread at a time, and adds its
 // count to the atom's total.  Called by all threads of the CTA.
 __device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, int base, int na, long long step,
-                              uint32_t stream) {
+                              uint32_t stream, const float* u0 = nullptr) {
     // every atom with at most one chunk (mu <= 16, the usual case): lane a of
     // warp 0 inverts atom a's chunk, and the prefix scan of jump_phase (same
     // warp) follows without a CTA barrier.  Every warp takes this decision
@@ -142,8 +142,9 @@ __device__ void poisson_phase(const DevSys& s, const Params& p, JumpSmem& js, in
         if (threadIdx.x < na) {
             int k = 0;
             if (js.nch[lane] == 1) {
-                const uint4 x = rng_atom(s, p, BOUNCE_POISSON_SLOT, base + lane, step, stream);
-                k = poisson_chunk(u24(x.x), js.muc[lane], js.inv);
+                // u0: the uniforms of chunk 0, drawn ahead by another warp
+                const float u = u0 ? u0[lane] : u24(rng_atom(s, p, BOUNCE_POISSON_SLOT, base + lane, step, stream).x);
+                k = poisson_chunk(u, js.muc[lane], js.inv);
             }
             js.M[lane] = k;
         }
@@ -216,7 +217,7 @@ __device__ __forceinline__ int owner_of(const PropSmem& ps, int na, int g) {
 // The chain velocity (js.vf), its increment (js.dv) and accept count persist
 // across passes in shared memory.  Called by all threads of the CTA.
 __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropSmem& ps, int cur, int base, int na,
-                           long long step, uint32_t stream) {
+                           long long step, uint32_t stream, bool own_loaded = false) {
     const int lane = threadIdx.x & 31;
     int any = 0;  // the CTA has proposals (warp 0 knows it from the scan)
     if (threadIdx.x < 32) {  // prefix of the proposal counts: one warp scan (na <= 32)
@@ -235,9 +236,11 @@ __device__ void jump_phase(const DevSys& s, const Params& p, JumpSmem& js, PropS
     }
     if (threadIdx.x < na && any) {
         const int a = threadIdx.x, i = base + a;
-        ps.ahi[a] = s.phi[cur][i];
-        ps.alo[a] = s.plo[cur][i];
-        ps.an[a] = s.nlong[i];
+        if (!own_loaded) {
+            ps.ahi[a] = s.phi[cur][i];
+            ps.alo[a] = s.plo[cur][i];
+            ps.an[a] = s.nlong[i];
+        }
         if (p.typed) {
             const int ta = s.type[i];
             uint32_t c = 0u;
@@ -498,6 +501,9 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
     __shared__ PropSmem ps;
     __shared__ int sBoff[BOUNCE_GROUP + 1];
     __shared__ unsigned long long sPairs;
+    // per-atom inputs of warp 0's FP64 phases, fetched ahead by warps 1-4
+    __shared__ double sQ[BOUNCE_GROUP][3], sRef[BOUNCE_GROUP][3], sKick[BOUNCE_GROUP], sOsd[BOUNCE_GROUP];
+    __shared__ float sNz[BOUNCE_GROUP][3], sU[2][BOUNCE_GROUP], sHw[BOUNCE_GROUP], sLw[BOUNCE_GROUP];
     chain_enter();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = blockIdx.x * BOUNCE_GROUP;
@@ -516,6 +522,44 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
         for (int k = threadIdx.x; k < 129; k += blockDim.x) js.inv[k] = k ? __frcp_rn((float)k) : 0.f;
     if (threadIdx.x <= na) sBoff[threadIdx.x] = s.bt_off[base + threadIdx.x];
     __syncthreads();
+    // warps 1-4 fetch ahead what warp 0's FP64 phases read (own positions,
+    // kick and O-step factors, the O-step and Poisson draws), so that warp 0's
+    // critical path waits on shared memory, not on global loads or Philox
+    if (warp >= 1 && warp <= 4 && lane < na) {
+        const int i = base + lane;
+        if (warp == 1 && do_aoa) {  // O: Box-Muller on Philox slot 0, stream 0
+            const uint4 r = rng_atom(s, p, 0u, i, step, BOUNCE_STREAM_O);
+            const float ra = sqrtf(-2.f * logf(u24_open0(r.x)));
+            float sn, cs;
+            sincospif(2.f * u24(r.y), &sn, &cs);
+            sNz[lane][0] = ra * cs;
+            sNz[lane][1] = ra * sn;
+            sNz[lane][2] = sqrtf(-2.f * logf(u24_open0(r.z))) * cospif(2.f * u24(r.w));
+        } else if (warp == 2 && BOUNCE) {  // chunk 0 of each jump half-step's Poisson count
+            if (do_j2) sU[0][lane] = u24(rng_atom(s, p, BOUNCE_POISSON_SLOT, i, step - 1, BOUNCE_STREAM_J2).x);
+            if (do_j1) sU[1][lane] = u24(rng_atom(s, p, BOUNCE_POISSON_SLOT, i, step, BOUNCE_STREAM_J1).x);
+        } else if (warp == 3) {
+            sQ[lane][0] = s.qx[cur][i];
+            sQ[lane][1] = s.qy[cur][i];
+            sQ[lane][2] = s.qz[cur][i];
+            sKick[lane] = s.kick[i];
+            if (do_aoa) {
+                sOsd[lane] = s.osd[i];
+                sRef[lane][0] = s.refx[i];
+                sRef[lane][1] = s.refy[i];
+                sRef[lane][2] = s.refz[i];
+            }
+        } else if (warp == 4) {
+            const float4 h = s.phi[cur][i], l = s.plo[cur][i];
+            sHw[lane] = h.w;
+            sLw[lane] = l.w;
+            if (BOUNCE) {
+                ps.ahi[lane] = h;
+                ps.alo[lane] = l;
+                ps.an[lane] = s.nlong[i];
+            }
+        }
+    }
     // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n: pair sums, either
     // read from k_pairs (pre) or here, warps over atoms
     if (pre && threadIdx.x < na) {
@@ -589,8 +633,8 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
     }
     __syncthreads();
     if (do_j2) {
-        poisson_phase(s, p, js, base, na, step - 1, BOUNCE_STREAM_J2);
-        jump_phase(s, p, js, ps, cur, base, na, step - 1, BOUNCE_STREAM_J2);
+        poisson_phase(s, p, js, base, na, step - 1, BOUNCE_STREAM_J2, sU[0]);
+        jump_phase(s, p, js, ps, cur, base, na, step - 1, BOUNCE_STREAM_J2, true);
     }
     if (warp == 0 && lane < na) {
         const int i = base + lane;
@@ -600,18 +644,18 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
             vy += (double)js.dv[lane][1];
             vz += (double)js.dv[lane][2];
         }
-        const double c = hk * s.kick[i];
+        const double c = hk * sKick[lane];
         vx -= c * (double)sG[lane][0];
         vy -= c * (double)sG[lane][1];
         vz -= c * (double)sG[lane][2];
         if (hr != 0.0) {
-            const double cr = hr * s.kick[i];
+            const double cr = hr * sKick[lane];
             vx -= cr * s.grecip[i];
             vy -= cr * s.grecip[s.n + i];
             vz -= cr * s.grecip[2 * (size_t)s.n + i];
         }
         if (ext && hout != 0.0) {
-            const double co = hout * s.kick[i];
+            const double co = hout * sKick[lane];
             vx -= co * (double)sGp[lane][0];
             vy -= co * (double)sGp[lane][1];
             vz -= co * (double)sGp[lane][2];
@@ -623,8 +667,8 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
     }
     __syncthreads();
     if (do_j1) {
-        poisson_phase(s, p, js, base, na, step, BOUNCE_STREAM_J1);
-        jump_phase(s, p, js, ps, cur, base, na, step, BOUNCE_STREAM_J1);
+        poisson_phase(s, p, js, base, na, step, BOUNCE_STREAM_J1, sU[1]);
+        jump_phase(s, p, js, ps, cur, base, na, step, BOUNCE_STREAM_J1, true);
     }
     if (warp == 0 && lane < na) {
         const int i = base + lane;
@@ -636,17 +680,12 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
         }
         if (do_aoa) {
             const double h = 0.5 * p.dt;
-            double x = s.qx[cur][i] + h * vx, y = s.qy[cur][i] + h * vy, z = s.qz[cur][i] + h * vz;
-            // O: Box-Muller on Philox slot 0, stream 0
-            const uint4 r = rng_atom(s, p, 0u, i, step, BOUNCE_STREAM_O);
-            const float ra = sqrtf(-2.f * logf(u24_open0(r.x)));
-            float sn, cs;
-            sincospif(2.f * u24(r.y), &sn, &cs);
-            const float g2 = sqrtf(-2.f * logf(u24_open0(r.z))) * cospif(2.f * u24(r.w));
-            const double sd = s.osd[i];
-            vx = p.c1 * vx + sd * (double)(ra * cs);
-            vy = p.c1 * vy + sd * (double)(ra * sn);
-            vz = p.c1 * vz + sd * (double)g2;
+            double x = sQ[lane][0] + h * vx, y = sQ[lane][1] + h * vy, z = sQ[lane][2] + h * vz;
+            // O: the Box-Muller normals drawn ahead (Philox slot 0, stream 0)
+            const double sd = sOsd[lane];
+            vx = p.c1 * vx + sd * (double)sNz[lane][0];
+            vy = p.c1 * vy + sd * (double)sNz[lane][1];
+            vz = p.c1 * vz + sd * (double)sNz[lane][2];
             x += h * vx;
             y += h * vy;
             z += h * vz;
@@ -660,11 +699,10 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
                 wz -= p.Ld[2] * floor(z / p.Ld[2]);
             }
             const float hx = __double2float_rn(wx), hy = __double2float_rn(wy), hz = __double2float_rn(wz);
-            const float4 oldh = s.phi[cur][i], oldl = s.plo[cur][i];
-            s.phi[nxt][i] = make_float4(hx, hy, hz, oldh.w);
+            s.phi[nxt][i] = make_float4(hx, hy, hz, sHw[lane]);
             s.plo[nxt][i] = make_float4(__double2float_rn(wx - (double)hx), __double2float_rn(wy - (double)hy),
-                                        __double2float_rn(wz - (double)hz), oldl.w);
-            const double ex = x - s.refx[i], ey = y - s.refy[i], ez = z - s.refz[i];
+                                        __double2float_rn(wz - (double)hz), sLw[lane]);
+            const double ex = x - sRef[lane][0], ey = y - sRef[lane][1], ez = z - sRef[lane][2];
             if (ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
         }
         s.vx[i] = vx;
