@@ -68,7 +68,7 @@ DT = 1.0
 # DRAM bytes (read + write) of one body step (pair-sum kernel + step kernel)
 # with this split on the same-size droplet at its lattice start (ncu, cold
 # caches; ~670 row entries per atom there, ~920 after equilibration)
-K_STEP_TRAFFIC = (34263040 + 4096) + (2804736 + 0)  # k_pairs + k_step<BOUNCE>
+K_STEP_TRAFFIC = (34264320 + 768) + (2803200 + 0)  # k_pairs + k_step<BOUNCE>
 # Algorithmic lane-operations per unit of work in the fused step kernel,
 # counted from the kernel source:
 OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
