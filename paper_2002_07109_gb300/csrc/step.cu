@@ -3,12 +3,15 @@
 //
 // Step fusion: B and J do not commute, but the end of step n (J then B/2)
 // and the start of step n+1 (B/2 then J) act at the same positions.  So one
-// launch per step does, for every atom, at positions q_n:
+// step-kernel launch per step does, for every atom, at positions q_n:
 //     F_0(q_n)  ->  J(delta/2) [stream 2, step n-1]  ->  B(delta)
 //               ->  J(delta/2) [stream 1, step n]   ->  A(delta/2) O A(delta/2)
 // writing q_{n+1} to the other position buffer (J of atom i reads partners
 // at q_n).  A run is a head launch (B/2 instead of J B), bodies, and a tail
-// launch (J then B/2, no drift).
+// launch (J then B/2, no drift).  Where F_0's pair sums run over the long
+// candidate rows they come from k_pairs, a kernel of their own launched just
+// before (more warps in flight on the partners' gathers); short-row pair sums
+// stay in the step kernel.
 //
 // Work mapping (one CTA = 32 consecutive atoms, NW warps):
 //   * pair sums and jump proposals are warp-cooperative, lanes over
