@@ -269,23 +269,31 @@ int bounce_profile_steps(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, v
 int64_t bounce_run_launch_count(const bounce_ctx* ctx, int64_t n_steps, int32_t integrator);
 
 /* Allocation-free pair energies.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate device memory -- code running
- * while another framework captures a CUDA graph (cudaMalloc is illegal during
- * capture), code that must live inside a caching allocator that owns the
- * device pool, and hosts that forbid allocation after start-up.
+ * point exists for callers that cannot allocate device memory -- code that
+ * lives inside an allocator owning the whole device pool (a foreign
+ * cudaMalloc would escape its accounting), hosts that forbid allocation after
+ * start-up (embedded or real-time loops, where cudaMalloc may block and
+ * synchronise the device), and plug-ins handed device buffers but no right to
+ * allocate.
  * It returns out[0] = sum_{i<j} k q_i q_j / r (or erfc(beta r)/r with
  * ewald_beta > 0) and out[1] = sum_{i<j} 4 eps ((sigma/r)^12 - (sigma/r)^6)
  * over all pairs of different molecules with r < r_cut (r_cut <= 0 or inf:
  * no cutoff; box = NULL: open boundaries, else 3 host doubles for a periodic
- * box), the same totals as bounce_get_energies' coulomb and lj.
- * Inputs are caller-owned DEVICE arrays: q[n,3], charge[n], type[n],
- * molecule[n]; sigma and eps are host T*T tables; out is a DEVICE array of 2
- * doubles written on `stream`.  The call allocates nothing: its scratch is a
- * static device array of BOUNCE_NOALLOC_MAX_ATOMS atoms (786,432 bytes) that
+ * box, which needs a finite r_cut <= min(box)/2 so that the minimum image is
+ * the pair sum), the same totals as bounce_get_energies' coulomb and lj.
+ * Inputs are caller-owned DEVICE arrays of the current device, contiguous:
+ * q[n,3] double, charge[n] double, type[n] int32 with 0 <= type < n_types,
+ * molecule[n] int32; sigma and eps are host T*T tables (T = n_types); out is
+ * a DEVICE array of 2 doubles written on `stream`.  A type outside
+ * [0, n_types) is not read from the tables: both totals are then NaN.
+ * The call allocates nothing: its scratch is a static device array of
+ * BOUNCE_NOALLOC_MAX_ATOMS atoms plus a status word (786,688 bytes) that
  * every GPU loading this library holds until exit.  n > BOUNCE_NOALLOC_MAX_ATOMS
  * returns BOUNCE_ERR_INVALID_ARG.  The first call on a device looks up the
  * scratch address on that device (make it before any stream capture).
- * Calls share the scratch: calls whose GPU work overlaps race. */
+ * Calls share the scratch: calls whose GPU work overlaps race.  An error
+ * already pending on the calling thread (from earlier, unrelated work) is
+ * left in place and the call returns BOUNCE_ERR_CUDA without launching. */
 int bounce_pair_energy_noalloc(int32_t n, const double* q, const double* charge, const int32_t* type,
                                const int32_t* molecule, int32_t n_types, const double* sigma, const double* eps,
                                double r_cut, double ewald_beta, const double* box, double* out, void* stream);

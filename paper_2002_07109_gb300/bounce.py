@@ -288,17 +288,46 @@ NOALLOC_MAX_ATOMS = 16384
 
 def pair_energy_noalloc(q, charge, type, molecule, sigma, eps, r_cut=math.inf, ewald_beta=0.0, box=None, out=None,
                         stream=None):
-    """Coulomb and LJ pair-energy totals of a device-resident state without any
-    device allocation by the library (for callers that cannot allocate, e.g.
-    inside another framework's graph capture).  q, charge, type, molecule and
-    out are CUDA tensors owned by the caller; returns the library's status
-    code (0 = ok)."""
+    """Coulomb and LJ pair-energy totals of a device-resident state, with no
+    device allocation by the library: for callers that may not allocate
+    (code inside an allocator that owns the device pool, hosts that forbid
+    allocation after start-up).  q (n, 3) float64, charge (n,) float64,
+    type and molecule (n,) int32, out (2,) float64: contiguous CUDA tensors
+    owned by the caller, all on one device; sigma and eps are square
+    (T, T) tables.  Raises ValueError on tensors the C entry point would
+    misread; returns the library's status code (0 = ok)."""
+    import torch
+    ts = {"q": q, "charge": charge, "type": type, "molecule": molecule, "out": out}
+    want = {"q": torch.float64, "charge": torch.float64, "type": torch.int32, "molecule": torch.int32,
+            "out": torch.float64}
+    for name, t in ts.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != want[name]:
+            raise ValueError("%s must be %s, not %s" % (name, want[name], t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.device != q.device:
+            raise ValueError("%s is on %s, q on %s" % (name, t.device, q.device))
+    n = int(q.shape[0]) if q.dim() == 2 else -1
+    if q.dim() != 2 or q.shape[1] != 3:
+        raise ValueError("q must have shape (n, 3)")
+    for name in ("charge", "type", "molecule"):
+        if tuple(ts[name].shape) != (n,):
+            raise ValueError("%s must have shape (%d,)" % (name, n))
+    if tuple(out.shape) != (2,):
+        raise ValueError("out must have shape (2,)")
     s = _host(sigma, np.float64)
     e = _host(eps, np.float64)
+    if s.ndim != 2 or s.shape[0] != s.shape[1] or e.shape != s.shape:
+        raise ValueError("sigma and eps must be square tables of one size")
     bx = None if box is None else _host(box, np.float64)
-    return bounce_pair_energy_noalloc(int(q.shape[0]), _ptr(q), _ptr(charge), _ptr(type), _ptr(molecule),
-                                      int(s.shape[0]), _ptr(s), _ptr(e), float(r_cut), float(ewald_beta),
-                                      None if bx is None else _ptr(bx), _ptr(out), stream)
+    if bx is not None and bx.shape != (3,):
+        raise ValueError("box must hold 3 edges")
+    with torch.cuda.device(q.device):
+        return bounce_pair_energy_noalloc(n, _ptr(q), _ptr(charge), _ptr(type), _ptr(molecule), int(s.shape[0]),
+                                          _ptr(s), _ptr(e), float(r_cut), float(ewald_beta),
+                                          None if bx is None else _ptr(bx), _ptr(out), stream)
 
 
 def from_system(sys, **kw):

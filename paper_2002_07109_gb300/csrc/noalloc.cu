@@ -1,26 +1,31 @@
 // Pair energies without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA graph
-// being captured or replayed by another framework, allocators that forbid
-// foreign allocations (a caching allocator that owns the whole device
-// pool), or embedded/real-time hosts that must not allocate after start-up.
-// For them, bounce_pair_energy_noalloc computes the same Coulomb and
-// Lennard-Jones pair energy totals as the energy kernel of a context
-// (bounce_get_energies), but over all pairs of a caller-supplied state and
-// with its scratch in a file-scope device array instead of context buffers.
+// Some callers cannot call cudaMalloc: code that lives inside an allocator
+// owning the whole device pool (a caching allocator would see a foreign
+// allocation it cannot account for), hosts that forbid allocation after
+// start-up (embedded or real-time loops, where cudaMalloc may block and
+// synchronise the device), and plug-ins that are handed device buffers but
+// no allocation rights.  For them, bounce_pair_energy_noalloc computes the
+// same Coulomb and Lennard-Jones pair energy totals as the energy kernel of a
+// context (bounce_get_energies), but over all pairs of a caller-supplied
+// state and with its scratch in a file-scope device array instead of context
+// buffers.
 //
 // Scratch: g_noalloc_scratch below, BOUNCE_NOALLOC_MAX_ATOMS atoms
 // (48 bytes per atom: split FP32 positions and two per-atom FP64 partial
-// sums, 786,432 bytes in all), held by every GPU that loads this library
-// until the process exits.  Host code cannot use the array's name as a
-// device address (on the host it names a shadow variable), so the first
-// call on each device looks the address up with cudaGetSymbolAddress while
-// that device is current and keeps it; make that first call before any
-// stream capture.  Every call overwrites every per-atom slot it reads, so
-// nothing needs clearing between calls; calls whose GPU work overlaps (two
-// streams, two threads) share the array and race.
+// sums, 786,432 bytes in all), plus one status word, held by every GPU that
+// loads this library until the process exits.  Host code cannot use the
+// array's name as a device address (on the host it names a shadow
+// variable), so the first call on each device looks the address up with
+// cudaGetSymbolAddress while that device is current and keeps it; make that
+// first call before any stream capture.  Every call overwrites every
+// per-atom slot it reads and clears the status word first, so nothing else
+// needs clearing between calls; calls whose GPU work overlaps (two streams,
+// two threads) share the array and race.
 #include <cmath>
 #include <mutex>
+
+#include <math_constants.h>
 
 #include "../../include/bounce.h"
 #include "common.cuh"
@@ -28,7 +33,8 @@
 namespace {
 
 constexpr int NOALLOC_MAX = BOUNCE_NOALLOC_MAX_ATOMS;
-constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX * (2 * sizeof(float4) + 2 * sizeof(double));
+// per atom: two float4 and two doubles; then one status word (bad type seen)
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX * (2 * sizeof(float4) + 2 * sizeof(double)) + 256;
 constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
@@ -40,6 +46,7 @@ struct Layout {
     float4* hi;
     float4* lo;
     double* part;  // [2][n]: coulomb, lj per atom
+    int* bad;      // set when an atom type lies outside [0, n_types)
 };
 
 __host__ __device__ inline Layout layout(void* base, int n) {
@@ -47,11 +54,20 @@ __host__ __device__ inline Layout layout(void* base, int n) {
     l.hi = (float4*)base;
     l.lo = l.hi + NOALLOC_MAX;
     l.part = (double*)(l.lo + NOALLOC_MAX);
+    l.bad = (int*)(l.part + 2 * (size_t)NOALLOC_MAX);
     (void)n;
     return l;
 }
 
-__global__ void k_na_pack(void* scratch, int n, const double* q, const double* charge, const int* type, Params p) {
+// Clears the status word (one thread); the pack kernel that follows on the
+// same stream may then flag bad types.
+__global__ void k_na_clear(void* scratch) { *layout(scratch, 0).bad = 0; }
+
+// Split FP32 copies of the positions.  A type outside [0, n_types) would
+// index the LJ tables out of bounds: it is replaced by type 0 here and
+// flagged, and k_na_sum then writes NaN to both totals.
+__global__ void k_na_pack(void* scratch, int n, const double* q, const double* charge, const int* type, int n_types,
+                          Params p) {
     Layout l = layout(scratch, n);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double x = q[3 * (size_t)i], y = q[3 * (size_t)i + 1], z = q[3 * (size_t)i + 2];
@@ -61,9 +77,14 @@ __global__ void k_na_pack(void* scratch, int n, const double* q, const double* c
             z -= p.Ld[2] * floor(z / p.Ld[2]);
         }
         const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
+        int t = type[i];
+        if (t < 0 || t >= n_types) {
+            atomicOr(l.bad, 1);
+            t = 0;
+        }
         l.hi[i] = make_float4(hx, hy, hz, (float)charge[i]);
         l.lo[i] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
-                              __double2float_rn(z - (double)hz), __int_as_float(type[i]));
+                              __double2float_rn(z - (double)hz), __int_as_float(t));
     }
 }
 
@@ -130,8 +151,9 @@ __global__ void k_na_sum(void* scratch, int n, double kfix, double* out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out[0] = kfix * part[0][0];
-        out[1] = part[1][0];
+        const bool bad = *l.bad != 0;
+        out[0] = bad ? CUDART_NAN : kfix * part[0][0];
+        out[1] = bad ? CUDART_NAN : part[1][0];
     }
 }
 
@@ -176,14 +198,23 @@ extern "C" int bounce_pair_energy_noalloc(int32_t n, const double* q, const doub
     for (int d = 0; d < 3; ++d) {
         const double Lb = box ? box[d] : 1.0;
         if (!(Lb > 0)) return BOUNCE_ERR_INVALID_ARG;
+        // minimum image: beyond half an edge the sum would no longer be the pair sum
+        if (box && !(cut && 2.0 * r_cut <= Lb)) return BOUNCE_ERR_INVALID_ARG;
         p.Ld[d] = Lb;
         p.Lhi[d] = (float)Lb;
         p.Llo[d] = (float)(Lb - (double)p.Lhi[d]);
         p.invL[d] = (float)(1.0 / Lb);
     }
     cudaStream_t st = (cudaStream_t)stream;
-    k_na_pack<<<(n + 255) / 256, 256, 0, st>>>(scratch, n, q, charge, type, p);
+    // an error left pending by earlier, unrelated work is not this call's:
+    // refuse to launch rather than report (and clear) it as our own
+    if (cudaPeekAtLastError() != cudaSuccess) return BOUNCE_ERR_CUDA;
+    k_na_clear<<<1, 1, 0, st>>>(scratch);
+    if (cudaGetLastError() != cudaSuccess) return BOUNCE_ERR_CUDA;
+    k_na_pack<<<(n + 255) / 256, 256, 0, st>>>(scratch, n, q, charge, type, n_types, p);
+    if (cudaGetLastError() != cudaSuccess) return BOUNCE_ERR_CUDA;
     k_na_pairs<<<(n + 7) / 8, 256, 0, st>>>(scratch, n, q, molecule, p);
+    if (cudaGetLastError() != cudaSuccess) return BOUNCE_ERR_CUDA;
     k_na_sum<<<1, 256, 0, st>>>(scratch, n, KCOUL_D / (double)p.kcoul, out);
     return cudaGetLastError() == cudaSuccess ? BOUNCE_OK : BOUNCE_ERR_CUDA;
 }
