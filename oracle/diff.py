@@ -18,11 +18,16 @@ import numpy as np
 import torch
 
 from .forcefield import K_COUL
+from .neighbors import rows_cell_list, to_pairs
 
 
 def _pairs(q, mol, r_cut, box):
-    """Directed pairs (i, j) of different molecules with r^2 < r_c^2 (FP64)."""
+    """Directed pairs (i, j) of different molecules with r^2 < r_c^2 (FP64):
+    through the oracle's cell list when there is a cutoff (the same set as
+    the brute-force rows, which pin it), else every pair."""
     n = len(mol)
+    if math.isfinite(r_cut):
+        return to_pairs(rows_cell_list(q, mol, r_cut, box))
     ii, jj = np.nonzero(mol[:, None] != mol[None, :])
     d = q[ii] - q[jj]
     if box is not None:
@@ -80,4 +85,4 @@ def force_matching_loss(q, typ, mol, qt, sig, eps, F_target, r_cut, ewald_beta=0
     # the symmetrisation halves each off-diagonal derivative: undo it
     gs = gs + gs.T - torch.diag(torch.diagonal(gs))
     ge = ge + ge.T - torch.diag(torch.diagonal(ge))
-    return float(L), F.detach().numpy(), float(E), gq.numpy(), gqt.numpy(), gs.numpy(), ge.numpy()
+    return float(L.detach()), F.detach().numpy(), float(E.detach()), gq.numpy(), gqt.numpy(), gs.numpy(), ge.numpy()

@@ -188,9 +188,12 @@ class OracleMD:
         self.step_index = int(step)
         self.q_ref = None
         self.row_list = None
+        self._plist = None          # BAOAB's own pair list (see full_pairs)
+        self._plist_ref = None
         self.rebuilds = 0
         self.proposals = 0
         self.accepts = 0
+        self.tie_atoms = set()      # atoms whose thinning decision was within 1e-6 of a tie
         from .bounds import bound_table, pair_weights
         T = int(max(topo.type.max() + 1, p.lj_sigma.shape[0]))
         self.L, self.Lstar = bound_table(topo.charge, topo.type, T, p.lj_sigma, p.lj_eps, p)
@@ -209,6 +212,16 @@ class OracleMD:
     def pairs(self):
         return to_pairs(self.row_list)
 
+    def full_pairs(self):
+        """Pairs for BAOAB's full gradient from a list of its own, refreshed by
+        the same skin rule: BAOAB reads no candidate rows, so its steps leave
+        the rows of the jump step (and their rebuild history) untouched.  The
+        pairs inside r_c are the same either way."""
+        if self._plist is None or (math.isfinite(self.r_list) and needs_rebuild(self.q, self._plist_ref, self.skin)):
+            self._plist = to_pairs(build_rows(self.q, self.topo.mol, self.r_list, self.p.box))
+            self._plist_ref = self.q.copy()
+        return self._plist
+
     def grad_short(self):
         """F_0: bonded + (1 - chi) pair part."""
         return self.grad_short_pairs() + self.grad_bonded()
@@ -222,8 +235,8 @@ class OracleMD:
         t = self.topo
         return bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box)
 
-    def grad_full(self):
-        ii, jj = self.pairs()
+    def grad_full(self, pairs=None):
+        ii, jj = self.pairs() if pairs is None else pairs
         t = self.topo
         return (pair_gradients(self.q, t.charge, t.type, ii, jj, self.p, "full")
                 + bonded_gradients(self.q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0, self.p.box))
@@ -274,17 +287,17 @@ class OracleMD:
                                 pair_bounds=self.pair_bounds)
         self.proposals += int(rec['M'].sum())
         self.accepts += int(rec['accepted'].sum()) if len(rec['accepted']) else 0
+        if len(rec['U']):
+            self.tie_atoms.update(rec['atom'][np.abs(rec['U'] - rec['ratio']) < 1e-6].tolist())
         return rec if record else None
 
     def step_baoab(self):
         h = 0.5 * self.dt
-        self.ensure_rows()
-        self.kick(self.grad_full() + self.recip()[1], h)
+        self.kick(self.grad_full(self.full_pairs()) + self.recip()[1], h)
         self.drift(h)
         self.v = o_step(self.v, self.topo.mass, self.T, self.gamma, self.dt, self.seed, self.step_index)
         self.drift(h)
-        self.ensure_rows()
-        self.kick(self.grad_full() + self.recip()[1], h)
+        self.kick(self.grad_full(self.full_pairs()) + self.recip()[1], h)
         self.step_index += 1
 
     def _f0(self, with_recip, bonded_only):
