@@ -107,6 +107,17 @@ typedef struct bounce_config {
                             * per atom type, partner uniform over the row (0)  */
     int32_t respa_m2;      /* intermediate steps per BOUNCE-RESPA1 outer step,
                             * 1..8 (3)                                           */
+    double pair_skin;      /* skin of the cluster pair lists of the pair sums
+                            * (systems with a cutoff); they are rebuilt when an
+                            * atom has moved pair_skin/2.  0: the same as skin.
+                            * Internal to the pair sums: results do not depend
+                            * on it (0)                                         */
+    int32_t step_kernel;   /* step kernel: 0 automatic (thread per atom where the
+                            * jump bounds predict under 0.5 proposals per
+                            * atom-step, else 32-atom cooperative CTAs), 1 the
+                            * cooperative kernel, 2 thread per atom (systems
+                            * whose pair sums run over clusters or tiles).  Both
+                            * give the same results bit for bit (0)            */
 } bounce_config;
 
 /* Energies and counters (bounce_get_energies). */
@@ -127,6 +138,15 @@ typedef struct bounce_energies {
     int64_t full_pairs; /* pair terms evaluated for the full gradient (BAOAB)    */
     double recip;       /* E_recip + E_self + E_exclusion of periodic Ewald (0)   */
 } bounce_energies;
+
+/* Launch parameters chosen by bounce_autotune. */
+typedef struct bounce_tuning {
+    int32_t tile_j;      /* atoms per j-block of the all-pairs tile kernel (0: not used)   */
+    int32_t tile_blocks; /* its resident grid (CTAs of 256 threads)                        */
+    double column_edge;  /* edge of the cluster columns in A (0: not used)                 */
+    double pair_ms;      /* pair-sum kernel time of the chosen candidate, ms per launch    */
+    int32_t candidates;  /* candidates timed                                               */
+} bounce_tuning;
 
 /* Fill *cfg with the defaults documented above. */
 void bounce_config_default(bounce_config* cfg);
@@ -262,6 +282,28 @@ int bounce_msd(bounce_ctx* ctx, int32_t type, double* out, void* stream);
  * the number of step-kernel launches.  Synchronises `stream`. */
 int bounce_profile_steps(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, void* stream, double* kernel_ms,
                          int64_t* launches);
+
+/* Autotuner: times the pair-sum kernel of `integrator` on the current state
+ * for each candidate launch shape and keeps the fastest for later runs.
+ * Systems without a cutoff (droplets, replica batches): the j-block length
+ * of the all-pairs tiles (32, 64, 128, 256 atoms) and the resident grid
+ * (2, 4, 8 CTAs per SM); systems with a cutoff: the edge of the cluster
+ * columns (0.8 to 1.25 times (8 / density)^(1/3)).  The results of a run do
+ * not depend on the choice except through the order of FP32 partial sums.
+ * Captured graphs are dropped.  *out receives the choice.  Synchronises
+ * `stream`.  Errors: STATE (no state), CUDA. */
+int bounce_autotune(bounce_ctx* ctx, int32_t integrator, void* stream, bounce_tuning* out);
+
+/* Profiling breakdown: advance n_steps exactly as bounce_run does, but with
+ * direct launches (no graph) and CUDA events around each group of launches
+ * of every step boundary.  ms[5] receives the summed device time of
+ * (0) the pair-sum kernel, (1) the step kernel, (2) the candidate-row
+ * rebuild launches, (3) the cluster-list rebuild launches, (4) the SPME
+ * launches; groups[5] (may be NULL) the number of boundaries timed for each
+ * (a gated rebuild that finds nothing to do still counts).  Synchronises
+ * `stream`.  Errors: as bounce_run. */
+int bounce_profile_breakdown(bounce_ctx* ctx, int64_t n_steps, int32_t integrator, void* stream, double* ms,
+                             int64_t* groups);
 
 /* Number of kernel launches a bounce_run of n_steps of `integrator` would
  * issue from the current state (launch accounting: gated row-rebuild

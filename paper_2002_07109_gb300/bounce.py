@@ -37,7 +37,13 @@ class bounce_config(C.Structure):
                 ("box", C.c_double * 3), ("max_neighbors", C.c_int32), ("max_short", C.c_int32),
                 ("device", C.c_int32), ("pme_grid", C.c_int32 * 3), ("pme_order", C.c_int32),
                 ("respa_m", C.c_int32), ("jump_coulomb", C.c_int32),
-                ("pair_bounds", C.c_int32), ("respa_m2", C.c_int32)]
+                ("pair_bounds", C.c_int32), ("respa_m2", C.c_int32), ("pair_skin", C.c_double),
+                ("step_kernel", C.c_int32)]
+
+
+class bounce_tuning(C.Structure):
+    _fields_ = [("tile_j", C.c_int32), ("tile_blocks", C.c_int32), ("column_edge", C.c_double),
+                ("pair_ms", C.c_double), ("candidates", C.c_int32)]
 
 
 class bounce_energies(C.Structure):
@@ -70,6 +76,8 @@ _sig = {
     "bounce_set_msd_reference": (C.c_int, [_P, _P]),
     "bounce_msd": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), _P]),
     "bounce_profile_steps": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "bounce_profile_breakdown": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P]),
+    "bounce_autotune": (C.c_int, [_P, C.c_int32, _P, C.POINTER(bounce_tuning)]),
     "bounce_run_launch_count": (C.c_int64, [_P, C.c_int64, C.c_int32]),
     "bounce_pair_energy_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, C.c_double, C.c_double,
                                              _P, _P, _P]),
@@ -109,7 +117,7 @@ class Context:
 
     def __init__(self, *, dt=1.0, gamma=0.001, temperature=300.0, seed=0, r_on=4.0, r_off=5.0, r_cut=math.inf,
                  skin=1.0, ewald_beta=0.0, box=None, max_neighbors=2048, max_short=256, device=0, pme_grid=None,
-                 pme_order=5, respa_m=2, jump_coulomb=True, pair_bounds=False, respa_m2=3):
+                 pme_order=5, respa_m=2, jump_coulomb=True, pair_bounds=False, respa_m2=3, pair_skin=0.0, step_kernel=0):
         cfg = bounce_config()
         bounce_config_default(C.byref(cfg))
         cfg.dt_fs, cfg.gamma_per_fs, cfg.temperature_K, cfg.seed = dt, gamma, temperature, seed
@@ -124,6 +132,8 @@ class Context:
         cfg.jump_coulomb = 1 if jump_coulomb else 0
         cfg.pair_bounds = 1 if pair_bounds else 0
         cfg.respa_m2 = respa_m2
+        cfg.pair_skin = pair_skin
+        cfg.step_kernel = step_kernel
         self.cfg = cfg
         h = C.c_void_p()
         r = bounce_create(C.byref(h), C.byref(cfg))
@@ -234,6 +244,22 @@ class Context:
         self._check(bounce_profile_steps(self.h, int(n_steps), int(integrator), stream, C.byref(ms), C.byref(nl)),
                     "profile_steps")
         return ms.value, nl.value
+
+    def profile_breakdown(self, n_steps, integrator=BOUNCE, stream=None):
+        """Summed device ms and timed boundaries of (pairs, step kernel, row
+        rebuild, cluster rebuild, SPME) over n_steps run as bounce_run does."""
+        ms = np.zeros(5)
+        groups = np.zeros(5, np.int64)
+        self._check(bounce_profile_breakdown(self.h, int(n_steps), int(integrator), stream, _ptr(ms), _ptr(groups)),
+                    "profile_breakdown")
+        return dict(zip(("pairs", "step", "rows", "clusters", "pme"), ms)), groups
+
+    def autotune(self, integrator=BOUNCE, stream=None):
+        """Time the pair kernel's candidate launch shapes on the current state
+        and keep the fastest; returns the choice."""
+        t = bounce_tuning()
+        self._check(bounce_autotune(self.h, int(integrator), stream, C.byref(t)), "autotune")
+        return {k: getattr(t, k) for k, _ in bounce_tuning._fields_}
 
     def run_launch_count(self, n_steps, integrator=BOUNCE):
         return int(bounce_run_launch_count(self.h, int(n_steps), int(integrator)))

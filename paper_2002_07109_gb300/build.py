@@ -14,7 +14,8 @@ OUT = os.path.join(HERE, "libbounce.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["api.cu", "nlist.cu", "step.cu", "energy.cu", "observe.cu", "noalloc.cu", "pme.cu", "diff.cu"]
+SOURCES = ["api.cu", "nlist.cu", "step.cu", "cluster.cu", "tile.cu", "energy.cu", "observe.cu", "noalloc.cu", "pme.cu",
+           "diff.cu"]
 
 
 def nvcc():

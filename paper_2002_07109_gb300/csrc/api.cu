@@ -64,8 +64,8 @@ struct bounce_ctx {
     double* h_stage = nullptr;   // pinned [6 n]: interleaved q then v on their way to or from the device
     double* d_stage = nullptr;   // device [6 n]
     unsigned long long* h_cnt = nullptr;
-    int bitmap_warps = 1;
-    size_t bitmap_bytes = 0;
+    int bitmap_warps = 1;        // window words per bitmap of the row builder
+    size_t bitmap_bytes = 0;     // its shared memory per CTA
     int ncell_alloc = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[5][64] = {};  // [integrator][RESPA phase of the chunk's first step]
@@ -75,6 +75,21 @@ struct bounce_ctx {
     DevPme pme{};
     double* diff_part = nullptr;   // [NPAR n + NPAR] parameter partials and sums of the pair backward
     double e_self = 0.0;
+    // cluster-pair path: allocated capacities (buffers grow, never shrink)
+    int cl_cap_ncol = 0, cl_cap_ncl = 0, cl_cap_items = 0;
+    size_t cl_cap_lst[2] = {0, 0};
+    bool cl_atoms_alloc = false;
+    // after BAOAB runs on clusters the step kernel did not test the rows:
+    // the next row consumer tests the displacement first
+    bool rows_check_due = false;
+    // tuning (bounce_autotune): cluster column edge factor, tile j-block and grid
+    double cl_edge_factor = 1.0;
+    bool cl_force = false;        // the next setup_clusters recomputes the grid
+    int tile_j = 64, tile_blocks = 152 * 4;
+    int4* tile_items = nullptr;
+    int tile_cap = 0;
+    std::vector<int> rep_bounds;  // [replicas + 1] atom ranges for the tiles ({0, n} for one system)
+    bool lite_jumps = false;      // BOUNCE integrators take the thread-per-atom step kernel
 };
 
 namespace {
@@ -112,6 +127,13 @@ void drop_graphs(bounce_ctx* c) {
             }
 }
 
+void reset_cluster_caps(bounce_ctx* c) {
+    c->cl_cap_ncol = c->cl_cap_ncl = c->cl_cap_items = 0;
+    c->cl_cap_lst[0] = c->cl_cap_lst[1] = 0;
+    c->cl_atoms_alloc = false;
+    c->rows_check_due = false;
+}
+
 void free_all(bounce_ctx* c) {
     if (c->h_stage) cudaFreeHost(c->h_stage);
     c->h_stage = nullptr;
@@ -128,6 +150,9 @@ void free_all(bounce_ctx* c) {
     c->has_pme = false;
     c->pme = DevPme{};
     c->diff_part = nullptr;
+    c->tile_items = nullptr;
+    c->tile_cap = 0;
+    reset_cluster_caps(c);
 }
 
 // ---------------------------------------------------------------- bounds
@@ -219,6 +244,15 @@ void compute_bounds(bounce_ctx* c, const std::vector<double>& sig, const std::ve
             c->L[a * T + b] = best * (1.0 + 1e-6);
             c->Lstar[a] = std::max(c->Lstar[a], c->L[a * T + b]);
         }
+}
+
+bool finite_cut(const bounce_config& g) { return std::isfinite(g.r_cut) && g.r_cut > 0; }
+
+// Short candidate rows (r < r_off + skin) for F_0 exist only for systems
+// without a cutoff (all pairs); with a cutoff the pair sums run over clusters.
+bool short_rows(const bounce_config& g) {
+    const double rs = g.r_off + g.skin;
+    return g.jump_coulomb && std::isfinite(rs) && !finite_cut(g);
 }
 
 double r_list(const bounce_config& cfg) {
@@ -356,7 +390,7 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     p.rlist2_lo = std::isfinite(rl2) ? (float)(rl2 * (1.0 - 1e-5)) : INFINITY;
     p.rlist2_hi = std::isfinite(rl2) ? (float)(rl2 * (1.0 + 1e-5)) : INFINITY;
     const double rs = g.r_off + g.skin;
-    p.rshort2 = (g.jump_coulomb && std::isfinite(rs) && rs < rl) ? (float)(rs * rs * (1.0 + 1e-4)) : INFINITY;
+    p.rshort2 = short_rows(g) ? (float)(rs * rs * (1.0 + 1e-4)) : INFINITY;
     p.coul_jump = g.jump_coulomb ? 1 : 0;
     p.typed = g.pair_bounds ? 1 : 0;
     p.n_types = T;
@@ -458,8 +492,206 @@ int setup_grid(bounce_ctx* c, const double* q) {
     return BOUNCE_OK;
 }
 
-// Launch the rebuild sequence (gated by the device flag unless forced).
+// Cluster-pair grid for the current host positions (finite cutoff, one
+// system): columns of edge ~ (8 / density)^(1/3) over (x, y), so that a
+// cluster of 8 z-sorted atoms is roughly a cube; capacities from the host
+// positions with margins (an overflow during a run is reported as
+// BOUNCE_ERR_LIST_OVERFLOW).  A droplet keeps its grid while every atom
+// stays inside it, so that captured graphs stay valid.
+int setup_clusters(bounce_ctx* c, const double* q) {
+    DevClu& k = c->ds.cl;
+    const bounce_config& g = c->cfg;
+    const int n = c->n;
+    if (!finite_cut(g) || c->ds.rep_of) {
+        k.on = 0;
+        return BOUNCE_OK;
+    }
+    const double cskin = g.pair_skin > 0 ? g.pair_skin : g.skin;
+    const double rl = g.r_cut + cskin;
+    const bool two = g.jump_coulomb && g.r_off < g.r_cut;
+    const double rsh = std::min(g.r_off, g.r_cut) + cskin;
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        if (g.periodic) {
+            lo[d] = 0.0;
+            hi[d] = g.box[d];
+        } else {
+            lo[d] = 1e300;
+            hi[d] = -1e300;
+            for (int i = 0; i < n; ++i) {
+                lo[d] = std::min(lo[d], q[3 * i + d]);
+                hi[d] = std::max(hi[d], q[3 * i + d]);
+            }
+        }
+    }
+    // keep the current grid (a periodic box's is fixed; a droplet's while
+    // every atom lies inside it) while the columns stay well inside capacity
+    if (k.on && !c->cl_force) {
+        const double x0 = k.ox, y0 = k.oy, x1 = k.ox + k.ncx / k.ihx, y1 = k.oy + k.ncy / k.ihy;
+        if (g.periodic || (lo[0] >= x0 && lo[1] >= y0 && hi[0] <= x1 && hi[1] <= y1)) {
+            std::vector<int> cnt(k.ncol, 0);
+            int mx = 0;
+            for (int i = 0; i < n; ++i) {
+                double x = q[3 * i], y = q[3 * i + 1];
+                if (g.periodic) {
+                    x -= g.box[0] * std::floor(x / g.box[0]);
+                    y -= g.box[1] * std::floor(y / g.box[1]);
+                }
+                const int cx = std::min(std::max((int)std::floor((x - x0) * k.ihx), 0), k.ncx - 1);
+                const int cy = std::min(std::max((int)std::floor((y - y0) * k.ihy), 0), k.ncy - 1);
+                mx = std::max(mx, ++cnt[cy * k.ncx + cx]);
+            }
+            if (4 * mx <= 3 * k.maxcol) return BOUNCE_OK;
+        }
+    }
+    double vol = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (!g.periodic) {
+            lo[d] -= 2.0;
+            hi[d] += 2.0;
+        }
+        vol *= hi[d] - lo[d];
+    }
+    // a droplet fills about half of its bounding box
+    const double rho = std::max(n / (g.periodic ? vol : 0.55 * vol), 1e-4);
+    double a = std::min(std::max(std::cbrt(8.0 / rho) * c->cl_edge_factor, 2.5), 12.0);
+    c->cl_force = false;
+    int nc[2];
+    for (;;) {
+        for (int d = 0; d < 2; ++d) nc[d] = std::max(1, (int)std::floor((hi[d] - lo[d]) / a));
+        if ((long long)nc[0] * nc[1] <= 65536) break;
+        a *= 1.25;
+    }
+    DevClu nk = k;
+    nk.on = 1;
+    nk.ncx = nc[0];
+    nk.ncy = nc[1];
+    nk.ncol = nc[0] * nc[1];
+    nk.ox = g.periodic ? 0.f : (float)lo[0];
+    nk.oy = g.periodic ? 0.f : (float)lo[1];
+    nk.ihx = (float)(nc[0] / (hi[0] - lo[0]));
+    nk.ihy = (float)(nc[1] / (hi[1] - lo[1]));
+    std::vector<int> cnt(nk.ncol, 0);
+    int mx = 0;
+    for (int i = 0; i < n; ++i) {
+        double x = q[3 * i], y = q[3 * i + 1];
+        if (g.periodic) {
+            x -= g.box[0] * std::floor(x / g.box[0]);
+            y -= g.box[1] * std::floor(y / g.box[1]);
+        }
+        const int cx = std::min(std::max((int)std::floor((x - nk.ox) * nk.ihx), 0), nk.ncx - 1);
+        const int cy = std::min(std::max((int)std::floor((y - nk.oy) * nk.ihy), 0), nk.ncy - 1);
+        mx = std::max(mx, ++cnt[cy * nk.ncx + cx]);
+    }
+    const int want = (mx * 3 / 2 + 16 + 7) / 8 * 8;
+    if (mx > BOUNCE_CL_MAXCOL) return fail(c, BOUNCE_ERR_UNSUPPORTED, "a cluster column holds more than 1024 atoms");
+    nk.maxcol = std::min(want, BOUNCE_CL_MAXCOL);
+    nk.maxcl = nk.maxcol / BOUNCE_CL;
+    const int ncl = nk.ncol * nk.maxcl;
+    // lists: atoms within the search radius R of a cluster box of edge ~a
+    // (its volume by Steiner's formula), with a margin; the lower clusters of
+    // the order hold up to the whole count, the mean is half of it
+    const double rho_a = std::max(n / (g.periodic ? vol : 0.52 * vol), 0.02);
+    const double rr[2] = {rl, rsh};
+    nk.nlists = two ? 2 : 1;
+    for (int L = 0; L < 2; ++L) {
+        const double R = rr[L];
+        const double V = a * a * a + 6.0 * a * a * R + 3.0 * M_PI * a * R * R + 4.18879 * R * R * R;
+        const int est = (int)(rho_a * V);
+        nk.capj[L] = L < nk.nlists ? (est * 2 + 128 + 31) / 32 * 32 : 1;
+        const double rm = rr[L] + 1e-3;
+        nk.rsx[L] = (float)rm;
+        nk.rs2[L] = (float)(rm * rm);
+    }
+    nk.capitems = ncl * (nk.capj[0] / BOUNCE_CL_EPW + 1);
+    nk.cskin_half2 = 0.25 * cskin * cskin;
+    int r;
+    if (!c->cl_atoms_alloc) {
+        if ((r = dalloc(c, &nk.col_atoms, n)) || (r = dalloc(c, &nk.atom_col, n)) || (r = dalloc(c, &nk.a2s, n)) ||
+            (r = dalloc(c, &nk.crefx, n)) || (r = dalloc(c, &nk.crefy, n)) || (r = dalloc(c, &nk.crefz, n)) ||
+            (r = dalloc(c, &nk.cofx, n)) || (r = dalloc(c, &nk.cofy, n)) || (r = dalloc(c, &nk.cofz, n)) ||
+            (r = dalloc(c, &nk.nitems, 2)) || (r = dalloc(c, &nk.rebuild, 1)) || (r = dalloc(c, &nk.done_ctr, 2)))
+            return r;
+        c->cl_atoms_alloc = true;
+    }
+    if (nk.ncol > c->cl_cap_ncol) {
+        if ((r = dalloc(c, &nk.col_count, nk.ncol)) || (r = dalloc(c, &nk.col_start, nk.ncol + 1)) ||
+            (r = dalloc(c, &nk.col_fill, nk.ncol)) || (r = dalloc(c, &nk.col_ncl, nk.ncol)))
+            return r;
+        c->cl_cap_ncol = nk.ncol;
+    }
+    if (ncl > c->cl_cap_ncl) {
+        const size_t sl = (size_t)ncl * BOUNCE_CL;
+        if ((r = dalloc(c, &nk.cl_atom, sl)) || (r = dalloc(c, &nk.sphi[0], sl)) || (r = dalloc(c, &nk.sphi[1], sl)) ||
+            (r = dalloc(c, &nk.splo[0], sl)) || (r = dalloc(c, &nk.splo[1], sl)) || (r = dalloc(c, &nk.smol, sl)) ||
+            (r = dalloc(c, &nk.bb_lo, ncl)) || (r = dalloc(c, &nk.bb_hi, ncl)) || (r = dalloc(c, &nk.lcnt[0], ncl)) ||
+            (r = dalloc(c, &nk.lcnt[1], ncl)) || (r = dalloc(c, &nk.acc, 3 * sl)))
+            return r;
+        c->cl_cap_ncl = ncl;
+    }
+    for (int L = 0; L < 2; ++L)
+        if ((size_t)ncl * nk.capj[L] > c->cl_cap_lst[L]) {
+            if ((r = dalloc(c, &nk.lst[L], (size_t)ncl * nk.capj[L]))) return r;
+            c->cl_cap_lst[L] = (size_t)ncl * nk.capj[L];
+        }
+    if (nk.capitems > c->cl_cap_items) {
+        if ((r = dalloc(c, &nk.items[0], nk.capitems)) || (r = dalloc(c, &nk.items[1], nk.capitems))) return r;
+        c->cl_cap_items = nk.capitems;
+    }
+    k = nk;
+    return BOUNCE_OK;
+}
+
+// All-pairs tiles (systems without a cutoff): the static items of the
+// current replica layout for j-blocks of c->tile_j atoms.
+int setup_tiles(bounce_ctx* c) {
+    DevTile& T = c->ds.tl;
+    if (finite_cut(c->cfg)) {
+        T.on = 0;
+        return BOUNCE_OK;
+    }
+    if (c->rep_bounds.size() < 2) c->rep_bounds = {0, c->n};
+    std::vector<int4> items;
+    for (size_t r = 0; r + 1 < c->rep_bounds.size(); ++r) {
+        const int b = c->rep_bounds[r], e = c->rep_bounds[r + 1];
+        for (int i0 = b; i0 < e; i0 += 32)
+            for (int j0 = i0; j0 < e; j0 += c->tile_j)
+                items.push_back(make_int4(i0, std::min(32, e - i0), j0, std::min(c->tile_j, e - j0)));
+    }
+    int r;
+    if ((int)items.size() > c->tile_cap) {
+        if ((r = dalloc(c, &c->tile_items, items.size()))) return r;
+        c->tile_cap = (int)items.size();
+    }
+    if (!T.acc && (r = dalloc(c, &T.acc, 3 * (size_t)c->n))) return r;
+    CU(cudaMemcpy(c->tile_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    T.on = 1;
+    T.items = c->tile_items;
+    T.nitems = (int)items.size();
+    T.tj = c->tile_j;
+    T.blocks = c->tile_blocks;
+    drop_graphs(c);
+    return BOUNCE_OK;
+}
+
+// Raise the cluster rebuild flag (positions were replaced).
+int flag_clusters(bounce_ctx* c, cudaStream_t st) {
+    if (!c->ds.cl.on) return BOUNCE_OK;
+    static const int one = 1;
+    CU(cudaMemcpyAsync(c->ds.cl.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    return BOUNCE_OK;
+}
+
+// Launch the rebuild sequence of the candidate rows (gated by the device
+// flag unless forced).  After BAOAB runs on clusters the step kernel did not
+// test the rows' displacement, so it is tested here first, at the current
+// positions (the test the oracle applies before every use of the rows).
 void rebuild(bounce_ctx* c, int step_off, bool force, cudaStream_t st) {
+    if (c->rows_check_due) {
+        long long step = c->cur_step;
+        if (step_off == 0) launch_flag_moved(c->ds, c->pp, (int)(step & 1), st);
+        c->rows_check_due = false;
+    }
     launch_rebuild(c->ds, c->pp, step_off, force, c->bitmap_warps, c->bitmap_bytes, st);
 }
 
@@ -517,13 +749,48 @@ void plan(const bounce_ctx* c, int integ, int variant, long long step, bool& pme
     }
 }
 
+// System view of a run of `integ`: BAOAB on clusters needs no candidate
+// rows, so its step kernel does not test them (rows_flag = 0).
+DevSys run_view(const bounce_ctx* c, int integ) {
+    DevSys s = c->ds;
+    s.rows_flag = (integ == BOUNCE_BAOAB && s.cl.on) ? 0 : 1;
+    const int sk = c->cfg.step_kernel;
+    s.lite = sk == 2 ? 1 : (sk == 1 ? 0 : ((integ == BOUNCE_BAOAB || c->lite_jumps) ? 1 : 0));
+    return s;
+}
+
+// Expected jump proposals per atom-step from the bounds: beta <|v_a|> L*_a
+// n delta summed over the atoms' types, with <|v_a|> = sqrt(8 k_B T / (pi
+// m_a)) and n the atoms within r_list at density rho (an upper bound of the
+// rate: the per-type-pair bounds only lower it).
+double expected_proposals(const bounce_ctx* c, double rho) {
+    const bounce_config& g = c->cfg;
+    const double beta = 1.0 / (KB_D * g.temperature_K);
+    const double rl = r_list(g);
+    const double nbar = std::isfinite(rl) ? std::min((double)c->n, rho * 4.18879 * rl * rl * rl) : (double)c->n;
+    double sum = 0.0;
+    for (int i = 0; i < c->n; ++i) {
+        const double vbar = std::sqrt(8.0 * KB_D * g.temperature_K * ACCEL_D / (M_PI * c->mass[i]));
+        sum += beta * vbar * c->Lstar[c->type[i]] * nbar * g.dt_fs;
+    }
+    return sum / c->n;
+}
+
+// The gated rebuilds at one step boundary: the clusters (their own flag) and
+// the candidate rows, which only the jump step reads (BOUNCE integrators, or
+// every integrator without clusters, whose pair sums run over the rows).
+void rebuild_for(bounce_ctx* c, int integ, int off, cudaStream_t st) {
+    if (c->ds.cl.on) launch_cluster_rebuild(c->ds, c->pp, off, false, st);
+    if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st);
+}
+
 void boundary(bounce_ctx* c, int integ, int variant, int off, long long step, cudaStream_t st) {
     bool pme;
     double hr, hout;
     plan(c, integ, variant, step, pme, hr, hout);
-    rebuild(c, off, false, st);
+    rebuild_for(c, integ, off, st);
     if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
-    launch_step(c->ds, c->pp, integ, variant, off, hr, hout, st);
+    launch_step(run_view(c, integ), c->pp, integ, variant, off, hr, hout, st);
 }
 
 // Steps after which the kick pattern of the integrator repeats.
@@ -600,7 +867,7 @@ int bounce_create(bounce_ctx** out, const bounce_config* cfg) {
     *out = nullptr;
     if (!(cfg->dt_fs > 0) || !(cfg->temperature_K > 0) || cfg->gamma_per_fs < 0 || cfg->skin < 0 ||
         cfg->max_neighbors < 1 || cfg->max_short < 1 || !(cfg->r_off >= cfg->r_on) || cfg->r_on < 0 ||
-        cfg->ewald_beta < 0)
+        cfg->ewald_beta < 0 || !(cfg->pair_skin >= 0) || cfg->step_kernel < 0 || cfg->step_kernel > 2)
         return BOUNCE_ERR_INVALID_ARG;
     if (cfg->periodic && !(cfg->box[0] > 0 && cfg->box[1] > 0 && cfg->box[2] > 0)) return BOUNCE_ERR_INVALID_ARG;
     if (cfg->respa_m < 1 || cfg->respa_m > 8 || cfg->respa_m2 < 1 || cfg->respa_m2 > 8) return BOUNCE_ERR_INVALID_ARG;
@@ -693,7 +960,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     const double rs = c->cfg.r_off + c->cfg.skin;
     // Short rows exist only when they are a strict subset of the long rows;
     // otherwise F_0 reads the long rows (rshort2 = +inf) and one slot is kept.
-    const bool distinct_short = c->cfg.jump_coulomb && std::isfinite(rs) && rs < rl;
+    const bool distinct_short = short_rows(c->cfg) && rs < rl;
     s.caps = distinct_short ? c->cfg.max_short : 1;
     if ((r = dalloc(c, &s.vx, n)) || (r = dalloc(c, &s.vy, n)) || (r = dalloc(c, &s.vz, n)) ||
         (r = dalloc(c, &kick, n)) || (r = dalloc(c, &osd, n)) || (r = dalloc(c, &dtype, n)) ||
@@ -718,6 +985,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     s.bt_idx = bidx;
     s.bt_par = bpar;
     s.step_base = c->d_step;
+    s.rows_flag = 1;
     std::vector<double> hk(n), ho(n);
     const double c1 = std::exp(-c->cfg.gamma_per_fs * c->cfg.dt_fs);
     for (int i = 0; i < n; ++i) {
@@ -746,31 +1014,18 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
         CU(cudaMemcpy(s.phi[b], hh.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(s.plo[b], hl.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
     }
-    // bitmap shared memory of the row builder
-    int dev = c->cfg.device, optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t words = (size_t)(n + 31) / 32;
-    // Row builder.  Per warp of the warp-per-atom kernel: the long-row
-    // bitmaps (one per partner type with per-type-pair bounds) and the
-    // short-row bitmap, each rounded to 16 bytes, and 3 x 128 ints of
-    // cell-row runs.  When that exceeds 8 KB (large systems: the bitmaps span
-    // all atoms) the CTA-per-atom kernel runs instead, with one such set per
-    // CTA plus a touched flag per 32-word group, a count per (bitmap, group)
-    // and the list of touched groups.
-    const size_t nbm = (c->cfg.pair_bounds ? (size_t)c->n_types : 1) + 1;
-    const size_t per_warp = nbm * ((words + 3) / 4 * 16) + 3 * 128 * 4;
-    const size_t groups = (words + 31) / 32;
-    const size_t per_cta = nbm * ((words + 3) / 4 * 16) + (groups + 15) / 16 * 16 + (nbm * groups + 3) / 4 * 16 +
-                           (groups + 3) / 4 * 16 + 3 * 128 * 4;
-    if (per_warp <= 8192) {
-        c->bitmap_warps = 8;
-        c->bitmap_bytes = per_warp * 8;
-    } else {
-        if (per_cta > (size_t)optin) return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for the row builder bitmap");
-        c->bitmap_warps = 0;
-        c->bitmap_bytes = per_cta;
-    }
+    // Row builder: per warp, the bitmaps over a window of atom indices (one
+    // per partner type with per-type-pair bounds, plus the short-row bitmap
+    // when short rows exist) and 3 x 128 ints of cell-row runs, at most 8 KB;
+    // the window spans every atom when that fits (short rows need it).
+    const int words = (n + 31) / 32;
+    const int nbm = (c->cfg.pair_bounds ? c->n_types : 1) + (distinct_short ? 1 : 0);
+    const int wmax = ((8192 - 3 * 128 * 4) / (4 * nbm)) & ~3;
+    c->bitmap_warps = std::min((words + 3) & ~3, wmax);  // window words per bitmap
+    c->bitmap_bytes = (size_t)8 * ((size_t)nbm * c->bitmap_warps + 3 * 128) * 4;
     nlist_set_smem_limit(c->bitmap_bytes);
+    c->rep_bounds = {0, n};
+    if ((r = setup_tiles(c))) return r;
     c->have_topo = true;
     return BOUNCE_OK;
 }
@@ -818,15 +1073,34 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
     for (size_t k = 0; k < n3; ++k)
         if (!std::isfinite(hq[k]) || !std::isfinite(hv[k]))
             return fail(c, BOUNCE_ERR_NONFINITE, "non-finite position or velocity");
+    // short rows (systems without a cutoff) need one row-builder window over every atom
+    if (!c->ds.rep_of && c->pp.rshort2 < INFINITY && c->bitmap_warps < (c->n + 31) / 32)
+        return fail(c, BOUNCE_ERR_UNSUPPORTED, "too many atoms for short rows without a cutoff");
     const DevSys before = c->ds;
     int r = setup_grid(c, hq);
     if (r) return r;
+    if ((r = setup_clusters(c, hq))) return r;
+    {
+        // density for the rate estimate: the box, or half the droplet's bounding box
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, vol = 1.0;
+        for (int i = 0; i < c->n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], hq[3 * i + d]);
+                hi[d] = std::max(hi[d], hq[3 * i + d]);
+            }
+        for (int d = 0; d < 3; ++d) vol *= c->cfg.periodic ? c->cfg.box[d] : std::max(hi[d] - lo[d], 1.0);
+        const double rho = c->n / (c->cfg.periodic ? vol : 0.55 * vol);
+        const bool lite = expected_proposals(c, rho) < 0.5;
+        if (lite != c->lite_jumps) drop_graphs(c);
+        c->lite_jumps = lite;
+    }
     // captured graphs hold the system view by value: recapture only if the grid changed
     const DevSys& g = c->ds;
     if (g.ncx != before.ncx || g.ncy != before.ncy || g.ncz != before.ncz || g.ox != before.ox || g.oy != before.oy ||
         g.oz != before.oz || g.ihx != before.ihx || g.ihy != before.ihy || g.ihz != before.ihz ||
         g.mx != before.mx || g.my != before.my || g.mz != before.mz ||
-        g.cell_count != before.cell_count || g.cell_start != before.cell_start || g.cell_fill != before.cell_fill)
+        g.cell_count != before.cell_count || g.cell_start != before.cell_start || g.cell_fill != before.cell_fill ||
+        std::memcmp(&g.cl, &before.cl, sizeof(DevClu)) != 0)
         drop_graphs(c);
     const int cur = (int)(step & 1);
     DevSys& s = c->ds;
@@ -854,6 +1128,8 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
         CU(cudaMemcpyAsync(s.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
         c->rows_valid = true;
     }
+    if ((r = flag_clusters(c, st))) return r;
+    c->rows_check_due = false;
     CU(cudaMemsetAsync(s.err, 0, sizeof(int), st));
     CU(cudaStreamSynchronize(st));
     c->step0 = step;
@@ -912,6 +1188,7 @@ int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
     // tail: [J] B/2
     boundary(c, integ, 2, 0, s0 + n_steps, st);
     c->cur_step = s0 + n_steps;
+    if (integ == BOUNCE_BAOAB && c->ds.cl.on) c->rows_check_due = true;
     CU(cudaGetLastError());
     return check_err(c, st);
 }
@@ -931,10 +1208,10 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
         bool pme;
         double hr, hout;
         plan(c, integ, variant, step, pme, hr, hout);
-        rebuild(c, off, false, st);
+        rebuild_for(c, integ, off, st);
         if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
         cudaEventRecord(ev[2 * k], st);
-        launch_step(c->ds, c->pp, integ, variant, off, hr, hout, st);
+        launch_step(run_view(c, integ), c->pp, integ, variant, off, hr, hout, st);
         cudaEventRecord(ev[2 * k + 1], st);
     };
     timed(0, 0, 0, s0);
@@ -943,6 +1220,7 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
     if (n_steps > 1) launch_advance_step(c->ds, n_steps - 1, st);
     timed((int)n_steps, 2, 0, s0 + n_steps);
     c->cur_step = s0 + n_steps;
+    if (integ == BOUNCE_BAOAB && c->ds.cl.on) c->rows_check_due = true;
     CU(cudaStreamSynchronize(st));
     double tot = 0.0;
     for (int64_t k = 0; k <= n_steps; ++k) {
@@ -956,14 +1234,163 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
     return check_err(c, st);
 }
 
+int bounce_profile_breakdown(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream, double* ms,
+                             int64_t* groups) {
+    if (!c) return BOUNCE_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    if (n_steps < 1 || !ms) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad profile arguments");
+    if (int r0 = check_run_args(c, n_steps, integ)) return r0;
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    constexpr int NK = 5;  // pair sums, step kernel, row rebuild, cluster rebuild, SPME
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    auto mark = [&](int k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        kind.push_back(k);
+        return true;
+    };
+    const long long s0 = c->cur_step;
+    bool ok = true;
+    auto one = [&](int variant, int off, long long step) {
+        bool pme;
+        double hr, hout;
+        plan(c, integ, variant, step, pme, hr, hout);
+        const DevSys v = run_view(c, integ);
+        ok = ok && mark(-1);
+        if (c->ds.cl.on) launch_cluster_rebuild(c->ds, c->pp, off, false, st);
+        ok = ok && mark(3);
+        if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st);
+        ok = ok && mark(2);
+        if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
+        ok = ok && mark(4);
+        const int pre = launch_step_pairs(v, c->pp, integ, off, hout, st);
+        ok = ok && mark(0);
+        launch_step_kernel(v, c->pp, integ, variant, off, hr, hout, pre, st);
+        ok = ok && mark(1);
+    };
+    one(0, 0, s0);
+    launch_advance_step(c->ds, 1, st);
+    for (int64_t k = 0; k < n_steps - 1; ++k) one(1, (int)k, s0 + 1 + k);
+    if (n_steps > 1) launch_advance_step(c->ds, n_steps - 1, st);
+    one(2, 0, s0 + n_steps);
+    c->cur_step = s0 + n_steps;
+    if (integ == BOUNCE_BAOAB && c->ds.cl.on) c->rows_check_due = true;
+    CU(cudaStreamSynchronize(st));
+    for (int k = 0; k < NK; ++k) {
+        ms[k] = 0.0;
+        if (groups) groups[k] = 0;
+    }
+    for (size_t e = 1; e < ev.size(); ++e) {
+        if (kind[e] < 0) continue;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[e - 1], ev[e]);
+        ms[kind[e]] += t;
+        if (groups) groups[kind[e]] += 1;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (!ok) return fail(c, BOUNCE_ERR_CUDA, "cudaEventCreate failed");
+    return check_err(c, st);
+}
+
+int bounce_autotune(bounce_ctx* c, int32_t integ, void* stream, bounce_tuning* out) {
+    if (!c || !out || integ < BOUNCE_BAOAB || integ > BOUNCE_BOUNCE_RESPA1)
+        return fail(c, BOUNCE_ERR_INVALID_ARG, "bad autotune arguments");
+    if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
+    cudaSetDevice(c->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::memset(out, 0, sizeof(*out));
+    const int part = integ == BOUNCE_BAOAB ? 5 : 3;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    constexpr int REPS = 5;
+    auto time_pairs = [&](auto launch) -> double {
+        launch();  // warm
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < REPS; ++k) launch();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / REPS;
+    };
+    int r = BOUNCE_OK;
+    if (c->ds.tl.on) {
+        // tile kernel: j-block length x resident grid
+        const int tjs[4] = {32, 64, 128, 256}, grids[3] = {152 * 2, 152 * 4, 152 * 8};
+        double best = 1e30;
+        int bj = c->tile_j, bg = c->tile_blocks;
+        for (int tj : tjs)
+            for (int gb : grids) {
+                c->tile_j = tj;
+                c->tile_blocks = gb;
+                if ((r = setup_tiles(c))) break;
+                const double ms = time_pairs([&] { launch_tile_pairs(c->ds, c->pp, 0, part, st); });
+                ++out->candidates;
+                if (ms < best) {
+                    best = ms;
+                    bj = tj;
+                    bg = gb;
+                }
+            }
+        c->tile_j = bj;
+        c->tile_blocks = bg;
+        if (!r) r = setup_tiles(c);
+        CU(cudaMemsetAsync(c->ds.tl.acc, 0, 3 * (size_t)c->n * sizeof(unsigned long long), st));
+        out->tile_j = bj;
+        out->tile_blocks = bg;
+        out->pair_ms = best;
+    } else if (c->ds.cl.on) {
+        // cluster columns: edge factor around (8 / density)^(1/3)
+        std::vector<double> q(3 * (size_t)c->n);
+        if ((r = bounce_get_state(c, q.data(), nullptr, BOUNCE_HOST, stream))) return r;
+        const double fs[5] = {0.8, 0.9, 1.0, 1.12, 1.25};
+        double best = 1e30, bf = c->cl_edge_factor;
+        const int list = (part == 3 && c->ds.cl.nlists > 1) ? 1 : 0;
+        for (double f : fs) {
+            c->cl_edge_factor = f;
+            c->cl_force = true;
+            if ((r = setup_clusters(c, q.data()))) break;
+            launch_cluster_rebuild(c->ds, c->pp, 0, true, st);
+            const double ms = time_pairs([&] { launch_cluster_pairs(c->ds, c->pp, 0, part, list, st); });
+            ++out->candidates;
+            if (ms < best) {
+                best = ms;
+                bf = f;
+            }
+        }
+        c->cl_edge_factor = bf;
+        c->cl_force = true;
+        if (!r) r = setup_clusters(c, q.data());
+        if (!r) launch_cluster_rebuild(c->ds, c->pp, 0, true, st);
+        const size_t ns = (size_t)c->ds.cl.ncol * c->ds.cl.maxcl * BOUNCE_CL;
+        CU(cudaMemsetAsync(c->ds.cl.acc, 0, 3 * ns * sizeof(unsigned long long), st));
+        out->column_edge = 1.0 / c->ds.cl.ihx;
+        out->pair_ms = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_graphs(c);
+    CU(cudaStreamSynchronize(st));
+    if (r) return r;
+    return check_err(c, st);
+}
+
 int64_t bounce_run_launch_count(const bounce_ctx* c, int64_t n, int32_t integ) {
     if (!c || n <= 0) return 0;
     // gated row-rebuild kernels (cells count + scan, scatter, rows + flag clear;
     // one kernel for a batch of replicas) + the fused step kernel, and the
     // pair-sum kernel wherever the boundary has pair sums over the long rows
-    const int64_t per_boundary = (c->ds.rep_of ? 1 : 3) + 1;
+    const bool clu = c->ds.cl.on != 0;
+    // gated rebuilds: the clusters (4), the rows (3, or 1 for a batch) unless
+    // BAOAB runs on clusters; then the step kernel
+    const int64_t per_boundary = (clu ? 4 : 0) + ((clu && integ == BOUNCE_BAOAB) ? 0 : (c->ds.rep_of ? 1 : 3)) + 1;
     const bool ext = integ >= BOUNCE_BOUNCE_RESPA_EXT;
-    const bool short_f0 = integ != BOUNCE_BAOAB && c->pp.rshort2 < INFINITY;
+    const bool short_f0 = !clu && integ != BOUNCE_BAOAB && c->pp.rshort2 < INFINITY;
     const int64_t pme_launches = 10; // spread, load, 3 + 3 transforms, convolve, gather
     int64_t total = 2;               // step-counter updates after the head and the bodies
     for (int64_t k = 0; k <= n; ++k) {
@@ -1115,6 +1542,22 @@ int bounce_compute_gradient(bounce_ctx* c, int32_t part, double* grad, int32_t w
         for (int d = 0; d < 3; ++d)
             CU(cudaMemcpy2DAsync(grad + d, 3 * sizeof(double), c->pme.grad + (size_t)d * c->n, sizeof(double),
                                  sizeof(double), c->n, kind, st));
+    } else if (c->ds.tl.on && (part == BOUNCE_GRAD_FULL || (part == BOUNCE_GRAD_SHORT && !(c->pp.rshort2 < INFINITY)))) {
+        // bonded terms, then the all-pairs tile sums added (the run's kernels)
+        double* out = c->terms;
+        launch_gradient(c->ds, c->pp, 4, (int)(step & 1), out, st);
+        launch_tile_pairs(c->ds, c->pp, 0, part == BOUNCE_GRAD_FULL ? 5 : 3, st);
+        launch_tile_collect(c->ds, out, st);
+        CU(cudaMemcpyAsync(grad, out, 3 * (size_t)c->n * sizeof(double), kind, st));
+    } else if (c->ds.cl.on && part != BOUNCE_GRAD_LONG) {
+        // bonded terms, then the cluster pair sums added (the run's kernels)
+        double* out = c->terms;
+        launch_cluster_rebuild(c->ds, c->pp, 0, false, st);
+        launch_gradient(c->ds, c->pp, 4, (int)(step & 1), out, st);
+        const bool full = part == BOUNCE_GRAD_FULL;
+        launch_cluster_pairs(c->ds, c->pp, 0, full ? 5 : 3, (!full && c->ds.cl.nlists > 1) ? 1 : 0, st);
+        launch_cluster_collect(c->ds, out, st);
+        CU(cudaMemcpyAsync(grad, out, 3 * (size_t)c->n * sizeof(double), kind, st));
     } else {
         double* out = c->terms;  // scratch of 6 n doubles >= 3 n
         launch_gradient(c->ds, c->pp, part, (int)(step & 1), out, st);
@@ -1211,6 +1654,8 @@ int bounce_set_replicas(bounce_ctx* c, int32_t n_rep, const int32_t* off, const 
     c->ds.local_idx = dloc;
     c->ds.rep_off = doff;
     c->ds.rep_key = dkey;
+    c->rep_bounds.assign(off, off + n_rep + 1);
+    if ((rr = setup_tiles(c))) return rr;
     drop_graphs(c);
     c->rows_valid = false;
     return BOUNCE_OK;
@@ -1252,6 +1697,7 @@ int bounce_pair_forward(bounce_ctx* c, const double* q, int32_t T, const double*
         CU(cudaMemcpy2DAsync(c->ds.qz[cur], sizeof(double), q + 2, 3 * sizeof(double), sizeof(double), n,
                              cudaMemcpyDeviceToDevice, st));
         launch_pack_positions(c->ds, c->pp, cur, st);
+        if ((r = flag_clusters(c, st))) return r;
         rebuild(c, 0, true, st);
     } else {
         rebuild(c, 0, false, st);

@@ -24,6 +24,74 @@ constexpr double KCOUL_D = 332.063713;
 constexpr double KB_D = 0.0019872041;
 constexpr double ACCEL_D = 4.184e-4;
 
+// Cluster-pair structure of the pair sums (finite cutoff, one system):
+// atoms binned into columns of a grid over (x, y), sorted by z inside each
+// column and cut into clusters of BOUNCE_CL consecutive atoms; cluster I of
+// column col has id col * maxcl + k and owns slots id * BOUNCE_CL + t.  The
+// list of cluster I holds every atom of a cluster J >= I that lies within a
+// search radius (r_c, or the short-range radius, plus the skin) of I's
+// bounding box, with the periodic image code of the pair; the pair kernel
+// sums both sides of every pair once (Newton's third law) into int64
+// fixed-point accumulators, one per slot and component.
+#define BOUNCE_CL 8
+#define BOUNCE_CL_EPW 256          // list entries per work item of the pair kernel
+#define BOUNCE_CL_MAXCOL 1024      // atoms per column (one CTA sorts a column in shared memory)
+constexpr double CL_FIX = 4294967296.0;        // fixed-point scale 2^32 of the accumulators
+constexpr double CL_UNFIX = 2.3283064365386963e-10;  // 2^-32
+
+struct DevClu {
+    int on;                  // the pair sums run over clusters
+    int ncx, ncy, ncol;      // column grid
+    float ox, oy;            // grid origin (droplets)
+    float ihx, ihy;          // inverse column edges
+    int maxcl;               // cluster ids per column
+    int maxcol;              // atoms per column (<= BOUNCE_CL_MAXCOL)
+    int nlists;              // 1, or 2 with a distinct short-range list
+    int capj[2];             // entries per cluster of each list
+    float rs2[2];            // squared search radii of the lists (with margins)
+    float rsx[2];            // the radii themselves
+    int capitems;            // work items per list
+    double cskin_half2;      // rebuild when an atom moved more than skin/2 since the build
+    int* col_count;          // [ncol]
+    int* col_start;          // [ncol + 1]
+    int* col_fill;           // [ncol]
+    int* col_atoms;          // [n] atoms in column order
+    int* col_ncl;            // [ncol] clusters of each column
+    int* atom_col;           // [n] column of each atom at the build
+    int* cl_atom;            // [ncl * CL] atom of each slot (-1: padding)
+    int* a2s;                // [n] slot of each atom
+    float4* sphi[2];         // slot-ordered copies of phi / plo (same buffers as the positions)
+    float4* splo[2];
+    int* smol;               // [ncl * CL] molecule id (-1: padding)
+    float4* bb_lo;           // [ncl] bounding box of each cluster (high FP32 parts)
+    float4* bb_hi;
+    int* lst[2];             // [ncl * capj] slot of j | image code << 27
+    int* lcnt[2];            // [ncl] entries of each cluster
+    int2* items[2];          // (I, first entry) of each work item
+    int* nitems;             // [2]
+    unsigned long long* acc; // [3 * ncl * CL] fixed-point gradient sums (x, y, z blocks)
+    double* crefx;           // [n] positions at the build
+    double* crefy;
+    double* crefz;
+    double* cofx;            // [n] periodic image offset L floor(q / L) of each atom at the build:
+    double* cofy;            //     the slot copies keep q - cof until the next build, so that the
+    double* cofz;            //     image codes of the lists stay valid when atoms cross a face
+    int* rebuild;            // 1 = the clusters must be rebuilt before the next pair sums
+    unsigned int* done_ctr;  // [2] finished-CTA counters (zero between launches)
+};
+
+// All-pairs sums (systems without a cutoff): static items (first i, count,
+// first j, count) of 32-atom i-tiles against j-blocks of one replica, and
+// atom-indexed int64 fixed-point accumulators.
+struct DevTile {
+    int on;                  // the pair sums over all pairs run over tiles
+    int nitems;
+    int blocks;              // resident grid of the tile kernel
+    int tj;                  // atoms per j-block
+    const int4* items;
+    unsigned long long* acc; // [3 n] (x, y, z blocks)
+};
+
 // Device pointers of one system (passed by value).
 struct DevSys {
     int n;
@@ -81,6 +149,10 @@ struct DevSys {
     const int* local_idx;
     const uint2* rep_key;
     const int* rep_off;      // [replicas + 1] first atom of each replica
+    DevClu cl;               // cluster-pair structure (cl.on = 0: pair sums over the rows)
+    DevTile tl;              // all-pairs tiles (systems without a cutoff)
+    int rows_flag;           // the step kernel raises `rebuild` for the rows (0 in BAOAB runs on clusters)
+    int lite;                // thread-per-atom step kernel (rare jump proposals)
 };
 
 // Smooth particle-mesh Ewald state (periodic boxes with a reciprocal part).
@@ -330,6 +402,59 @@ __device__ __forceinline__ float chi_of(const Params& p, float r) {
     return s * s * s * (10.f + s * (-15.f + 6.f * s));
 }
 
+// 1: the pair sums take erfc from the CUDA library instead of 7.1.26
+#ifndef CL_LIBRARY_ERFC
+#define CL_LIBRARY_ERFC 0
+#endif
+
+// erfc(x) e^{x^2} for x >= 0 by Abramowitz and Stegun, Handbook of
+// Mathematical Functions, 7.1.26: t = 1/(1 + p x), t (a1 + t (a2 + t (a3 +
+// t (a4 + t a5)))); absolute error of erfc(x) below 1.5e-7.  The pair sums
+// use it (with the exp(-x^2) they need for the derivative anyway); the jump
+// step keeps the library erfcf.
+__device__ __forceinline__ float erfc_scaled_as(float x) {
+    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.f));
+    return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                    0.254829592f);
+}
+
+// W'(r)/r of one pair for the pair sums (cluster and tile kernels), without
+// branches on the pair's own values (every lane of a warp runs it; masked
+// pairs pass r2 = 1):
+// PART 5 the full W', PART 3 the F_0 share (1 - chi) W'_sw + W'_fixed.
+template <int PART>
+__device__ __forceinline__ float pairsum_w(const Params& p, float r2, float qq, float c12, float c6) {
+    const float ir = rsqrt_nr(r2);
+    const float ir2 = ir * ir;
+    const float r = r2 * ir;
+    float wc;
+    if (p.ebeta > 0.f) {
+        const float x = p.ebeta * r;
+        const float e = __expf(-x * x);
+#if CL_LIBRARY_ERFC
+        wc = -qq * (erfcf(x) * ir2 + p.e2b_sqrtpi * e * ir) * ir;
+#else
+        wc = -qq * (erfc_scaled_as(x) * e * ir2 + p.e2b_sqrtpi * e * ir) * ir;
+#endif
+    } else {
+        wc = -qq * ir2 * ir;
+    }
+    const float ir6 = ir2 * ir2 * ir2;
+    const float wl = -((12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2);
+    // explicit roundings: the F_0 share with chi = 0 equals the full term bit
+    // for bit whatever the compiler contracts around it
+    const float wsum = __fadd_rn(wc, wl);
+    if (PART == 5) return wsum;
+    float chi;
+    if (p.chi_step) {
+        chi = r >= p.r_off ? 1.f : 0.f;
+    } else {
+        const float sx = fminf(fmaxf((r - p.r_on) * p.inv_span, 0.f), 1.f);
+        chi = sx * sx * sx * fmaf(sx, fmaf(6.f, sx, -15.f), 10.f);
+    }
+    return p.coul_jump ? __fmul_rn(wsum, 1.f - chi) : __fadd_rn(__fmul_rn(wl, 1.f - chi), wc);
+}
+
 // Pair energy W(r) components (Coulomb or erfc, LJ), r2 < rc2 assumed.
 __device__ __forceinline__ void pair_W(const Params& p, float r2, float qq, int tp, float& ec, float& el) {
     float ir = rsqrt_nr(r2);
@@ -451,10 +576,14 @@ inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
 }
 
 // Launchers implemented in the .cu files.
-void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
+void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int window_words, size_t bitmap_bytes,
                     cudaStream_t st);
 void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
                  double hout, cudaStream_t st);
+// launch_step in two parts (for per-kernel timing): the pair sums, then the step kernel.
+int launch_step_pairs(const DevSys& s, const Params& p, int integrator, int step_off, double hout, cudaStream_t st);
+void launch_step_kernel(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
+                        double hout, int pre, cudaStream_t st);
 void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st);
 void launch_pme_energy(const DevPme& m, int n, double* out, cudaStream_t st);
 void launch_gradient(const DevSys& s, const Params& p, int part, int cur, double* out, cudaStream_t st);
@@ -468,3 +597,14 @@ void launch_state_out(const DevSys& s, double* q, double* v, cudaStream_t st);
 // Raises the rebuild flag when an atom at positions `cur` lies more than
 // skin/2 from its position at the last row build (the step kernel's test).
 void launch_flag_moved(const DevSys& s, const Params& p, int cur, cudaStream_t st);
+// Cluster-pair path (cluster.cu): gated rebuild of the clusters and lists,
+// the pair sums of `part` (3: F_0 share, 5: full pairs) over list `list`
+// into the fixed-point accumulators, and their read-out (added to out[3n],
+// accumulators cleared).
+void launch_cluster_rebuild(const DevSys& s, const Params& p, int step_off, bool force, cudaStream_t st);
+void launch_cluster_pairs(const DevSys& s, const Params& p, int step_off, int part, int list, cudaStream_t st);
+void launch_cluster_collect(const DevSys& s, double* out, cudaStream_t st);
+// All-pairs tiles (tile.cu): the pair sums of `part` into the atom-indexed
+// accumulators, and their read-out (added to out[3n], accumulators cleared).
+void launch_tile_pairs(const DevSys& s, const Params& p, int step_off, int part, cudaStream_t st);
+void launch_tile_collect(const DevSys& s, double* out, cudaStream_t st);

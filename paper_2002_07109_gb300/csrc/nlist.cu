@@ -7,11 +7,13 @@
 // scatter), then one warp per atom scans the cells that meet its r_list
 // sphere, screens each candidate in FP32 from the high position parts and
 // settles the few candidates near r_list exactly in FP64.  Accepted
-// candidates set a bit in a per-warp bitmap over all atom indices in shared
-// memory (one per partner type with per-type-pair bounds, then a bitmap of
-// the short-row members, r < r_off + skin);
+// candidates set a bit in a per-warp bitmap over a window of atom indices
+// centred on the atom's own (one per partner type with per-type-pair
+// bounds, then a bitmap of the short-row members, r < r_off + skin);
 // reading a bitmap back in word order yields the row already in ascending
-// order (no sort), and duplicate visits of a cell are harmless.
+// order (no sort), and duplicate visits of a cell are harmless.  Members
+// outside the window take further passes (rare when atoms are numbered in
+// spatial order).
 // Every kernel returns at once unless a rebuild is pending (the step kernel
 // raises the flag when an atom has moved more than skin/2 since the last
 // build), so the sequence can sit in a captured CUDA graph.  Three launches:
@@ -25,7 +27,6 @@
 namespace {
 
 constexpr int RANGE_MAX = 128;  // cell-row runs per atom (<= 2 (2*3+1)^2 = 98)
-constexpr int ROWS_NT = 256;    // threads per CTA of the row builder
 
 // Entry of a gated rebuild kernel: after its predecessor in the chain, is a
 // rebuild due (or forced)?
@@ -266,7 +267,8 @@ __device__ int candidate_runs(const DevSys& s, const Params& p, float4 hi, int* 
 
 // Writes the set bits of a warp's bitmap, in ascending order, as indices to
 // row[0 .. cap) and returns their count (which may exceed cap; cap may be
-// zero or negative, then nothing is written).  Passes of 32 words: a prefix
+// zero or negative, then nothing is written); word w of the bitmap stands
+// for atoms 32 (wbase + w) .. 32 (wbase + w) + 31.  Passes of 32 words: a prefix
 // of their popcounts, then the pass's set bits are spread over the lanes,
 // 32 at a time: output k of the pass finds its word by a shuffle search over
 // the prefix and its bit by a popcount halving search, so the stores are
@@ -288,7 +290,7 @@ __device__ __forceinline__ int select_bit(uint32_t b, int r) {
     return pos;
 }
 
-__device__ int expand_bitmap(const uint32_t* bm, int nwords, int* row, int cap) {
+__device__ int expand_bitmap(const uint32_t* bm, int nwords, int* row, int cap, int wbase = 0) {
     const int lane = threadIdx.x & 31;
     int total = 0;
     for (int w0 = 0; w0 < nwords; w0 += 32) {
@@ -316,7 +318,7 @@ __device__ int expand_bitmap(const uint32_t* bm, int nwords, int* row, int cap) 
             const int r = k - __shfl_sync(0xffffffffu, excl, l);
             if (k < tc) {
                 const int pos = total + k;
-                if (pos < cap) row[pos] = ((w0 + l) << 5) + select_bit(b, r);
+                if (pos < cap) row[pos] = ((wbase + w0 + l) << 5) + select_bit(b, r);
             }
         }
         total += tc;
@@ -324,255 +326,178 @@ __device__ int expand_bitmap(const uint32_t* bm, int nwords, int* row, int cap) 
     return total;
 }
 
-// Rows of the cell-list builder, one warp per atom (systems whose bitmaps
-// over all atoms are small): the warp screens the candidates of its atom and
-// sets bits in its own bitmaps, then reads them back in word order.
-__global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int words_per_warp) {
+// Member test of candidate j for atom i at r_list: FP32 screen on the high
+// parts, settled in FP64 inside the band around r_list or when the minimum
+// image is ambiguous in FP32.  r2 receives the FP32 distance squared.
+__device__ __forceinline__ bool row_member(const DevSys& s, const Params& p, int cur, int i, float4 hi, float4 hj,
+                                           int j, float& r2) {
+    float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
+    if (p.periodic) {
+        dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
+        dy -= rintf(dy * p.invL[1]) * p.Lhi[1];
+        dz -= rintf(dz * p.invL[2]) * p.Lhi[2];
+    }
+    r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) return true;
+    if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) return false;
+    return in_list_fp64(s, p, cur, i, j);
+}
+
+// Rows of the cell-list builder, one warp per atom.  The warp's bitmaps (one
+// per partner type with per-type-pair bounds, and one for the short rows)
+// cover a window of `ww` words of atom indices centred on the atom's own
+// index: reading them back in word order yields the row in ascending order
+// without a sort.  The first pass screens the candidates, sets the bits of
+// the members inside the window and counts, per type, the members below and
+// above it; the window's members go to their final place in the row at
+// once.  Members outside the window (index order far from spatial order)
+// take further passes over windows below, then above it, each screening the
+// candidates again; systems numbered in spatial order need one pass, and a
+// window that spans every atom always does.
+__global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww) {
     if (!pending(s, force)) return;
     extern __shared__ uint32_t smem_bm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int nwords = (s.n + 31) >> 5;
-    // long-row bitmaps (one per partner type with per-type-pair bounds), then
-    // the short-row bitmap
-    const int wr = (nwords + 3) & ~3, nbm = p.typed ? p.n_types : 1;
-    uint32_t* bm = smem_bm + (size_t)warp * words_per_warp;
-    uint32_t* bs = bm + (size_t)nbm * wr;
+    const int nbm = p.typed ? p.n_types : 1;
+    const bool has_short = p.rshort2 < INFINITY;  // only when one window spans every atom
+    const int nb = nbm + (has_short ? 1 : 0);
+    const int per_warp = nb * ww + 3 * RANGE_MAX;
+    uint32_t* bm = smem_bm + (size_t)warp * per_warp;
+    uint32_t* bs = bm + (size_t)nbm * ww;  // the short-row bitmap (has_short)
+    int* rb = (int*)(bm + (size_t)nb * ww);
+    int* rl = rb + RANGE_MAX;
+    int* rp = rl + RANGE_MAX;
     const int cur = (int)((*s.step_base + step_off) & 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
+    // the bitmaps start clear; after each atom only the words it touched are cleared
+    for (int w = lane; w < nb * ww; w += 32) bm[w] = 0u;
+    __syncwarp();
     for (int i = blockIdx.x * wpb + warp; i < s.n; i += gridDim.x * wpb) {
-        for (int w = lane; w < (nbm + 1) * wr; w += 32) bm[w] = 0u;
-        __syncwarp();
         const float4 hi = s.phi[cur][i];
         const int mi = s.mol[i];
-        int* rb = (int*)(bm + words_per_warp - 3 * RANGE_MAX);
-        int* rl = rb + RANGE_MAX;
-        int* rp = rl + RANGE_MAX;
         int nr_tot;
         const int total_c = candidate_runs(s, p, hi, rb, rl, rp, nr_tot);
         __syncwarp();
-        // 3) all lanes stride over the concatenated candidates (cell-ordered
-        //    copies: consecutive lanes read consecutive entries of a run)
+        // window A: ww words centred on the atom's word, inside [0, nwords)
+        const int wa = max(0, min((i >> 5) - ww / 2, nwords - ww));
+        const int wz = min(wa + ww, nwords);
+        int below[BOUNCE_MAXT], above[BOUNCE_MAXT];
+#pragma unroll
+        for (int t = 0; t < BOUNCE_MAXT; ++t) below[t] = above[t] = 0;
+        int wmin = nwords, wmax = -1;  // words of the members outside the window
+        int ulo = ww, uhi = -1;        // window words the members touched
         int lo_r = 0;  // run of candidate t: rp[lo_r] <= t < rp[lo_r + 1]; t only grows
         for (int t = lane; t < total_c; t += 32) {
             while (lo_r + 1 < nr_tot && rp[lo_r + 1] <= t) ++lo_r;
             const int idx = rb[lo_r] + (t - rp[lo_r]);
             const int j = s.cell_atoms[idx];
-            const int mj = s.cell_mol[idx];
-            // screen with the high FP32 parts; the band covers their error
-            const float4 hj = s.cell_phi[idx];
-            if (j == i || mj == mi) continue;
-            float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
-            if (p.periodic) {
-                dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
-                dy -= rintf(dy * p.invL[1]) * p.Lhi[1];
-                dz -= rintf(dz * p.invL[2]) * p.Lhi[2];
-            }
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            bool in;
-            if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
-            else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
-            else in = in_list_fp64(s, p, cur, i, j);
-            if (in) {
-                uint32_t* bt = p.typed ? bm + (size_t)s.cell_type[idx] * wr : bm;
-                atomicOr(&bt[j >> 5], 1u << (j & 31));
+            if (j == i || s.cell_mol[idx] == mi) continue;
+            float r2;
+            if (!row_member(s, p, cur, i, hi, s.cell_phi[idx], j, r2)) continue;
+            const int ty = p.typed ? s.cell_type[idx] : 0, w = j >> 5;
+            if (w < wa) {
+                wmin = min(wmin, w);
+#pragma unroll
+                for (int u = 0; u < BOUNCE_MAXT; ++u) below[u] += u == ty;
+            } else if (w >= wz) {
+                wmax = max(wmax, w);
+#pragma unroll
+                for (int u = 0; u < BOUNCE_MAXT; ++u) above[u] += u == ty;
+            } else {
+                atomicOr(&bm[(size_t)ty * ww + (w - wa)], 1u << (j & 31));
+                ulo = min(ulo, w - wa);
+                uhi = max(uhi, w - wa);
                 // short rows: r < r_off + skin (rshort2 carries a 1e-4 margin)
-                if (r2 < p.rshort2) atomicOr(&bs[j >> 5], 1u << (j & 31));
+                if (has_short && r2 < p.rshort2) atomicOr(&bs[w - wa], 1u << (j & 31));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+            wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+            ulo = min(ulo, __shfl_xor_sync(0xffffffffu, ulo, o));
+            uhi = max(uhi, __shfl_xor_sync(0xffffffffu, uhi, o));
+        }
+        const bool outside = __any_sync(0xffffffffu, wmax >= 0 || wmin < nwords);
+        if (outside) {
+#pragma unroll
+            for (int u = 0; u < BOUNCE_MAXT; ++u) {
+                below[u] = warp_sum_i(below[u]);
+                above[u] = warp_sum_i(above[u]);
             }
         }
         __syncwarp();
-        // bitmaps -> ascending rows
-        // (typed rows: the type groups one after the other, group sizes to nseg)
-        int total = 0;
-        for (int t = 0; t < nbm; ++t) {
-            const int c = expand_bitmap(bm + (size_t)t * wr, nwords, s.rows + (size_t)i * s.cap + total,
-                                        s.cap - total);
-            if (p.typed && lane == 0) s.nseg[(size_t)i * BOUNCE_MAXT + t] = c;
-            total += c;
+        // members of window A per type: popcounts over the touched words
+        const int nu = uhi >= ulo ? uhi - ulo + 1 : 0;
+        int inside[BOUNCE_MAXT], seg[BOUNCE_MAXT], total = 0;
+#pragma unroll
+        for (int u = 0; u < BOUNCE_MAXT; ++u) {
+            int c = 0;
+            if (u < nbm)
+                for (int w = lane; w < nu; w += 32) c += __popc(bm[(size_t)u * ww + ulo + w]);
+            inside[u] = warp_sum_i(c);
+            seg[u] = total;
+            total += u < nbm ? below[u] + inside[u] + above[u] : 0;
         }
-        const int ns = p.rshort2 < INFINITY ? expand_bitmap(bs, nwords, s.srows + (size_t)i * s.caps, s.caps) : 0;
-        if (lane == 0) {
-            s.nlong[i] = min(total, s.cap);
-            if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
-            s.nshort[i] = min(ns, s.caps);
-            if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
-            s.refx[i] = s.qx[cur][i];
-            s.refy[i] = s.qy[cur][i];
-            s.refz[i] = s.qz[cur][i];
-        }
-        __syncwarp();
-    }
-    if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
-}
-
-// Rows of the cell-list builder for large systems, one CTA per atom: warp 0
-// finds the candidate runs, all threads screen the candidates and set bits in
-// the CTA's bitmaps (one per partner type with per-type-pair bounds, one for
-// the short rows) and a touched flag per 32-word group; then the touched
-// groups in order, their popcounts and prefix, and the warps expand them into
-// the rows in ascending index and clear them.  The work per atom follows its
-// neighbours, not n, and the bitmaps are shared by the CTA's 8 warps.
-__global__ void __launch_bounds__(ROWS_NT) k_rows_cta(DevSys s, Params p, int step_off, int force) {
-    if (!pending(s, force)) return;
-    extern __shared__ uint32_t smem_bm[];
-    __shared__ int s_nr, s_tc, s_ntg, s_tot[BOUNCE_MAXT + 1];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = ROWS_NT / 32;
-    const int nwords = (s.n + 31) >> 5, wr = (nwords + 3) & ~3, nbm = p.typed ? p.n_types : 1;
-    // short rows exist only for a finite short radius (else F_0 reads the
-    // long rows and srows has a single slot)
-    const bool has_short = p.rshort2 < INFINITY;
-    const int nb = nbm + (has_short ? 1 : 0);  // bitmaps in use
-    const int ngroups = (nwords + 31) >> 5;
-    uint32_t* bm = smem_bm;  // bitmaps b = 0 .. nbm - 1 (long rows), b = nbm (short rows)
-    uint8_t* touched = (uint8_t*)(bm + (size_t)(nbm + 1) * wr);
-    int* goff = (int*)(touched + ((ngroups + 15) & ~15));  // per (bitmap, touched group): count, then offset
-    int* tg = goff + (((nbm + 1) * ngroups + 3) & ~3);     // touched groups, ascending
-    int* rb = tg + ((ngroups + 3) & ~3);
-    int* rl = rb + RANGE_MAX;
-    int* rp = rl + RANGE_MAX;
-    const int cur = (int)((*s.step_base + step_off) & 1);
-    if (blockIdx.x == 0 && tid == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
-    // full clear once; after each atom only its touched groups are cleared
-    for (int w = tid; w < (nbm + 1) * wr; w += ROWS_NT) bm[w] = 0u;
-    for (int g = tid; g < ngroups; g += ROWS_NT) touched[g] = 0;
-    __syncthreads();
-    for (int i = blockIdx.x; i < s.n; i += gridDim.x) {
-        const float4 hi = s.phi[cur][i];
-        const int mi = s.mol[i];
-        if (warp == 0) {
-            int nr;
-            const int tc = candidate_runs(s, p, hi, rb, rl, rp, nr);
-            if (lane == 0) {
-                s_nr = nr;
-                s_tc = tc;
-            }
-        }
-        __syncthreads();
-        // screen the candidates (each thread's t only grows, so its run index
-        // advances monotonically)
-        const int nr = s_nr, tc = s_tc;
-        int lo_r = 0;
-        for (int t = tid; t < tc; t += ROWS_NT) {
-            while (lo_r + 1 < nr && rp[lo_r + 1] <= t) ++lo_r;
-            const int idx = rb[lo_r] + (t - rp[lo_r]);
-            const int j = s.cell_atoms[idx];
-            const int mj = s.cell_mol[idx];
-            // screen with the high FP32 parts; the band covers their error
-            const float4 hj = s.cell_phi[idx];
-            if (j == i || mj == mi) continue;
-            float dx = hi.x - hj.x, dy = hi.y - hj.y, dz = hi.z - hj.z;
-            if (p.periodic) {
-                dx -= rintf(dx * p.invL[0]) * p.Lhi[0];
-                dy -= rintf(dy * p.invL[1]) * p.Lhi[1];
-                dz -= rintf(dz * p.invL[2]) * p.Lhi[2];
-            }
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            bool in;
-            if (r2 < p.rlist2_lo && !image_ambiguous(p, hi, hj)) in = true;
-            else if (r2 > p.rlist2_hi && !image_ambiguous(p, hi, hj)) in = false;
-            else in = in_list_fp64(s, p, cur, i, j);
-            if (in) {
-                uint32_t* bt = p.typed ? bm + (size_t)s.cell_type[idx] * wr : bm;
-                atomicOr(&bt[j >> 5], 1u << (j & 31));
-                touched[j >> 10] = 1;  // every thread writes the same value: no atomic needed
-                // short rows: r < r_off + skin (rshort2 carries a 1e-4 margin)
-                if (has_short && r2 < p.rshort2) atomicOr(&bm[(size_t)nbm * wr + (j >> 5)], 1u << (j & 31));
-            }
-        }
-        __syncthreads();
-        // the touched groups, ascending (warp 0)
-        if (warp == 0) {
-            int k = 0;
-            for (int g0 = 0; g0 < ngroups; g0 += 32) {
-                const int g = g0 + lane;
-                const bool t = g < ngroups && touched[g];
-                const uint32_t m = __ballot_sync(0xffffffffu, t);
-                if (t) tg[k + __popc(m & ((1u << lane) - 1u))] = g;
-                k += __popc(m);
-            }
-            if (lane == 0) s_ntg = k;
-        }
-        __syncthreads();
-        const int ntg = s_ntg, nitems = nb * ntg;
-        // members per (bitmap, touched group)
-        for (int it = warp; it < nitems; it += nwarp) {
-            const int b = it / ntg, g = tg[it - b * ntg];
-            const int w = (g << 5) + lane;
-            const int c = warp_sum_i(w < nwords ? __popc(bm[(size_t)b * wr + w]) : 0);
-            if (lane == 0) goff[it] = c;
-        }
-        __syncthreads();
-        // exclusive prefix: the long bitmaps one after the other (typed rows:
-        // type groups in order), the short bitmap on its own
-        if (warp == 0) {
-            int run = 0;
-            for (int b = 0; b < nb; ++b) {
-                if (b == nbm) run = 0;
-                int tb = 0;
-                for (int k0 = 0; k0 < ntg; k0 += 32) {
-                    const int k = k0 + lane;
-                    const int c = k < ntg ? goff[b * ntg + k] : 0;
-                    int x = c;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    if (k < ntg) goff[b * ntg + k] = run + tb + x - c;
-                    tb += __shfl_sync(0xffffffffu, x, 31);
-                }
-                if (lane == 0) s_tot[b] = tb;
-                run += tb;
-            }
-        }
-        __syncthreads();
-        // expand: lane w of the warp owns word w of the group; then clear it
+        // window A in place (touched words only, cleared after): type group u
+        // starts at seg[u], its members below the window first
         int* row = s.rows + (size_t)i * s.cap;
-        int* srow = s.srows + (size_t)i * s.caps;
-        for (int it = warp; it < nitems; it += nwarp) {
-            const int b = it / ntg, g = tg[it - b * ntg];
-            const int w = (g << 5) + lane;
-            const uint32_t bits = w < nwords ? bm[(size_t)b * wr + w] : 0u;
-            const int c = __popc(bits);
-            int x = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            // the group's T set bits spread over the lanes: bit k lies in the
-            // last word whose exclusive prefix is <= k (a shuffle binary
-            // search), at its (k - prefix)-th set bit (a popcount descent)
-            const int pre = x - c, T = __shfl_sync(0xffffffffu, x, 31), base = goff[it];
-            int* out = b < nbm ? row : srow;
-            const int cap = b < nbm ? s.cap : s.caps;
-            for (int k0 = 0; k0 < T; k0 += 32) {
-                const int k = k0 + lane;
-                int src = 0;
+        for (int u = 0; u < nbm; ++u) {
+            int off = 0;
 #pragma unroll
-                for (int h = 16; h > 0; h >>= 1) {
-                    const int pc = __shfl_sync(0xffffffffu, pre, src + h);
-                    if (pc <= k) src += h;
-                }
-                uint32_t v = __shfl_sync(0xffffffffu, bits, src);
-                int r = k - __shfl_sync(0xffffffffu, pre, src), pos = 0;
-#pragma unroll
-                for (int h = 16; h >= 1; h >>= 1) {
-                    const int lowc = __popc(v & ((1u << h) - 1u));
-                    if (r >= lowc) {
-                        r -= lowc;
-                        v >>= h;
-                        pos += h;
-                    }
-                }
-                if (k < T && base + k < cap) out[base + k] = (((g << 5) + src) << 5) + pos;
-            }
-            if (w < nwords) bm[(size_t)b * wr + w] = 0u;
+            for (int v = 0; v < BOUNCE_MAXT; ++v) off = v == u ? seg[v] + below[v] : off;
+            expand_bitmap(bm + (size_t)u * ww + ulo, nu, row + off, s.cap - off, wa + ulo);
         }
-        if (tid == 0) {
-            int total = 0;
-            for (int b = 0; b < nbm; ++b) {
-                if (p.typed) s.nseg[(size_t)i * BOUNCE_MAXT + b] = s_tot[b];
-                total += s_tot[b];
+        const int ns = has_short ? expand_bitmap(bs + ulo, nu, s.srows + (size_t)i * s.caps, s.caps, wa + ulo) : 0;
+        __syncwarp();
+        for (int u = 0; u < nb; ++u)
+            for (int w = lane; w < nu; w += 32) bm[(size_t)u * ww + ulo + w] = 0u;
+        __syncwarp();
+        // further windows: below window A (ascending from the lowest member), then above it
+        if (outside)
+            for (int side = 0; side < 2; ++side) {
+                int w0 = side == 0 ? wmin : wz;
+                const int wend = side == 0 ? wa : wmax + 1;
+                int off[BOUNCE_MAXT];
+#pragma unroll
+                for (int u = 0; u < BOUNCE_MAXT; ++u) off[u] = seg[u] + (side == 0 ? 0 : below[u] + inside[u]);
+                for (; w0 < wend; w0 += ww) {
+                    const int w1 = min(w0 + ww, wend);
+                    lo_r = 0;
+                    for (int t = lane; t < total_c; t += 32) {
+                        while (lo_r + 1 < nr_tot && rp[lo_r + 1] <= t) ++lo_r;
+                        const int idx = rb[lo_r] + (t - rp[lo_r]);
+                        const int j = s.cell_atoms[idx];
+                        const int w = j >> 5;
+                        if (w < w0 || w >= w1 || j == i || s.cell_mol[idx] == mi) continue;
+                        float r2;
+                        if (!row_member(s, p, cur, i, hi, s.cell_phi[idx], j, r2)) continue;
+                        const int ty = p.typed ? s.cell_type[idx] : 0;
+                        atomicOr(&bm[(size_t)ty * ww + (w - w0)], 1u << (j & 31));
+                    }
+                    __syncwarp();
+                    for (int u = 0; u < nbm; ++u) {
+                        int o = 0;
+#pragma unroll
+                        for (int v = 0; v < BOUNCE_MAXT; ++v) o = v == u ? off[v] : o;
+                        const int c = expand_bitmap(bm + (size_t)u * ww, w1 - w0, row + o, s.cap - o, w0);
+#pragma unroll
+                        for (int v = 0; v < BOUNCE_MAXT; ++v) off[v] += v == u ? c : 0;
+                    }
+                    __syncwarp();
+                    for (int w = lane; w < nbm * ww; w += 32) bm[w] = 0u;
+                    __syncwarp();
+                }
             }
-            const int ns = has_short ? s_tot[nbm] : 0;
+        if (lane == 0) {
+            if (p.typed)
+                for (int u = 0; u < nbm; ++u) {
+                    int c = 0;
+#pragma unroll
+                    for (int v = 0; v < BOUNCE_MAXT; ++v) c = v == u ? below[v] + inside[v] + above[v] : c;
+                    s.nseg[(size_t)i * BOUNCE_MAXT + u] = c;
+                }
             s.nlong[i] = min(total, s.cap);
             if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
             s.nshort[i] = min(ns, s.caps);
@@ -581,8 +506,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_rows_cta(DevSys s, Params p, int st
             s.refy[i] = s.qy[cur][i];
             s.refz[i] = s.qz[cur][i];
         }
-        for (int k = tid; k < ntg; k += ROWS_NT) touched[tg[k]] = 0;
-        __syncthreads();
+        __syncwarp();
     }
     if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
 }
@@ -661,7 +585,7 @@ void launch_flag_moved(const DevSys& s, const Params& p, int cur, cudaStream_t s
     k_flag_moved<<<(s.n + 255) / 256, 256, 0, st>>>(s, p, cur);
 }
 
-void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int bitmap_warps, size_t bitmap_bytes,
+void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int window_words, size_t bitmap_bytes,
                     cudaStream_t st) {
     const int f = force ? 1 : 0;
     if (s.rep_of) {
@@ -673,18 +597,12 @@ void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, 
     const int gb = (s.n + tb - 1) / tb;
     launch_chained(k_cells_count, gb, tb, 0, st, s, p, step_off, f);
     launch_chained(k_cells_scatter, gb, tb, 0, st, s, p, step_off, f);
-    if (bitmap_warps > 0) {  // warp per atom, a grid-stride loop over one wave of CTAs
-        const int words = (int)(bitmap_bytes / 4 / bitmap_warps);
-        const int per_sm = std::max(1, std::min(8, (int)((227u << 10) / std::max<size_t>(bitmap_bytes, 1))));
-        const int blocks = std::min((s.n + bitmap_warps - 1) / bitmap_warps, 152 * per_sm);
-        launch_chained(k_rows_warp, blocks, bitmap_warps * 32, bitmap_bytes, st, s, p, step_off, f, words);
-    } else {  // CTA per atom, a grid-stride loop over a GPU-filling grid (an idle launch stays small)
-        const int blocks = std::min(s.n, 152 * 8);
-        launch_chained(k_rows_cta, blocks, ROWS_NT, bitmap_bytes, st, s, p, step_off, f);
-    }
+    // warp per atom, 8 warps per CTA, a grid-stride loop over one wave of CTAs
+    const int per_sm = std::max(1, std::min(8, (int)((227u << 10) / std::max<size_t>(bitmap_bytes, 1))));
+    const int blocks = std::min((s.n + 7) / 8, 152 * per_sm);
+    launch_chained(k_rows_warp, blocks, 256, bitmap_bytes, st, s, p, step_off, f, window_words);
 }
 
 void nlist_set_smem_limit(size_t bytes) {
     cudaFuncSetAttribute(k_rows_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaFuncSetAttribute(k_rows_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }

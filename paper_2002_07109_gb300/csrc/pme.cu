@@ -8,13 +8,14 @@
 //             fixed-point grid (2^40 scale), so the grid is bit-identical
 //             whatever the atomic order;
 //   load      fixed point -> FP32 complex grid; clears the int64 grid;
-//   dft x3    forward transform, one CTA per grid line: the line and a
-//             twiddle table sit in shared memory and each output is a direct
-//             sum over the line (K^2 work per line, FP32);
+//   fft x3    forward transform along each axis: batched mixed-radix
+//             (4, 2, 3, 5) Stockham FFT of 16 lines per CTA in shared memory
+//             (K log K work per line, FP32); grid sizes with another prime
+//             factor take a direct sum per line instead (K^2 work);
 //   convolve  multiply by the influence function B(m) C(m) (FP32 table made
 //             on the host in FP64) and accumulate the energy partials
 //             sum B C |F(Q)|^2 per CTA (FP64);
-//   dft x3    inverse transform (no 1/K normalisation);
+//   fft x3    inverse transform (no 1/K normalisation);
 //   gather    per atom, q K/L sum dM M M conv (FP32) plus the removal of the
 //             same-molecule pairs, -k q_i q_j erf(beta r)/r, into an FP64
 //             gradient (SoA) that the step kernel kicks with.
@@ -24,7 +25,6 @@
 
 namespace {
 
-constexpr double FIX = 1099511627776.0;  // 2^40
 constexpr int MAX_ORDER = 8;
 
 // M_n(fr + t), t = 0..n-1, and dM_n/dx at the same points, by the recursion
@@ -60,6 +60,21 @@ __device__ __forceinline__ void frac_coord(double x, double L, int K, int& fl, f
     if (fl >= K) fl -= K;
 }
 
+// round(v 2^40) as a 64-bit integer from the bits of the FP32 value, with
+// integer operations only (|v| < 2^23; halves round away from zero).
+__device__ __forceinline__ unsigned long long fix40(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const unsigned long long mant = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = min(e - 110, 38);  // v 2^40 = mant 2^(e - 150 + 40)
+    unsigned long long r;
+    if (e == 0) r = 0ull;
+    else if (sh >= 0) r = mant << sh;
+    else if (sh > -25) r = (mant + (1ull << (-sh - 1))) >> (-sh);
+    else r = 0ull;
+    return (b & 0x80000000u) ? (unsigned long long)(-(long long)r) : r;
+}
+
 __global__ void k_pme_spread(DevSys s, DevPme m, int step_off) {
     const int cur = (int)((*s.step_base + step_off) & 1);
     const int n = m.order;
@@ -81,8 +96,7 @@ __global__ void k_pme_spread(DevSys s, DevPme m, int step_off) {
                 const size_t row = ((size_t)ix * m.K[1] + iy) * m.K[2];
                 for (int c = 0; c < n; ++c) {
                     const int iz = (f[2] - c + m.K[2]) % m.K[2];
-                    const long long v = __double2ll_rn((double)(qab * w[2][c]) * FIX);
-                    atomicAdd(&m.qgrid[row + iz], (unsigned long long)v);
+                    atomicAdd(&m.qgrid[row + iz], fix40(qab * w[2][c]));
                 }
             }
         }
@@ -93,7 +107,7 @@ __global__ void k_pme_load(DevPme m) {
     const size_t N = (size_t)m.K[0] * m.K[1] * m.K[2];
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
         const long long v = (long long)m.qgrid[k];
-        m.cgrid[k] = make_float2((float)((double)v / FIX), 0.f);
+        m.cgrid[k] = make_float2(__ll2float_rn(v) * 9.094947017729282e-13f, 0.f);  // v 2^-40
         m.qgrid[k] = 0ull;
     }
 }
@@ -142,6 +156,168 @@ __global__ void k_pme_dft(DevPme m, int axis, float sign) {
     __syncthreads();
     cnt = 0;
     for (int k = threadIdx.x; k < K; k += blockDim.x, ++cnt) m.cgrid[base + k * stride] = out[cnt];
+}
+
+// Batched mixed-radix FFT of the grid lines along one axis: a CTA takes
+// FFT_B lines that are neighbours in the grid's fastest other index (so that
+// the loads and stores of the strided axes are coalesced), keeps them in
+// shared memory and runs the stages of the Stockham autosort formulation
+// (each stage reads sub-transforms of span Ns, applies the twiddles
+// exp(sign 2 pi i r (j mod Ns) / (Ns R)) and an R-point DFT, and writes its
+// outputs in natural order; Govindaraju et al., SC'08), for radices 4, 2, 3
+// and 5.  X_k = sum_j x_j exp(sign 2 pi i j k / K), no normalisation.
+constexpr int FFT_B = 16;
+constexpr int FFT_MAXST = 16;
+
+struct FftPlan {
+    int nst;                  // number of stages
+    int rad[FFT_MAXST];       // radix of each stage
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// sign * i * a
+__device__ __forceinline__ float2 cisg(float2 a, float sg) { return make_float2(-sg * a.y, sg * a.x); }
+
+// R-point DFT in place, y_k = sum_r v_r exp(sign 2 pi i r k / R).
+__device__ __forceinline__ void small_dft(float2* v, int R, float sg) {
+    if (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const float2 s13 = cadd(v[1], v[3]), d13 = cisg(csub(v[1], v[3]), sg);
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    } else if (R == 3) {
+        const float h = 0.86602540378443865f;  // sin(2 pi / 3)
+        const float2 t = cadd(v[1], v[2]), u = cisg(csub(v[1], v[2]), sg * h);
+        const float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, u);
+        v[2] = csub(m, u);
+    } else {  // R == 5
+        const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;  // cos(2 pi / 5), cos(4 pi / 5)
+        const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;   // sin(2 pi / 5), sin(4 pi / 5)
+        const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        const float2 a0 = v[0];
+        const float2 r1 = make_float2(a0.x + c1 * t1.x + c2 * t2.x, a0.y + c1 * t1.y + c2 * t2.y);
+        const float2 r2 = make_float2(a0.x + c2 * t1.x + c1 * t2.x, a0.y + c2 * t1.y + c1 * t2.y);
+        const float2 i1 = cisg(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y), sg);
+        const float2 i2 = cisg(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y), sg);
+        v[0] = cadd(a0, cadd(t1, t2));
+        v[1] = cadd(r1, i1);
+        v[4] = csub(r1, i1);
+        v[2] = cadd(r2, i2);
+        v[3] = csub(r2, i2);
+    }
+}
+
+// One Stockham stage of radix R over the FFT_B lines of the CTA.
+template <int R>
+__device__ __forceinline__ void fft_stage(const float2* src, float2* dst, const float2* tw, int K, int Ns, float sign) {
+    const int KR = K / R, tstep = K / (Ns * R);
+    for (int t = threadIdx.x; t < FFT_B * KR; t += blockDim.x) {
+        const int b = t / KR, j = t - b * KR;
+        const float2* x = src + b * K;
+        float2* y = dst + b * K;
+        float2 v[R];
+        const int jm = j % Ns;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 a = x[j + r * KR];
+            v[r] = r == 0 ? a : cmul(a, tw[r * jm * tstep]);
+        }
+        small_dft(v, R, sign);
+        const int od = (j / Ns) * Ns * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[od + r * Ns] = v[r];
+    }
+}
+
+__global__ void k_pme_fft(DevPme m, int axis, float sign, FftPlan pl) {
+    extern __shared__ float2 sh[];
+    const int K = m.K[axis];
+    float2* buf0 = sh;
+    float2* buf1 = sh + FFT_B * K;
+    float2* tw = sh + 2 * FFT_B * K;
+    // lines: index l over the two other axes; element j of line l at base(l) + j stride
+    const int nlines = (int)((size_t)m.K[0] * m.K[1] * m.K[2] / K);
+    const int l0 = blockIdx.x * FFT_B;
+    const int nb = min(FFT_B, nlines - l0);
+    size_t stride;
+    if (axis == 2) stride = 1;
+    else if (axis == 1) stride = m.K[2];
+    else stride = (size_t)m.K[1] * m.K[2];
+    auto base = [&](int l) -> size_t {
+        if (axis == 2) return (size_t)l * m.K[2];
+        if (axis == 1) return (size_t)(l / m.K[2]) * m.K[1] * m.K[2] + (l % m.K[2]);
+        return (size_t)l;
+    };
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)K, &sn, &cs);
+        tw[k] = make_float2(cs, sign * sn);
+    }
+    // load: contiguous lines element-fastest, strided lines line-fastest (coalesced either way)
+    for (int e = threadIdx.x; e < FFT_B * K; e += blockDim.x) {
+        int b, j;
+        if (stride == 1) {
+            b = e / K;
+            j = e - b * K;
+        } else {
+            j = e / FFT_B;
+            b = e - j * FFT_B;
+        }
+        buf0[b * K + j] = b < nb ? m.cgrid[base(l0 + b) + (size_t)j * stride] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* src = buf0;
+    float2* dst = buf1;
+    int Ns = 1;
+    for (int st = 0; st < pl.nst; ++st) {
+        const int R = pl.rad[st];
+        if (R == 4) fft_stage<4>(src, dst, tw, K, Ns, sign);
+        else if (R == 2) fft_stage<2>(src, dst, tw, K, Ns, sign);
+        else if (R == 3) fft_stage<3>(src, dst, tw, K, Ns, sign);
+        else fft_stage<5>(src, dst, tw, K, Ns, sign);
+        __syncthreads();
+        float2* tmp = src;
+        src = dst;
+        dst = tmp;
+        Ns *= R;
+    }
+    for (int e = threadIdx.x; e < FFT_B * K; e += blockDim.x) {
+        int b, j;
+        if (stride == 1) {
+            b = e / K;
+            j = e - b * K;
+        } else {
+            j = e / FFT_B;
+            b = e - j * FFT_B;
+        }
+        if (b < nb) m.cgrid[base(l0 + b) + (size_t)j * stride] = src[b * K + j];
+    }
+}
+
+// Radices of an FFT of size K (4s first, then 2, 3, 5); false when K has
+// another prime factor (the direct transform serves those sizes).
+bool fft_plan(int K, FftPlan& pl) {
+    pl.nst = 0;
+    int r = K;
+    const int rads[4] = {4, 2, 3, 5};
+    for (int q : rads)
+        while (r % q == 0 && pl.nst < FFT_MAXST) {
+            pl.rad[pl.nst++] = q;
+            r /= q;
+        }
+    return r == 1 && K >= 2;
 }
 
 // F(Q) <- B C F(Q); energy partial sum B C |F(Q)|^2 of this CTA into eterm.
@@ -257,11 +433,18 @@ void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off,
     const size_t N = (size_t)m.K[0] * m.K[1] * m.K[2];
     k_pme_load<<<(int)std::min<size_t>((N + 255) / 256, 4096), 256, 0, st>>>(m);
     const int lines[3] = {m.K[1] * m.K[2], m.K[0] * m.K[2], m.K[0] * m.K[1]};
-    for (int axis = 2; axis >= 0; --axis)
-        k_pme_dft<<<lines[axis], 128, 2 * m.K[axis] * sizeof(float2), st>>>(m, axis, -1.f);
+    auto transform = [&](int axis, float sign) {
+        FftPlan pl;
+        if (fft_plan(m.K[axis], pl)) {
+            const size_t smem = (2 * (size_t)FFT_B + 1) * m.K[axis] * sizeof(float2);
+            k_pme_fft<<<(lines[axis] + FFT_B - 1) / FFT_B, 128, smem, st>>>(m, axis, sign, pl);
+        } else {
+            k_pme_dft<<<lines[axis], 128, 2 * m.K[axis] * sizeof(float2), st>>>(m, axis, sign);
+        }
+    };
+    for (int axis = 2; axis >= 0; --axis) transform(axis, -1.f);
     k_pme_convolve<<<PME_CONV_CTAS, 256, 0, st>>>(m);
-    for (int axis = 2; axis >= 0; --axis)
-        k_pme_dft<<<lines[axis], 128, 2 * m.K[axis] * sizeof(float2), st>>>(m, axis, 1.f);
+    for (int axis = 2; axis >= 0; --axis) transform(axis, 1.f);
     k_pme_gather<<<(s.n + tb - 1) / tb, tb, 0, st>>>(s, p, m, step_off);
 }
 

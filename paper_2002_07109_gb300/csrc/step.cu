@@ -46,6 +46,9 @@ __device__ __forceinline__ int warp_scan_incl(int x) {
     return x;
 }
 constexpr int FU = 2;  // proposals per thread in flight in the jump phase
+// The staged proposals carry the partner's type group in the low bits of x2
+// (x2 & 3), below the 26 bits that u53 reads: room for 4 types.
+static_assert(BOUNCE_MAXT <= 4, "the partner type group is packed into 2 bits of x2");
 
 struct JumpSmem {
     double s[BOUNCE_GROUP];       // ||v|| (FP64)
@@ -61,6 +64,18 @@ struct JumpSmem {
     float inv[129];               // 1/k, k = 0..128 (round-to-nearest reciprocals)
     unsigned long long cnt[3];    // proposals, accepts, near ties
 };
+
+// Split FP32 copy (hi, lo) of the position x - of: the slot copies of the
+// cluster lists keep the image of the last build (continuous motion across
+// faces), whatever the wrap of phi.
+__device__ __forceinline__ void split_pos(double x, double y, double z, double ox, double oy, double oz, float w_hi,
+                                          float w_lo, float4& ph, float4& pl) {
+    const double a = x - ox, b = y - oy, c = z - oz;
+    const float hx = __double2float_rn(a), hy = __double2float_rn(b), hz = __double2float_rn(c);
+    ph = make_float4(hx, hy, hz, w_hi);
+    pl = make_float4(__double2float_rn(a - (double)hx), __double2float_rn(b - (double)hy),
+                     __double2float_rn(c - (double)hz), w_lo);
+}
 
 // Lane-parallel (warp 0): quantities of the jump step of atom `a` that need FP64.
 __device__ __forceinline__ void jump_prep(const DevSys& s, const Params& p, JumpSmem& js, int a, int i, double vx,
@@ -506,6 +521,8 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
     __shared__ unsigned long long sPairs;
     // per-atom inputs of warp 0's FP64 phases, fetched ahead by warps 1-4
     __shared__ double sQ[BOUNCE_GROUP][3], sRef[BOUNCE_GROUP][3], sKick[BOUNCE_GROUP], sOsd[BOUNCE_GROUP];
+    __shared__ double sCref[BOUNCE_GROUP][3];
+    __shared__ int sSlot[BOUNCE_GROUP];
     __shared__ float sNz[BOUNCE_GROUP][3], sU[2][BOUNCE_GROUP], sHw[BOUNCE_GROUP], sLw[BOUNCE_GROUP];
     chain_enter();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -551,6 +568,11 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
                 sRef[lane][0] = s.refx[i];
                 sRef[lane][1] = s.refy[i];
                 sRef[lane][2] = s.refz[i];
+                if (s.cl.on) {
+                    sCref[lane][0] = s.cl.crefx[i];
+                    sCref[lane][1] = s.cl.crefy[i];
+                    sCref[lane][2] = s.cl.crefz[i];
+                }
             }
         } else if (warp == 4) {
             const float4 h = s.phi[cur][i], l = s.plo[cur][i];
@@ -566,8 +588,25 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
     // F_0 (BOUNCE) or the full gradient (BAOAB) at q_n: pair sums, either
     // read from k_pairs (pre) or here, warps over atoms
     if (pre && threadIdx.x < na) {
-        const float4 g = s.g0[base + threadIdx.x];
-        const int a = threadIdx.x;
+        const int a = threadIdx.x, i = base + a;
+        float4 g;
+        if (s.cl.on || s.tl.on) {
+            // cluster or tile pair sums: the atom's fixed-point accumulators
+            // (by slot, or by atom), cleared for the next evaluation
+            const int sl = s.cl.on ? s.cl.a2s[i] : i;
+            sSlot[a] = sl;
+            const size_t ns = s.cl.on ? (size_t)s.cl.ncol * s.cl.maxcl * BOUNCE_CL : (size_t)s.n;
+            unsigned long long* acc = s.cl.on ? s.cl.acc : s.tl.acc;
+            g = make_float4((float)((double)(long long)acc[sl] * CL_UNFIX),
+                            (float)((double)(long long)acc[ns + sl] * CL_UNFIX),
+                            (float)((double)(long long)acc[2 * ns + sl] * CL_UNFIX), 0.f);
+            acc[sl] = 0ull;
+            acc[ns + sl] = 0ull;
+            acc[2 * ns + sl] = 0ull;
+        } else {
+            g = s.g0[i];
+            atomicAdd(&sPairs, (unsigned long long)__float_as_int(g.w));
+        }
         const bool to_out = ext != 0;
         sG[a][0] = to_out ? 0.f : g.x;
         sG[a][1] = to_out ? 0.f : g.y;
@@ -575,7 +614,8 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
         sGp[a][0] = to_out ? g.x : 0.f;
         sGp[a][1] = to_out ? g.y : 0.f;
         sGp[a][2] = to_out ? g.z : 0.f;
-        atomicAdd(&sPairs, (unsigned long long)__float_as_int(g.w));
+    } else if (s.cl.on && do_aoa && threadIdx.x < na) {
+        sSlot[threadIdx.x] = s.cl.a2s[base + threadIdx.x];
     }
     for (int a = pre ? na : warp; a < na; a += NW) {
         int np = 0, np2 = 0;
@@ -702,11 +742,24 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
                 wz -= p.Ld[2] * floor(z / p.Ld[2]);
             }
             const float hx = __double2float_rn(wx), hy = __double2float_rn(wy), hz = __double2float_rn(wz);
-            s.phi[nxt][i] = make_float4(hx, hy, hz, sHw[lane]);
-            s.plo[nxt][i] = make_float4(__double2float_rn(wx - (double)hx), __double2float_rn(wy - (double)hy),
-                                        __double2float_rn(wz - (double)hz), sLw[lane]);
+            const float4 ph = make_float4(hx, hy, hz, sHw[lane]);
+            const float4 pl = make_float4(__double2float_rn(wx - (double)hx), __double2float_rn(wy - (double)hy),
+                                          __double2float_rn(wz - (double)hz), sLw[lane]);
+            s.phi[nxt][i] = ph;
+            s.plo[nxt][i] = pl;
             const double ex = x - sRef[lane][0], ey = y - sRef[lane][1], ez = z - sRef[lane][2];
-            if (ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+            if (s.rows_flag && ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+            if (s.cl.on) {
+                // slot-ordered copy for the cluster pair kernel (in the image of the
+                // build); displacement since the cluster build
+                const int sl = sSlot[lane];
+                float4 ch = ph, cw = pl;
+                if (p.periodic) split_pos(x, y, z, s.cl.cofx[i], s.cl.cofy[i], s.cl.cofz[i], ph.w, pl.w, ch, cw);
+                s.cl.sphi[nxt][sl] = ch;
+                s.cl.splo[nxt][sl] = cw;
+                const double cx = x - sCref[lane][0], cy = y - sCref[lane][1], cz = z - sCref[lane][2];
+                if (cx * cx + cy * cy + cz * cz > s.cl.cskin_half2) atomicOr(s.cl.rebuild, 1);
+            }
         }
         s.vx[i] = vx;
         s.vy[i] = vy;
@@ -719,6 +772,282 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
             atomicAdd(&s.cnt[CNT_PROPOSALS], js.cnt[0]);
             atomicAdd(&s.cnt[CNT_ACCEPTS], js.cnt[1]);
             atomicAdd(&s.cnt[CNT_NEAR], js.cnt[2]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- lite step
+// The same step as k_step with one thread per atom and no CTA barriers, for
+// runs whose jump proposals are rare (BAOAB, or BOUNCE splits with well
+// under one proposal per atom-step): each thread takes its atom's pair sums
+// from the pair kernel, adds its bonded terms in list order, and runs the
+// two jump half-steps of its atom sequentially -- the Poisson chunks, then
+// proposal k = 1..M in order, each decided with the velocity left by the
+// proposals before it -- with the arithmetic of jump_prep, poisson_phase
+// and jump_phase, so both kernels give the same results bit for bit.
+
+// One jump half-step J(delta/2) of atom i (thread-sequential): returns the
+// FP32 velocity increment and counts proposals, accepts and near ties.
+__device__ __forceinline__ void jump_thread(const DevSys& s, const Params& p, int cur, int i, int ti, double vx,
+                                            double vy, double vz, long long step, uint32_t stream, float4 ahi,
+                                            float4 alo, float& dvx, float& dvy, float& dvz, int& nprop, int& nacc,
+                                            int& near) {
+    dvx = dvy = dvz = 0.f;
+    const double sp = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
+    const double Ls = p.Lstar_d[ti];
+    double n;
+    uint32_t acum[BOUNCE_MAXT + 1];
+    int ast[BOUNCE_MAXT];
+    float slt[BOUNCE_MAXT];
+    if (p.typed) {
+        uint32_t W = 0u;
+        int st = 0;
+#pragma unroll
+        for (int b = 0; b < BOUNCE_MAXT; ++b) {
+            const int nb = s.nseg[(size_t)i * BOUNCE_MAXT + b];
+            acum[b] = W;
+            ast[b] = st;
+            W += (uint32_t)nb * p.lq[ti * BOUNCE_MAXT + b];
+            st += nb;
+            slt[b] = __double2float_rn(__dmul_rn(sp, p.lt_d[ti * BOUNCE_MAXT + b]));
+        }
+        acum[BOUNCE_MAXT] = W;
+        n = __dmul_rn((double)W, 1.52587890625e-05);
+    } else {
+        n = (double)s.nlong[i];
+    }
+    double mu = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(p.beta, sp), Ls), n), p.dt), 0.5);
+    if (!(mu <= 1e6)) {
+        atomicOr(s.err, BERR_RATE);
+        mu = 0.0;
+    }
+    if (!(mu > 0.0)) return;
+    const int nch = (int)ceil(__dmul_rn(mu, 0.0625));
+    const float muc = __double2float_rn(nch == 1 ? mu : __ddiv_rn(mu, (double)nch));
+    int M = 0;
+    for (int c = 0; c < nch; ++c) {
+        const float u = u24(rng_atom(s, p, BOUNCE_POISSON_SLOT | (uint32_t)c, i, step, stream).x);
+        float pk = expneg_f32(muc), cdf = pk;
+        int k = 0;
+        while (u > cdf && k < 128) {
+            ++k;
+            const float q = __fmul_rn(__fmul_rn(pk, muc), __frcp_rn((float)k));
+            const float cn = __fadd_rn(cdf, q);
+            if (cn == cdf) break;
+            pk = q;
+            cdf = cn;
+        }
+        M += k;
+    }
+    nprop += M;
+    if (M == 0) return;
+    const float sl = __double2float_rn(__dmul_rn(sp, Ls));
+    if (!p.typed) slt[0] = sl;
+    const float sp_f = __double2float_rn(sp);
+    float fvx = __double2float_rn(vx), fvy = __double2float_rn(vy), fvz = __double2float_rn(vz);
+    const int* row = s.rows + (size_t)i * s.cap;
+    const int an = s.nlong[i];
+    for (int k = 1; k <= M; ++k) {
+        const uint4 x = rng_atom(s, p, (uint32_t)k, i, step, stream);
+        uint32_t bsel = 0u;
+        int jj;
+        if (p.typed) {
+            const uint32_t tg = __umulhi(x.x, acum[BOUNCE_MAXT]);
+#pragma unroll
+            for (int b = 1; b < BOUNCE_MAXT; ++b)
+                if (acum[b] <= tg) bsel = (uint32_t)b;
+            uint32_t cb = 0u;
+            int sb = 0;
+#pragma unroll
+            for (int b = 0; b < BOUNCE_MAXT; ++b)
+                if ((uint32_t)b == bsel) {
+                    cb = acum[b];
+                    sb = ast[b];
+                }
+            const uint32_t xx = tg - cb, ab = ti * BOUNCE_MAXT + bsel;
+            const uint32_t th = __umulhi(p.lq_m[ab], xx);
+            jj = sb + (int)((th + ((xx - th) >> 1)) >> p.lq_s[ab]);
+        } else {
+            jj = (int)__umulhi(x.x, (uint32_t)an);
+        }
+        const uint32_t x1 = x.y, x2 = (x.z & ~63u) | bsel;
+        const int j = row[jj];
+        const float4 hj = s.phi[cur][j], lj = s.plo[cur][j];
+        const float3 d = pair_disp(p, ahi, alo, hj, lj);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        if (inside_cut(s, p, cur, i, j, r2)) {
+            float sw, fixed, r;
+            pair_dW_split(p, r2, p.kcoul * ahi.w * hj.w, type_of(alo) * BOUNCE_MAXT + type_of(lj), sw, fixed, r);
+            const float w = chi_of(p, r) * sw;
+            gx = w * d.x;
+            gy = w * d.y;
+            gz = w * d.z;
+        }
+        float slb = slt[0];
+#pragma unroll
+        for (int b = 1; b < BOUNCE_MAXT; ++b)
+            if ((uint32_t)b == (x2 & 3u)) slb = slt[b];
+        const float thr = u24(x1) * slb;
+        const float g2 = gx * gx + gy * gy + gz * gz;
+        const float err = 4e-6f * (thr + 1.0001f * sp_f * sqrtf(g2)) + 2.4e-7f * slb;
+        const float af = fvx * gx + fvy * gy + fvz * gz;
+        int dec = (thr + err < af) ? 1 : ((thr - err > af) ? 0 : 2);
+        if (dec == 2) {
+            const double Lb = p.typed ? p.lt_d[ti * BOUNCE_MAXT + (x2 & 3u)] : p.Lstar_d[ti];
+            dec = exact_decision(fvx, fvy, fvz, gx, gy, gz, x1, x2, sp, Lb);
+        }
+        if (fabsf(thr - af) < 1e-6f * slb) ++near;
+        if (dec == 1) {
+            const float coef = __fdividef(af + af, g2);
+            fvx -= coef * gx;
+            fvy -= coef * gy;
+            fvz -= coef * gz;
+            dvx -= coef * gx;
+            dvy -= coef * gy;
+            dvz -= coef * gz;
+            ++nacc;
+        }
+    }
+}
+
+template <int BOUNCE>
+__global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int variant, int step_off, double hr, int ext,
+                                                   double hout) {
+    __shared__ unsigned long long cnt[4];
+    chain_enter();
+    if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nprop = 0, nacc = 0, near = 0;
+    if (i < s.n) {
+        const long long step = *s.step_base + step_off;
+        const int cur = (int)(step & 1), nxt = cur ^ 1;
+        const bool do_j2 = BOUNCE && variant != 0;
+        const bool do_j1 = BOUNCE && variant != 2;
+        const bool do_aoa = variant != 2;
+        const double hk = variant == 1 ? p.dt : 0.5 * p.dt;
+        // pair sums of the pair kernel (absent between the outer kicks of the extended splits)
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        int sl = i;
+        if (s.cl.on) sl = s.cl.a2s[i];
+        if (!(ext && hout == 0.0)) {
+            const size_t ns = s.cl.on ? (size_t)s.cl.ncol * s.cl.maxcl * BOUNCE_CL : (size_t)s.n;
+            unsigned long long* acc = s.cl.on ? s.cl.acc : s.tl.acc;
+            gx = (float)((double)(long long)acc[sl] * CL_UNFIX);
+            gy = (float)((double)(long long)acc[ns + sl] * CL_UNFIX);
+            gz = (float)((double)(long long)acc[2 * ns + sl] * CL_UNFIX);
+            acc[sl] = 0ull;
+            acc[ns + sl] = 0ull;
+            acc[2 * ns + sl] = 0ull;
+        }
+        float Gx = ext ? 0.f : gx, Gy = ext ? 0.f : gy, Gz = ext ? 0.f : gz;
+        // bonded terms of the atom, in list order
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        for (int t = s.bt_off[i]; t < s.bt_off[i + 1]; ++t) {
+            const float3 g = bonded_grad(p, s, cur, i, s.bt_idx[t], s.bt_par[t]);
+            bx += g.x;
+            by += g.y;
+            bz += g.z;
+        }
+        Gx += bx;
+        Gy += by;
+        Gz += bz;
+        const float4 ahi = s.phi[cur][i], alo = s.plo[cur][i];
+        const int ti = s.type[i];
+        const double kick = s.kick[i];
+        double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
+        float dx, dy, dz;
+        if (do_j2) {
+            jump_thread(s, p, cur, i, ti, vx, vy, vz, step - 1, BOUNCE_STREAM_J2, ahi, alo, dx, dy, dz, nprop, nacc,
+                        near);
+            vx += (double)dx;
+            vy += (double)dy;
+            vz += (double)dz;
+        }
+        const double c = hk * kick;
+        vx -= c * (double)Gx;
+        vy -= c * (double)Gy;
+        vz -= c * (double)Gz;
+        if (hr != 0.0) {
+            const double cr = hr * kick;
+            vx -= cr * s.grecip[i];
+            vy -= cr * s.grecip[s.n + i];
+            vz -= cr * s.grecip[2 * (size_t)s.n + i];
+        }
+        if (ext && hout != 0.0) {
+            const double co = hout * kick;
+            vx -= co * (double)gx;
+            vy -= co * (double)gy;
+            vz -= co * (double)gz;
+        }
+        if (do_j1) {
+            jump_thread(s, p, cur, i, ti, vx, vy, vz, step, BOUNCE_STREAM_J1, ahi, alo, dx, dy, dz, nprop, nacc, near);
+            vx += (double)dx;
+            vy += (double)dy;
+            vz += (double)dz;
+        }
+        if (do_aoa) {
+            const double h = 0.5 * p.dt;
+            double x = s.qx[cur][i] + h * vx, y = s.qy[cur][i] + h * vy, z = s.qz[cur][i] + h * vz;
+            // O: Box-Muller on Philox slot 0, stream 0
+            const uint4 r = rng_atom(s, p, 0u, i, step, BOUNCE_STREAM_O);
+            const float ra = sqrtf(-2.f * logf(u24_open0(r.x)));
+            float sn, cs;
+            sincospif(2.f * u24(r.y), &sn, &cs);
+            const float n0 = ra * cs, n1 = ra * sn;
+            const float n2 = sqrtf(-2.f * logf(u24_open0(r.z))) * cospif(2.f * u24(r.w));
+            const double sd = s.osd[i];
+            vx = p.c1 * vx + sd * (double)n0;
+            vy = p.c1 * vy + sd * (double)n1;
+            vz = p.c1 * vz + sd * (double)n2;
+            x += h * vx;
+            y += h * vy;
+            z += h * vz;
+            s.qx[nxt][i] = x;
+            s.qy[nxt][i] = y;
+            s.qz[nxt][i] = z;
+            double wx = x, wy = y, wz = z;
+            if (p.periodic) {
+                wx -= p.Ld[0] * floor(x / p.Ld[0]);
+                wy -= p.Ld[1] * floor(y / p.Ld[1]);
+                wz -= p.Ld[2] * floor(z / p.Ld[2]);
+            }
+            const float hx = __double2float_rn(wx), hy = __double2float_rn(wy), hz = __double2float_rn(wz);
+            const float4 ph = make_float4(hx, hy, hz, ahi.w);
+            const float4 pl = make_float4(__double2float_rn(wx - (double)hx), __double2float_rn(wy - (double)hy),
+                                          __double2float_rn(wz - (double)hz), alo.w);
+            s.phi[nxt][i] = ph;
+            s.plo[nxt][i] = pl;
+            const double ex = x - s.refx[i], ey = y - s.refy[i], ez = z - s.refz[i];
+            if (s.rows_flag && ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+            if (s.cl.on) {
+                float4 ch = ph, cw = pl;
+                if (p.periodic) split_pos(x, y, z, s.cl.cofx[i], s.cl.cofy[i], s.cl.cofz[i], ph.w, pl.w, ch, cw);
+                s.cl.sphi[nxt][sl] = ch;
+                s.cl.splo[nxt][sl] = cw;
+                const double cx = x - s.cl.crefx[i], cy = y - s.cl.crefy[i], cz = z - s.cl.crefz[i];
+                if (cx * cx + cy * cy + cz * cz > s.cl.cskin_half2) atomicOr(s.cl.rebuild, 1);
+            }
+        }
+        s.vx[i] = vx;
+        s.vy[i] = vy;
+        s.vz[i] = vz;
+    }
+    if (BOUNCE) {
+        nprop = warp_sum_i(nprop);
+        nacc = warp_sum_i(nacc);
+        near = warp_sum_i(near);
+        if ((threadIdx.x & 31) == 0) {
+            if (nprop) atomicAdd(&cnt[0], (unsigned long long)nprop);
+            if (nacc) atomicAdd(&cnt[1], (unsigned long long)nacc);
+            if (near) atomicAdd(&cnt[2], (unsigned long long)near);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (cnt[0]) atomicAdd(&s.cnt[CNT_PROPOSALS], cnt[0]);
+            if (cnt[1]) atomicAdd(&s.cnt[CNT_ACCEPTS], cnt[1]);
+            if (cnt[2]) atomicAdd(&s.cnt[CNT_NEAR], cnt[2]);
         }
     }
 }
@@ -792,19 +1121,54 @@ __global__ void k_advance(DevSys s, long long by) {
 
 }  // namespace
 
-void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
-                 double hout, cudaStream_t st) {
-    const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
+// The pair sums a step boundary needs before its step kernel (their own
+// kernel); returns whether the step kernel reads them (pre).
+int launch_step_pairs(const DevSys& s, const Params& p, int integrator, int step_off, double hout, cudaStream_t st) {
     const int ext = integrator >= 3 ? 1 : 0;  // extended RESPA and RESPA1: bonded-only F_0
-    // pair sums over the long candidate rows in their own kernel; short rows
-    // (Coulomb on the jumps) stay in the step kernel, and so does a boundary
-    // without pair sums (the extended splits between outer kicks)
-    const bool short_f0 = integrator != 0 && p.rshort2 < INFINITY;
-    const int pre = ((ext && hout == 0.0) || short_f0) ? 0 : 1;
-    if (pre) launch_chained(k_pairs, (s.n + 7) / 8, 256, 0, st, s, p, step_off, integrator != 0 ? 3 : 5);
+    int pre;
+    if (s.cl.on) {
+        // cluster pair sums (Newton's third law, fixed-point accumulators),
+        // except at a boundary without pair sums (the extended splits between
+        // outer kicks); F_0 takes the short-range list when there is one
+        pre = (ext && hout == 0.0) ? 0 : 1;
+        if (pre)
+            launch_cluster_pairs(s, p, step_off, integrator != 0 ? 3 : 5, integrator != 0 && s.cl.nlists > 1 ? 1 : 0,
+                                 st);
+    } else {
+        // all pairs (no cutoff): tiles, or the long candidate rows in their
+        // own kernel; short rows (Coulomb on the jumps) stay in the step
+        // kernel, and so does a boundary without pair sums (the extended
+        // splits between outer kicks)
+        const bool short_f0 = integrator != 0 && p.rshort2 < INFINITY;
+        pre = ((ext && hout == 0.0) || short_f0) ? 0 : 1;
+        if (pre && s.tl.on) launch_tile_pairs(s, p, step_off, integrator != 0 ? 3 : 5, st);
+        else if (pre) launch_chained(k_pairs, (s.n + 7) / 8, 256, 0, st, s, p, step_off, integrator != 0 ? 3 : 5);
+    }
+    return pre;
+}
+
+void launch_step_kernel(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
+                        double hout, int pre, cudaStream_t st) {
+    const int blocks = (s.n + BOUNCE_GROUP - 1) / BOUNCE_GROUP;
+    const int ext = integrator >= 3 ? 1 : 0;
+    // the thread-per-atom kernel where its preconditions hold: pair sums
+    // from the cluster or tile kernel (or none at this boundary), and rare
+    // proposals (s.lite, decided on the host from the jump bounds)
+    if (s.lite && (s.cl.on || s.tl.on) && (pre || (ext && hout == 0.0))) {
+        const int lb = (s.n + 255) / 256;
+        if (integrator != 0) launch_chained(k_step_lite<1>, lb, 256, 0, st, s, p, variant, step_off, hr, ext, hout);
+        else launch_chained(k_step_lite<0>, lb, 256, 0, st, s, p, variant, step_off, hr, 0, 0.0);
+        return;
+    }
     if (integrator != 0)
         launch_chained(k_step<1>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, ext, hout, pre);
     else launch_chained(k_step<0>, blocks, NW * 32, 0, st, s, p, variant, step_off, hr, 0, 0.0, pre);
+}
+
+void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
+                 double hout, cudaStream_t st) {
+    const int pre = launch_step_pairs(s, p, integrator, step_off, hout, st);
+    launch_step_kernel(s, p, integrator, variant, step_off, hr, hout, pre, st);
 }
 
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,
