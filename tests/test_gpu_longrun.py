@@ -4,15 +4,19 @@ Independent realisations of the same process on both sides (the GPU library
 and the FP64 oracle, same equilibrated start, different Philox seeds): four
 runs of 20,000 BOUNCE steps each of the 64-molecule droplet (all pairs, LJ
 on jumps beyond a 4-5 A switch, Coulomb wholly in F_0, per-type-pair bounds,
-1 fs, friction 10/ps so that blocks of 2 ps are nearly independent), the
-oracle's four runs in a spawn process pool beside the GPU runs.  Observables
-per block of 2 ps: the mean potential energy per molecule, the kinetic
+1 fs, the workloads' friction of 1/ps), the oracle's four runs in a spawn
+process pool beside the GPU runs.  Observables per block of 4 ps (four
+times the thermostat's relaxation time 1/gamma, so that the block means are
+nearly independent): the mean potential energy per molecule, the kinetic
 temperature, the O-O coordination number within 3.5 A (the first shell of
 the O-O pair-distance histogram, the droplet's RDF observable) and the O
 self-diffusion coefficient from the growth of the mean squared displacement
-over the block's second ps.  Each must agree within two combined standard
-errors of the 40 block means per side; the whole O-O histogram (0-8 A, 0.25
-A bins) is compared by its chi^2 per bin, with standard errors from the
+over the block's second half.  Each must agree within three combined
+standard errors (of the 20 block means per side; of the four run means for
+the coordination number, a histogram observable; for four independent
+scalars, two standard errors would fail a correct program about one time in
+six; three, about one time in a hundred); the whole O-O histogram (0-8 A,
+0.25 A bins) is compared by its chi^2 per bin, with standard errors from the
 spread of the runs.  The printed z values are the
 per-observable agreement in standard errors.  This split keeps reflections
 rare, so the trajectories stay at the equilibrium temperature; with Coulomb
@@ -32,9 +36,9 @@ from paper_2002_07109_gb300.water import water_droplet
 
 bounce = pytest.importorskip("paper_2002_07109_gb300.bounce")
 
-RUNS, BLOCKS, BLOCK, EVERY = 4, 10, 2000, 20
+RUNS, BLOCKS, BLOCK, EVERY = 4, 5, 4000, 20
 R_SHELL, H_RMAX, H_BINS = 3.5, 8.0, 32
-GAMMA = 0.01
+GAMMA = 0.001
 
 
 def _stats(x):
@@ -93,8 +97,10 @@ def test_long_run_observables_match_oracle():
     z = {}
     for key in ("pe", "T", "D", "coord"):
         if key == "coord":
-            a = pooled(gpu, "hist")[:, :n_shell].sum(1) * 2.0 / n_o
-            b = pooled(ora, "hist")[:, :n_shell].sum(1) * 2.0 / n_o
+            # a histogram observable: standard errors from the spread of the
+            # runs' means, as for the histogram below
+            a = [r["hist"][:, :n_shell].sum(1).mean() * 2.0 / n_o for r in gpu]
+            b = [r["hist"][:, :n_shell].sum(1).mean() * 2.0 / n_o for r in ora]
         else:
             a, b = pooled(gpu, key), pooled(ora, key)
         m1, e1 = _stats(a)
@@ -102,16 +108,17 @@ def test_long_run_observables_match_oracle():
         z[key] = abs(m1 - m2) / math.hypot(e1, e2)
         print(key, "gpu %.4f +- %.4f  oracle %.4f +- %.4f  z %.2f" % (m1, e1, m2, e2, z[key]))
     # the histogram's slow parts (the droplet's shape) correlate the blocks of
-    # one run: its bins take their standard errors from the spread of the
-    # independent runs' means (t with 2 (RUNS - 1) degrees of freedom, whose
-    # z^2 has mean 1.5 for four runs per side)
+    # one run: its bins (and the coordination number above) take their
+    # standard errors from the spread of the independent runs' means (t with
+    # 2 (RUNS - 1) degrees of freedom, whose z^2 has mean 1.5 for four runs
+    # per side)
     h1, s1 = _stats([r["hist"].mean(0) for r in gpu])
     h2, s2 = _stats([r["hist"].mean(0) for r in ora])
     ok = (s1 + s2) > 0
     zb = np.abs(h1 - h2)[ok] / np.hypot(s1, s2)[ok]
     chi2 = float((zb ** 2).mean())
     print("O-O histogram: chi^2 per bin %.2f, largest bin z %.2f, over %d bins" % (chi2, zb.max(), int(ok.sum())))
-    assert all(v < 2.0 for v in z.values()), z
+    assert all(v < 3.0 for v in z.values()), z
     assert chi2 < 3.0, chi2
     # the runs stay at equilibrium (no jump heating at this split)
     assert abs(np.mean(pooled(gpu, "T")) - 300.0) < 15.0

@@ -7,10 +7,13 @@ decisions: identical except at atoms where the oracle's |U - lambda/lambda*|
 of atom i is measured against the sum of the magnitudes of the terms it
 adds, c_i = sum_j ||g_ij|| (bonded terms included), which bounds the
 rounding error of any floating-point summation; ||dg_i|| <= 1e-5 c_i for
-every atom, and the median plain relative error ||dg_i|| / ||g_i|| <= 1e-5
-(sums with heavy cancellation have a small ||g_i||, so the plain relative
-error of those atoms is not bounded by the precision).  Velocities after one
-jump half-step (single pair terms, no cancellation): ||dv_i|| / ||v_i|| <= 1e-5.
+every atom, and the plain relative error ||dg_i|| / ||g_i|| <= 2e-5 at the
+99th percentile of the atoms (sums with heavy cancellation have a small
+||g_i||, so the plain relative error of those few atoms is not bounded by
+the precision).  Velocities after one jump half-step (single pair terms, no
+cancellation): ||dv_i|| / ||v_i|| <= 1e-5.  Trajectories over several steps:
+the per-step bound, grown by the divergence of nearby trajectories (stated
+per test).
 """
 import math
 
@@ -93,8 +96,8 @@ def _check_sum(g, ref, scale):
     cond = d / np.maximum(scale, 1e-30)
     plain = d / np.maximum(np.linalg.norm(ref, axis=1), 1e-30)
     assert cond.max() < TOL, ("conditioned", cond.max(), int(cond.argmax()))
-    assert np.median(plain) < TOL, ("plain median", np.median(plain))
-    return cond.max(), np.median(plain), plain.max()
+    assert np.percentile(plain, 99) < 2 * TOL, ("plain p99", np.percentile(plain, 99))
+    return cond.max(), np.percentile(plain, 99), plain.max()
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -212,7 +215,10 @@ def test_no_long_range_bounce_is_baoab():
 
 def test_multi_step_trajectory_tracks_oracle():
     """20 BOUNCE steps: GPU and oracle stay together until a near tie flips a
-    decision (then they may separate); the counted proposals agree."""
+    decision (then they may separate); the counted proposals agree.  The
+    bound, 1e-4 after up to 20 steps, is the one-step bound of 1e-5 grown by
+    the divergence of nearby trajectories of liquid water (a factor of a few
+    per ps, here over a few tens of fs, plus the sum of 20 steps' errors)."""
     s, ctx, md = _setup("droplet_all_pairs", seed=21)
     for k in range(20):
         ctx.run(1, bounce.BOUNCE)
@@ -347,6 +353,20 @@ def test_recip_gradient_and_energy():
     ctx.close()
 
 
+def _tie_mask(md, n):
+    """Atoms to leave out after a run with near ties: each tie atom (one
+    decision may flip), its molecule (bonded partners feel its changed
+    position through stiff bonds) and its candidate row (pair partners)."""
+    keep = np.ones(n, bool)
+    mol = md.topo.mol
+    for i in md.tie_atoms:
+        keep[i] = False
+        keep[mol == mol[i]] = False
+        if md.row_list is not None:
+            keep[md.row_list[i]] = False
+    return ~keep
+
+
 def _kick_scale(md, part, with_recip):
     """||v_i|| error scale of one step: the summed magnitudes of the gradient
     terms an atom is kicked with, times dt 4.184e-4 / m."""
@@ -388,7 +408,7 @@ def test_one_step_with_recip(integrator):
     assert dq[~tie].max() < TOL, dq[~tie].max()
     dv = np.linalg.norm(v - md.v, axis=1)
     assert (dv / (np.linalg.norm(md.v, axis=1) + kscale))[~tie].max() < TOL
-    assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
+    assert np.percentile((dv / np.linalg.norm(md.v, axis=1))[~tie], 99) < 2 * TOL
     e = ctx.energies()
     assert e["recip"] != 0.0
     ctx.close()
@@ -415,10 +435,12 @@ def test_extended_respa_droplet_block():
         md.block_bounce_respa(2, extended=True)
     q, v = ctx.get_state()
     dv = np.linalg.norm(v - md.v, axis=1)
-    ok = dv / (np.linalg.norm(md.v, axis=1) + 4 * kscale) < TOL
-    # a near tie in any of the 8 jump half-steps may flip one atom's chain
-    assert ok.mean() > 0.99, ok.mean()
-    assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
+    # a near tie in any of the 8 jump half-steps may flip one decision: those
+    # atoms and their partners are left out, every other atom must agree
+    tie = _tie_mask(md, s.n_atoms)
+    assert tie.mean() < 0.25, tie.mean()
+    err = dv / (np.linalg.norm(md.v, axis=1) + 4 * kscale)
+    assert err[~tie].max() < TOL, (err[~tie].max(), len(md.tie_atoms))
     ctx.close()
 
 
@@ -438,10 +460,12 @@ def test_respa1_outer_step(case):
     md.run(6, "bounce_respa1", respa_m=2, respa_m2=3)
     q, v = ctx.get_state()
     dv = np.linalg.norm(v - md.v, axis=1)
-    ok = dv / (np.linalg.norm(md.v, axis=1) + 6 * kscale) < TOL
-    # a near tie in any of the 12 jump half-steps may flip one atom's chain
-    assert ok.mean() > 0.99, ok.mean()
-    assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
+    # a near tie in any of the 12 jump half-steps may flip one decision: those
+    # atoms and their partners are left out, every other atom must agree
+    tie = _tie_mask(md, s.n_atoms)
+    assert tie.mean() < 0.25, tie.mean()
+    err = dv / (np.linalg.norm(md.v, axis=1) + 6 * kscale)
+    assert err[~tie].max() < TOL, (err[~tie].max(), len(md.tie_atoms))
     ctx.close()
 
 
@@ -492,4 +516,40 @@ def test_full_size_box_pme_sampled():
     _, g_exc = ewald.exclusion(s.q, s.charge, ewald.molecule_pairs(s.molecule), 0.35, s.box)
     sc = np.linalg.norm(g_rec, axis=1) + np.linalg.norm(g_exc, axis=1)
     _check_sum(gr[sample], (g_rec + g_exc)[sample], sc[sample])
+    ctx.close()
+
+
+def _shuffled(s, seed):
+    """The same system with its molecules renumbered in random order, so that
+    atom indices carry no spatial order."""
+    import dataclasses
+    nm = len(s.molecule) // 3
+    perm = np.random.default_rng(seed).permutation(nm)          # new molecule k is old molecule perm[k]
+    old_of_new = (3 * perm[:, None] + np.arange(3)).ravel()
+    new_of_old = np.empty_like(old_of_new)
+    new_of_old[old_of_new] = np.arange(len(old_of_new))
+    return dataclasses.replace(
+        s, q=s.q[old_of_new], v=s.v[old_of_new], type=s.type[old_of_new], mass=s.mass[old_of_new],
+        charge=s.charge[old_of_new], molecule=np.repeat(np.arange(nm, dtype=np.int32), 3),
+        bonds=new_of_old[s.bonds].astype(np.int32), angles=new_of_old[s.angles].astype(np.int32))
+
+
+@pytest.mark.parametrize("typed", [False, True])
+def test_rows_windowed_random_order(typed):
+    """Rows of a 41,472-atom box whose molecules are numbered in random order:
+    the row builder's index window does not span every atom, so members
+    outside it take further passes; sampled rows against the oracle's brute
+    force, bit for bit (typed: grouped by partner type)."""
+    s = _shuffled(water_box(24, seed=8), seed=2)
+    ctx = bounce.from_system(s, seed=1, r_on=4.0, r_off=5.0, r_cut=8.0, skin=1.0, ewald_beta=0.35,
+                             max_neighbors=1024, pair_bounds=typed)
+    ctx.set_state(s.q, s.v, step=0)
+    sample = np.sort(np.random.default_rng(3).choice(s.n_atoms, 200, replace=False))
+    ref = oracle_rows(s.q, s.molecule, 9.0, s.box, atoms=sample)
+    if typed:
+        from oracle.integrate import typed_rows
+        ref, _ = typed_rows(ref, s.type, 2)
+    got = ctx.rows()
+    for a, i in enumerate(sample):
+        assert np.array_equal(got[i], ref[a]), i
     ctx.close()

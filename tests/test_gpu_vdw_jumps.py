@@ -50,7 +50,7 @@ def _check_sum(g, ref, scale):
     cond = d / np.maximum(scale, 1e-30)
     plain = d / np.maximum(np.linalg.norm(ref, axis=1), 1e-30)
     assert cond.max() < TOL, ("conditioned", cond.max(), int(cond.argmax()))
-    assert np.median(plain) < TOL, ("plain median", np.median(plain))
+    assert np.percentile(plain, 99) < 2 * TOL, ("plain p99", np.percentile(plain, 99))
 
 
 def _rel_err(a, ref):
@@ -118,7 +118,7 @@ def test_one_bounce_step_lj_only(name):
     kscale = md.dt * ACCEL / md.topo.mass * md.grad_scale("short")
     dv = np.linalg.norm(v - md.v, axis=1)
     assert (dv / (np.linalg.norm(md.v, axis=1) + kscale))[~tie].max() < TOL
-    assert np.median(dv / np.linalg.norm(md.v, axis=1)) < TOL
+    assert np.percentile((dv / np.linalg.norm(md.v, axis=1))[~tie], 99) < 2 * TOL
     e = ctx.energies()
     assert e["proposals"] > 0
     ctx.close()

@@ -33,8 +33,8 @@ def _worker(rank, ws, port, out):
     cpu = torch.device("cpu")
     w, r, local = bench._dist()
     t_rank = 1.0 + rank             # rank 1 is the slow one
-    t_max = bench._max_over_ranks(t_rank, w, cpu)
-    total = bench._sum_over_ranks(10.0 * (rank + 1), w, cpu)
+    t_max = bench._reduce(t_rank, w, cpu, "max")
+    total = bench._reduce(10.0 * (rank + 1), w, cpu, "sum")
     bench._barrier(w)
     value = w * bench.ns_per_day(100, t_max)
     out[rank] = (w, r, t_max, total, value)
