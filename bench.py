@@ -1,35 +1,41 @@
-"""Benchmark: BOUNCE vs BAOAB (1 fs) on a 4,096-molecule flexible-water
-droplet (12,288 atoms, 12 A cutoff, cell list) on one GB300.
+"""Benchmark: BOUNCE vs BAOAB (1 fs) on one GB300, at matched observables.
 
-One "step" is one full integrator step (row-rebuild check, F_0 or the full
-gradient, the two jump half-steps, B, A, O).  The headline value is BOUNCE
-ns/day with the split that keeps the observables of BAOAB 1 fs: LJ beyond
-the 4-5 A switch on the jumps, Coulomb in F_0.  BAOAB
-ns/day, pair evaluations per second and the matched-observables comparison
-ride along, with the paper's droplet split (Coulomb on the jumps too), which
-heats flexible water at 1 fs.
+Headline workload: the periodic box of 32,768 flexible 3-site water
+molecules (98,304 atoms, edge 99.3 A): Ewald direct erfc (beta 0.35 A^-1)
+and Lennard-Jones within 9 A, SPME 96^3 of order 5, jumps beyond a 7.5-8.5 A
+switch, 1 fs, friction 1/ps.  `value` is BOUNCE-RESPA (the reciprocal part on
+a 2 fs outer step, paper Sec. V) in ns/day; `baoab` is BAOAB 1 fs on the same
+GPU; BOUNCE-RESPA1 and plain BOUNCE ride along.  One "step" is one 1 fs step
+of the whole path (row and cluster rebuild checks, pair sums, SPME where the
+integrator evaluates it, the jump half-steps, B, A, O).
 
 Protocol (our arm):
-  * the droplet is pre-equilibrated on the GPU with BAOAB (friction 0.05/fs,
-    1,500 steps) from the seeded lattice;
-  * W warm-up steps, then the K timed steps in windows of 25 steps (one
-    run() call each); the trajectory continues across windows, so the row
-    rebuilds it triggers are inside the timed region;
-  * L2 is flushed (a 256 MB write) before each timed window;
-  * device time by CUDA events on the launch stream; nvidia-smi clocks are
+  * the box is melted from the lattice with BAOAB (friction 0.05/fs, 2 ps)
+    and relaxed at 1/ps (2 ps), all on the GPU;
+  * each arm: W warm-up steps, then the K timed steps (rounded up to whole
+    outer steps) in windows of 24 steps, one run() call each, with a 256 MB
+    write before each window (L2 flushed); the trajectory continues across
+    windows, so row and cluster rebuilds are inside the timed region;
+  * device time by CUDA events on the launch stream; nvidia-smi clocks
     sampled during the timed windows;
-  * e2e: the same windows through the public API with host buffers (state
-    upload, run, state download), host wall clock;
-  * roofline: the fused step kernel timed by CUDA events around each launch
-    in a separate profiling pass of the same workload;
-  * the heating split runs 5-step windows, each restarted from the
-    equilibrated state, and reports its temperature after each window;
-  * matched observables: 100 ps per integrator (block means of the potential
-    energy, temperature, O-O pair-distance histogram and O self-diffusion);
-  * a periodic-box section (98,304 atoms, SPME) compares BAOAB with
-    BOUNCE-RESPA and BOUNCE-RESPA1.
---impl reference times the FP64 oracle on the host cores on a bounded sample
-(every 8th atom of the droplet per step; time scaled to all atoms).
+  * e2e: the same windows through the public API with host arrays (state
+    upload from host memory, run, state download), host wall clock;
+  * per-kernel breakdown and the roofline of the pair kernel (the dominant
+    kernel) from CUDA events around each group of launches
+    (bounce_profile_breakdown) over 24 steps of the same trajectory;
+  * matched observables: four independent runs per arm (own Philox seeds)
+    from the relaxed box, 1.2 ps each to decorrelate, then 4.8 ps sampled every
+    0.24 ps: potential energy per molecule, kinetic temperature, O-O g(r) and
+    O self-diffusion; standard errors from the spread of the four runs; a
+    second BAOAB arm with other seeds is the null control;
+  * context: the 4,096-molecule droplet (r_c 12 A) with LJ on the jumps, the
+    force-matching forward + backward on a 4,096-molecule box, and 256
+    replica droplets of 64-1,024 molecules advanced together for 10,000 steps;
+  * cpu_baseline: the FP64 oracle as it stands on a bounded sample of the
+    workload (the same integrator on the 4,096-molecule box of the same
+    density, cutoffs and grid spacing), on one core and on every core (one
+    independent copy per core), scaled by the atom ratio.
+--impl reference times the oracle alone (one core) on the same sample.
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
 """
 import argparse
@@ -47,33 +53,25 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WINDOW = 25       # steps per timed window (one run() call); L2 flushed between windows
-HOT_WINDOW = 5    # windows of the split that heats, each restarted from the 300 K state
-# the headline split: LJ beyond the 4-5 A switch on the jumps, Coulomb (12 A
-# cutoff) in F_0, one bound per atom type (with ~0.1 proposals per atom-step
-# the two-stage choice of per-type-pair bounds saves less than its
-# type-grouped rows cost in the row builds and the F_0 gathers)
-SPLIT = dict(pair_bounds=False, jump_coulomb=False)
-RHO_O = 0.03343   # O atoms per A^3 in water at 1 g/cm^3
-# (name, integrator, split, restart every window)
-ARMS = (("bounce", "BOUNCE", SPLIT, False),
-        ("baoab", "BAOAB", {}, False),
-        ("bounce_coulomb_jumps", "BOUNCE", dict(pair_bounds=True), True),
-        ("bounce_coulomb_jumps_rowmax", "BOUNCE", dict(pair_bounds=False), True))
-WORKLOAD = ("BOUNCE (LJ beyond the 4-5 A switch on jumps, Coulomb in F_0), "
-            "4096-molecule flexible-water droplet (12288 atoms), r_c 12 A, cell list, 1 fs, friction 1/ps")
-N_SIDE = 16                  # 16^3 = 4096 molecules
-R_CUT, R_ON, R_OFF, SKIN = 12.0, 4.0, 5.0, 1.0
+METRIC = "ns/day & pair-evals/s, BOUNCE vs BAOAB 1fs on one GB300 at matched <E>, RDF"
+WINDOW = 24        # steps per timed window (a multiple of every arm's outer step)
+BOX_SIDE = 32      # 32^3 = 32,768 molecules
+R_CUT, R_ON, R_OFF, SKIN, BETA, GRID, ORDER = 9.0, 7.5, 8.5, 1.0, 0.35, 96, 5
 DT = 1.0
-# DRAM bytes (read + write) of one body step (pair-sum kernel + step kernel)
-# with this split on the same-size droplet at its lattice start (ncu, cold
-# caches; ~670 row entries per atom there, ~920 after equilibration)
-K_STEP_TRAFFIC = (34264320 + 768) + (2803200 + 0)  # k_pairs + k_step<BOUNCE>
-# Algorithmic lane-operations per unit of work in the fused step kernel,
-# counted from the kernel source:
-OPS_PER_PROPOSAL = 150       # Philox4x32-10 (~100 int ops) + partner gather + FP32 pair term + decision
-OPS_PER_SHORT_PAIR = 35      # FP32 pair term (displacement, r^2, rsqrt, chi, W'/r, accumulate)
-OPS_PER_FULL_PAIR = 25       # FP32 pair term without the switching function
+RHO_O = 0.03343    # O atoms per A^3 at 1 g/cm^3
+WORKLOAD = ("BOUNCE-RESPA (SPME on the 2 fs outer step) vs BAOAB 1 fs, 32,768-molecule periodic flexible-water box "
+            "(98,304 atoms, edge 99.3 A), Ewald erfc beta 0.35 + LJ within 9 A, SPME 96^3 order 5, "
+            "jumps beyond a 7.5-8.5 A switch, 1 fs, friction 1/ps")
+# Algorithmic lane-operations of one pair inside the cutoff in the cluster
+# pair kernel, counted from the source: displacement 9, r^2 3, 1/r with a
+# Newton step 5, r and 1/r^2 2, Ewald erfc term (A&S 7.1.26 and its
+# exponential) 22, LJ 6, both sides' accumulation 6, charge product 2; the
+# F_0 share adds the switching function and its weight (11).
+OPS_PER_PAIR = {"f0": 66, "full": 55}
+# DRAM traffic of one pair-kernel launch on this machine (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum, BAOAB full pairs at the
+# lattice start), None until measured on the current kernel
+PAIR_TRAFFIC = None
 
 
 def _peaks():
@@ -162,23 +160,13 @@ def _barrier(ws):
         dist.barrier()
 
 
-def _max_over_ranks(x, ws, device):
+def _reduce(x, ws, device, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
     t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def _sum_over_ranks(x, ws, device):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -186,33 +174,70 @@ def ns_per_day(steps, seconds):
     return steps * DT * 1e-6 * 86400.0 / seconds
 
 
-def _windows(steps, w_len):
-    return [w_len] * (steps // w_len) + ([steps % w_len] if steps % w_len else [])
+def box_cfg(device, **kw):
+    cfg = dict(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, skin=SKIN, dt=DT, ewald_beta=BETA, pme_grid=(GRID,) * 3,
+               pme_order=ORDER, max_neighbors=1024, device=device)
+    cfg.update(kw)
+    return cfg
 
 
-def time_arm(bounce, s, q0, v0, cfg, integ, extra, restart, args, flush, stream, sh, ws, rank, local, name,
-             e2e=False, profile=False):
-    """K timed steps of one integrator in windows (L2 flushed before each);
-    continuing arms carry the trajectory across windows, so the row rebuilds
-    it triggers are timed; restarting arms begin every window at the
-    equilibrated state (a split that heats)."""
+# The jump step's candidate rows are rebuilt when an atom has moved half
+# their skin; a wider skin makes them rarer (and longer) while the cluster
+# lists of the pair sums keep a 1 A skin.  BAOAB reads no rows.
+JUMP_ROWS = dict(skin=2.5, pair_skin=1.0, max_neighbors=2048)
+# (name, integrator name, extra config, outer period in steps)
+BOX_ARMS = (("bounce_respa", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2),
+            ("baoab", "BAOAB", {}, 1),
+            ("bounce_respa1", "BOUNCE_RESPA1", dict(JUMP_ROWS, respa_m=2, respa_m2=3), 6),
+            ("bounce", "BOUNCE", dict(JUMP_ROWS), 1))
+
+
+EQ_STRONG, EQ_STEPS, EQ_EVERY = 2000, 8000, 1000
+
+
+def equilibrate_box(bounce, s, device, sh, seed):
+    """Lattice -> liquid: BAOAB at friction 0.05/fs for 2 ps, then at the
+    workload's 1/ps for 8 ps; returns the state and the trace of the
+    temperature and the potential energy per molecule every ps of the second
+    part (flat over its last half when the box is relaxed)."""
+    eq = bounce.from_system(s, seed=seed, gamma=0.05, **box_cfg(device))
+    eq.set_state(s.q, s.v)
+    eq.run(EQ_STRONG, bounce.BAOAB, stream=sh)
+    q, v = eq.get_state(stream=sh)
+    eq.close()
+    eq = bounce.from_system(s, seed=seed + 1, **box_cfg(device))
+    eq.set_state(q, v)
+    n_mol = s.n_atoms // 3
+    trace = []
+    for _ in range(EQ_STEPS // EQ_EVERY):
+        eq.run(EQ_EVERY, bounce.BAOAB, stream=sh)
+        e = eq.energies(stream=sh)
+        trace.append((round(e["temperature"], 1), round(e["potential"] / n_mol, 4)))
+    q, v = eq.get_state(stream=sh)
+    eq.close()
+    return q, v, trace
+
+
+def _round_up(k, m):
+    return ((k + m - 1) // m) * m
+
+
+def time_arm(bounce, ctx, q0, v0, integ, period, args, flush, stream, sh, ws, local, e2e=False):
+    """W warm-up steps, then K timed steps (rounded up to whole outer steps)
+    in windows (L2 flushed before each); the trajectory continues."""
     import torch
-    w_len = HOT_WINDOW if restart else WINDOW
-    windows = _windows(args.steps, w_len)
-    ctx = bounce.from_system(s, seed=7 + rank, **cfg, **extra)
+    steps = _round_up(args.steps, period)
+    windows = [WINDOW] * (steps // WINDOW) + ([steps % WINDOW] if steps % WINDOW else [])
     ctx.set_state(q0, v0, step=0)
-    ctx.run(args.warmup, integ, stream=sh)
+    ctx.run(_round_up(args.warmup, period), integ, stream=sh)
     torch.cuda.synchronize()
     ctx.reset_counters(stream=sh)
-    ms, launches, t_end = 0.0, 0, []
+    ms, launches = 0.0, 0
     with Clocks(local) as clk:
         _barrier(ws)
         torch.cuda.synchronize()
         clk.start()
-        torch.cuda.nvtx.range_push(name + "_timed")
         for k, w in enumerate(windows):
-            if restart:
-                ctx.set_state(q0, v0, step=100000 * (k + 1))
             launches += ctx.run_launch_count(w, integ)
             flush.fill_(float(k))
             a = torch.cuda.Event(enable_timing=True)
@@ -222,22 +247,18 @@ def time_arm(bounce, s, q0, v0, cfg, integ, extra, restart, args, flush, stream,
             b.record(stream)
             b.synchronize()
             ms += a.elapsed_time(b)
-            if restart:
-                t_end.append(ctx.energies(stream=sh)["temperature"])
-        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         clk.stop()
         _barrier(ws)
-    e = ctx.energies(stream=sh)
-    out = dict(ms=ms, clocks=clk.summary(), energies=e, t_end=t_end, launches=launches, windows=len(windows),
-               w_len=w_len)
+    out = dict(ms=ms, steps=steps, clocks=clk.summary(), energies=ctx.energies(stream=sh), launches=launches,
+               windows=len(windows))
     if e2e:
         # the same windows through the public API with host buffers: state
-        # upload, run, state download (the trajectory continues on the host)
-        q, v, step, t_e2e = q0, v0, 200000, 0.0
-        for k, w in enumerate(windows):
-            if restart:
-                q, v = q0, v0
+        # upload from host memory, run, state download (the trajectory
+        # continues through the host)
+        q, v = ctx.get_state(stream=sh)
+        step, t_e2e = 0, 0.0
+        for w in windows:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx.set_state(q, v, step=step)
@@ -246,20 +267,21 @@ def time_arm(bounce, s, q0, v0, cfg, integ, extra, restart, args, flush, stream,
             t_e2e += time.perf_counter() - t0
             step += w
         out["e2e_s"] = t_e2e
-    if profile:
-        # fused step kernel timed by CUDA events around each launch
-        ctx.set_state(q0, v0, step=300000)
-        ctx.reset_counters(stream=sh)
-        out["kernel_ms"], out["kernel_launches"] = ctx.profile_steps(min(args.steps, WINDOW), integ, stream=sh)
-        out["prof"] = ctx.energies(stream=sh)
-    ctx.close()
+        out["e2e_bytes"] = 2 * q.size * 8
+    # per-kernel breakdown over 24 steps of the same trajectory
+    ctx.reset_counters(stream=sh)
+    ms_k, groups = ctx.profile_breakdown(WINDOW, integ, stream=sh)
+    e = ctx.energies(stream=sh)
+    out["breakdown"] = {k: round(v / WINDOW, 5) for k, v in ms_k.items()}
+    out["pair_launch_ms"] = ms_k["pairs"] / max(int(groups[0]), 1)
+    out["pairs_per_launch"] = (e["short_pairs"] + e["full_pairs"]) / max(int(groups[0]), 1)
     return out
 
 
 def our_arm(args):
     import torch
     from paper_2002_07109_gb300 import bounce
-    from paper_2002_07109_gb300.water import water_droplet
+    from paper_2002_07109_gb300.water import water_box
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -269,353 +291,420 @@ def our_arm(args):
         dist.init_process_group("nccl", init_method="env://")
     stream = torch.cuda.current_stream(device)
     sh = stream.cuda_stream
-    s = water_droplet(N_SIDE, seed=rank)
-    cfg = dict(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, skin=SKIN, dt=DT, device=local)
-    # pre-equilibration
-    eq = bounce.from_system(s, seed=1000 + rank, gamma=0.05, **cfg)
-    eq.set_state(s.q, s.v)
-    eq.run(1500, bounce.BAOAB, stream=sh)
-    q0, v0 = eq.get_state()
-    e_eq = eq.energies()
-    eq.close()
+    s = water_box(BOX_SIDE, seed=rank)
+    q0, v0, eq_trace = equilibrate_box(bounce, s, local, sh, 500 + rank)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
     res = {}
-    for name, integ, extra, restart in ARMS:
-        res[name] = time_arm(bounce, s, q0, v0, cfg, getattr(bounce, integ), extra, restart, args, flush, stream, sh,
-                             ws, rank, local, name, e2e=name == "bounce", profile=name in ("bounce", "baoab"))
-    steps = args.steps
+    for name, integ, extra, period in BOX_ARMS:
+        ctx = bounce.from_system(s, seed=21 + rank, **box_cfg(local, **extra))
+        res[name] = time_arm(bounce, ctx, q0, v0, getattr(bounce, integ), period, args, flush, stream, sh, ws, local,
+                             e2e=name == "bounce_respa")
+        ctx.close()
+    h, a = res["bounce_respa"], res["baoab"]
+    t_h = _reduce(h["ms"] / 1e3, ws, device, "max")
+    t_a = _reduce(a["ms"] / 1e3, ws, device, "max")
+    value = ws * ns_per_day(h["steps"], t_h)
+    baoab_value = ws * ns_per_day(a["steps"], t_a)
     n_atoms = s.n_atoms
-    b, a = res["bounce"], res["baoab"]
-    t_b = _max_over_ranks(b["ms"] / 1e3, ws, device)
-    t_a = _max_over_ranks(a["ms"] / 1e3, ws, device)
-    value = ws * ns_per_day(steps, t_b)
-    baoab_value = ws * ns_per_day(steps, t_a)
-    pe_b = _sum_over_ranks(b["energies"]["short_pairs"] + b["energies"]["proposals"], ws, device) / t_b
-    pe_a = _sum_over_ranks(a["energies"]["full_pairs"], ws, device) / t_a
-    # roofline of the fused BOUNCE step kernel: algorithmic lane-ops per launch / launch time
-    prof = b["prof"]
-    ops = OPS_PER_PROPOSAL * prof["proposals"] + OPS_PER_SHORT_PAIR * prof["short_pairs"]
-    per_launch_s = b["kernel_ms"] / 1e3 / b["kernel_launches"]
-    achieved = ops / b["kernel_launches"] / per_launch_s / 1e12
-    clk = b["clocks"]
+    # pair evaluations per second: F_0 pairs + proposals (BOUNCE), full pairs (BAOAB)
+    pe_h = _reduce(h["energies"]["short_pairs"] + h["energies"]["proposals"], ws, device, "sum") / t_h
+    pe_a = _reduce(a["energies"]["full_pairs"], ws, device, "sum") / t_a
+    clk = h["clocks"]
     sm_mhz = clk.get("sm_mhz") or 1995.0
     peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # FP32/INT32 lane-ops per second at the sampled clock
-    ops_a = OPS_PER_FULL_PAIR * a["prof"]["full_pairs"]
-    ach_a = ops_a / a["kernel_launches"] / (a["kernel_ms"] / 1e3 / a["kernel_launches"]) / 1e12
-    h2d = 2 * n_atoms * 3 * 8
-    e2e_val = ws * ns_per_day(steps, _max_over_ranks(b["e2e_s"], ws, device))
 
-    def hot(name):
+    def roof(r, kind):
+        return r["pairs_per_launch"] * OPS_PER_PAIR[kind] / (r["pair_launch_ms"] / 1e3) / 1e12
+
+    ach = roof(h, "f0")
+    e2e_val = ws * ns_per_day(h["steps"], _reduce(h["e2e_s"], ws, device, "max"))
+    arms = {}
+    for name, _, _, _ in BOX_ARMS:
         r = res[name]
-        t = _max_over_ranks(r["ms"] / 1e3, ws, device)
+        t = _reduce(r["ms"] / 1e3, ws, device, "max")
         e = r["energies"]
-        return {"value": round(ws * ns_per_day(steps, t), 4), "unit": "ns/day",
-                "proposals_per_atom_step": round(e["proposals"] / (steps * n_atoms), 3),
-                "accepts_per_atom_step": round(e["accepts"] / (steps * n_atoms), 3),
-                "temperature_end_of_windows_K": [round(x, 1) for x in r["t_end"]][:4]}
-
+        arms[name] = {"value": round(ws * ns_per_day(r["steps"], t), 3), "unit": "ns/day",
+                      "ms_per_step": round(t * 1e3 / r["steps"], 5), "steps": r["steps"],
+                      "proposals_per_atom_step": round(e["proposals"] / (r["steps"] * n_atoms), 5),
+                      "accepts_per_atom_step": round(e["accepts"] / (r["steps"] * n_atoms), 6),
+                      "breakdown_ms_per_step": r["breakdown"],
+                      "pair_kernel_ms_per_launch": round(r["pair_launch_ms"], 5),
+                      "pairs_in_cutoff_per_launch": int(r["pairs_per_launch"]),
+                      "temperature_end_K": round(e["temperature"], 1)}
     line = {
-        "metric": "ns/day & pair-evals/s, BOUNCE vs BAOAB 1fs on one GB300 at matched <E>, RDF",
+        "metric": METRIC,
         "value": round(value, 4),
         "unit": "ns/day",
         "n_gpus": ws,
-        "steps": steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(t_b * 1e3 / steps, 5),
+        "steps": h["steps"],
+        "warmup": _round_up(args.warmup, 2),
+        "ms_per_step": round(t_h * 1e3 / h["steps"], 5),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32 pair math, f64 integration",
-        "data": "synthetic: seeded lattice water droplet, BAOAB pre-equilibrated at 300 K",
+        "data": "synthetic: seeded lattice water box, melted and relaxed with BAOAB on the GPU",
         "config": {"workload": WORKLOAD, "atoms": n_atoms, "windows_of_steps": WINDOW,
-                   "l2": "flushed before each timed window",
-                   "trajectory": "continues across windows (row rebuilds are timed)",
+                   "l2": "flushed before each timed window (256 MB write)",
+                   "trajectory": "continues across windows (row, cluster and SPME work timed)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "baoab": {"value": round(baoab_value, 4), "unit": "ns/day", "ms_per_step": round(t_a * 1e3 / steps, 5),
+        "baoab": {"value": round(baoab_value, 4), "unit": "ns/day", "ms_per_step": round(t_a * 1e3 / a["steps"], 5),
                   "pair_evals_per_s": pe_a},
-        "bounce_pair_evals_per_s": pe_b,
         "speedup_vs_own_baoab": round(value / baoab_value, 4),
-        "proposals_per_atom_step": b["energies"]["proposals"] / (steps * n_atoms),
-        "accepts_per_atom_step": b["energies"]["accepts"] / (steps * n_atoms),
-        "near_ties": b["energies"]["near_ties"],
-        "rebuilds_in_timed_region": {"bounce": b["energies"]["rebuilds"], "baoab": a["energies"]["rebuilds"]},
-        "temperature_after_timed_steps_K": {"bounce": round(b["energies"]["temperature"], 1),
-                                            "baoab": round(a["energies"]["temperature"], 1)},
-        "bounce_coulomb_jumps": dict(
-            hot("bounce_coulomb_jumps"),
-            split="Coulomb and LJ beyond the 4-5 A switch on the jumps (the paper's droplet split); it heats "
-                  "flexible water at 1 fs, so each %d-step window restarts from the 300 K state" % HOT_WINDOW,
-            rowmax_bounds=hot("bounce_coulomb_jumps_rowmax")),
-        "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "Tops/s",
-                     "frac": round(achieved / peak, 4), "traffic": K_STEP_TRAFFIC,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, the k_pairs and "
-                                       "k_step<BOUNCE> launches of one body step with this split on the "
-                                       "same-size lattice droplet",
-                     "kernel": "k_pairs + k_step<BOUNCE> (F_0 pair sums; bonded terms, 2 jump half-steps, "
-                               "B A O A)",
-                     "baoab_kernel_frac": round(ach_a / peak, 4)},
-        "e2e": {"value": round(e2e_val, 4), "unit": "ns/day", "h2d_bytes_per_step": h2d * b["windows"] // steps,
-                "d2h_bytes_per_step": h2d * b["windows"] // steps},
-        "gpu_launches": b["launches"],
+        "bounce_pair_evals_per_s": pe_h,
+        "arms": arms,
+        "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3), "unit": "Tops/s",
+                     "frac": round(ach / peak, 4), "traffic": PAIR_TRAFFIC,
+                     "kernel": "k_cl_pairs (F_0 pair sums over the cluster lists, BOUNCE-RESPA)",
+                     "algorithmic_ops": "%d lane-ops per unique pair inside r_c" % OPS_PER_PAIR["f0"],
+                     "peak_source": "152 SMs x 128 FP32/INT32 lanes x sampled SM clock",
+                     "baoab_pair_kernel_frac": round(roof(a, "full") / peak, 4)},
+        "e2e": {"value": round(e2e_val, 4), "unit": "ns/day",
+                "h2d_bytes_per_step": h["e2e_bytes"] * h["windows"] // h["steps"],
+                "d2h_bytes_per_step": h["e2e_bytes"] * h["windows"] // h["steps"]},
+        "gpu_launches": h["launches"],
         "clocks": clk,
     }
-    line["matched_observables"] = matched_observables(s, q0, v0, cfg, rank, stream, sh)
-    line["pbc_box"] = pbc_box(rank, stream, sh)
+    line["matched_observables"] = matched_observables(bounce, s, q0, v0, local, stream, sh, rank)
+    line["matched_observables"]["equilibration"] = {
+        "protocol": "BAOAB %d steps at friction 0.05/fs, then %d steps at 1/ps" % (EQ_STRONG, EQ_STEPS),
+        "T_K_and_Epot_per_molecule_every_ps": eq_trace}
+    line["droplet_context"] = droplet_context(bounce, local, stream, sh, rank, args)
+    line["force_matching"] = force_matching(bounce, local, rank)
+    line["batched_replicas"] = batched_replicas(bounce, local, stream, sh, rank)
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(s)
+        line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def _block_stats(x):
+def _mean_se(x):
     x = np.asarray(x, dtype=np.float64)
     return x.mean(0), x.std(0, ddof=1) / math.sqrt(len(x))
 
 
-def matched_observables(s, q0, v0, cfg, rank, stream, sh, n_eq=5000, n_blocks=50, block=2000, samples=10):
-    """Long runs from the equilibrated droplet for the matched-observables
-    comparison with BAOAB 1 fs: n_eq steps of equilibration, then n_blocks
-    blocks of `block` steps (100 ps).  Per block: the means of the potential
-    energy per molecule, the kinetic temperature and the O-O pair-distance
-    histogram (0-8 A, 0.2 A bins, pairs per O atom; the droplet's RDF
-    observable, reported as g(r) over bulk density) over `samples` evenly
-    spaced samples, and the self-diffusion
-    coefficient of O from the growth of the mean squared displacement between
-    the block's middle and end (D = (MSD(2 ps) - MSD(1 ps)) / 6 ps).  Each arm
-    is compared with BAOAB by z = |difference of block means| / combined
-    standard error (RDF: chi^2 per bin over the bins with counts, and the
-    largest per-bin z).  ns/day here are over graph-captured chunks without
-    L2 flushes, for context."""
+def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=4, decor=1200, prod=4800, every=240):
+    """Four independent runs per arm from the relaxed box (own Philox
+    seeds): `decor` steps, then `prod` steps sampled every `every` steps
+    (all multiples of every arm's outer step).
+    Per run: mean potential energy per molecule, mean kinetic temperature,
+    O-O pair-distance histogram (0-8 A, 0.1 A bins) as g(r), and the O
+    self-diffusion D from the mean squared displacement over the production
+    (MSD(end) - MSD(middle)) / (6 * half the production).  Across runs: mean
+    and standard error of the run means; z = |difference| / combined SE
+    against the BAOAB arm (g(r): chi^2 per bin over bins with pairs, and the
+    largest bin z).  baoab_control is BAOAB with other seeds: the null."""
     import torch
-    from paper_2002_07109_gb300 import bounce
     n_mol = s.n_atoms // 3
     n_o = int((s.type == 0).sum())
-    # baoab_control: BAOAB again with other Philox streams, the null
-    # comparison that shows the spread of z between two runs of one method
-    arms = (("baoab", bounce.BAOAB, {}, 31),
-            ("baoab_control", bounce.BAOAB, {}, 131),
-            ("bounce", bounce.BOUNCE, SPLIT, 31),
-            ("bounce_respa_ext_2fs", bounce.BOUNCE_RESPA_EXT, dict(SPLIT, respa_m=2), 31))
-    chunk = block // samples
-    edges = np.arange(41) * 0.2
+    L = float(s.box[0])
+    edges = np.arange(81) * 0.1
     shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
-    raw, out = {}, {"protocol": "%d equilibration steps, then %d blocks of %d steps (%g ps) per arm, from the "
-                                "BAOAB-equilibrated droplet; friction 1/ps" % (n_eq, n_blocks, block,
-                                                                                n_blocks * block / 1000)}
-    for name, integ, extra, seed in arms:
-        ctx = bounce.from_system(s, seed=seed + rank, **cfg, **extra)
-        ctx.set_state(q0, v0, step=0)
-        obs = {"pe": [], "T": [], "D": [], "rdf": []}
+    arms = (("baoab", "BAOAB", {}, 1, 100),
+            ("baoab_control", "BAOAB", {}, 1, 200),
+            ("bounce_respa", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2, 100),
+            ("bounce_respa1", "BOUNCE_RESPA1", dict(JUMP_ROWS, respa_m=2, respa_m2=3), 6, 100))
+    raw = {}
+    out = {"protocol": "%d runs per arm from the relaxed box, %d steps to decorrelate, then %d steps sampled every %d; "
+                       "standard errors from the spread of the runs" % (runs, decor, prod, every)}
+    for name, integ_name, extra, period, seed0 in arms:
+        integ = getattr(bounce, integ_name)
+        per_run = {"pe": [], "T": [], "D": [], "g": []}
         ms, err = 0.0, None
-        try:
-            ctx.run(n_eq, integ, stream=sh)
-            for _ in range(n_blocks):
+        for r in range(runs):
+            ctx = bounce.from_system(s, seed=seed0 + 17 * r + 1000 * rank, **box_cfg(device, **extra))
+            try:
+                ctx.set_state(q0, v0, step=0)
+                ctx.run(decor, integ, stream=sh)
                 ctx.set_msd_reference(stream=sh)
-                pe, T, rdf, msd = [], [], np.zeros(40), []
-                for k in range(samples):
+                pe, T, hist, msd = [], [], np.zeros(80), {}
+                for k in range(prod // every):
                     a = torch.cuda.Event(enable_timing=True)
                     b = torch.cuda.Event(enable_timing=True)
                     a.record(stream)
-                    ctx.run(chunk, integ, stream=sh)
+                    ctx.run(every, integ, stream=sh)
                     b.record(stream)
                     b.synchronize()
                     ms += a.elapsed_time(b)
                     e = ctx.energies(stream=sh)
-                    pe.append(e["potential"] / n_mol)
+                    pe.append((e["potential"]) / n_mol)
                     T.append(e["temperature"])
-                    rdf += ctx.pair_histogram(0, 0, 8.0, 40, stream=sh) * (2.0 / n_o)
-                    if k in (samples // 2 - 1, samples - 1):
-                        msd.append(ctx.msd(0, stream=sh))
-                obs["pe"].append(np.mean(pe))
-                obs["T"].append(np.mean(T))
-                obs["rdf"].append(rdf / samples)
-                obs["D"].append((msd[1] - msd[0]) / (6.0 * block / 2000.0))  # A^2/ps
-        except Exception as ex:  # a blown-up state is reported, not compared
-            err = str(ex).split("(")[0].strip()
-        ctx.close()
-        raw[name] = obs
-        r = {"steps": n_eq + len(obs["pe"]) * block}
+                    hist += ctx.pair_histogram(0, 0, 8.0, 80, stream=sh)
+                    if k + 1 in (prod // every // 2, prod // every):
+                        msd[k + 1] = ctx.msd(0, stream=sh)
+                nk = prod // every
+                per_run["pe"].append(np.mean(pe))
+                per_run["T"].append(np.mean(T))
+                per_run["g"].append(hist / nk * 2.0 / n_o / (RHO_O * shell))
+                per_run["D"].append((msd[nk] - msd[nk // 2]) / (6.0 * (prod / 2) * DT / 1000.0))  # A^2/ps
+            except Exception as ex:  # a blown-up state is reported, not compared
+                err = str(ex).split("(")[0].strip()
+            ctx.close()
+            if err:
+                break
+        raw[name] = per_run
+        res = {"runs": len(per_run["pe"])}
         if err:
-            r["stopped"] = err
-        else:
-            r["ns_per_day"] = round(ns_per_day(n_blocks * block, ms / 1e3), 2)
+            res["stopped"] = err
+        if per_run["pe"]:
+            res["ns_per_day"] = round(ns_per_day(len(per_run["pe"]) * prod, ms / 1e3), 2)
+        if len(per_run["pe"]) >= 2:
             for k, unit in (("pe", "kcal/mol per molecule"), ("T", "K"), ("D", "A^2/ps")):
-                m, se = _block_stats(obs[k])
-                r[k] = {"mean": round(float(m), 4), "se": round(float(se), 4), "unit": unit}
-            m, _ = _block_stats(obs["rdf"])
-            g = m / (RHO_O * shell)   # pairs per O over the bulk-water expectation: g(r) of the droplet
-            k = int(np.argmax(g[:20]))
-            r["rdf_oo_first_peak"] = {"g": round(float(g[k]), 4), "r_A": round(0.2 * (k + 0.5), 2)}
-            if name != "baoab" and "rdf" in raw.get("baoab", {}) and raw["baoab"]["rdf"]:
-                ref = raw["baoab"]
+                m, se = _mean_se(per_run[k])
+                res[k] = {"mean": round(float(m), 5), "se": round(float(se), 5), "unit": unit}
+            m, _ = _mean_se(per_run["g"])
+            kk = int(np.argmax(m[:40]))
+            res["g_oo_first_peak"] = {"g": round(float(m[kk]), 4), "r_A": round(0.1 * (kk + 0.5), 2)}
+            ref = raw.get("baoab")
+            if name != "baoab" and ref and len(ref["pe"]) >= 2:
                 z = {}
                 for k in ("pe", "T", "D"):
-                    m1, e1 = _block_stats(obs[k])
-                    m2, e2 = _block_stats(ref[k])
+                    m1, e1 = _mean_se(per_run[k])
+                    m2, e2 = _mean_se(ref[k])
                     z[k] = round(float(abs(m1 - m2) / math.hypot(e1, e2)), 2)
-                m1, e1 = _block_stats(obs["rdf"])
-                m2, e2 = _block_stats(ref["rdf"])
+                m1, e1 = _mean_se(per_run["g"])
+                m2, e2 = _mean_se(ref["g"])
                 ok = (e1 + e2) > 0
                 zb = np.abs(m1 - m2)[ok] / np.hypot(e1, e2)[ok]
-                z["rdf_chi2_per_bin"] = round(float((zb ** 2).mean()), 2)
-                z["rdf_max_bin_z"] = round(float(zb.max()), 2)
-                r["z_vs_baoab"] = z
-        out[name] = r
+                z["g_oo_chi2_per_bin"] = round(float((zb ** 2).mean()), 2)
+                z["g_oo_max_bin_z"] = round(float(zb.max()), 2)
+                z["matched"] = bool(max(z["pe"], z["T"], z["D"]) < 2.0 and z["g_oo_chi2_per_bin"] < 2.0)
+                res["z_vs_baoab"] = z
+        out[name] = res
     return out
 
 
-def pbc_box(rank, stream, sh, n_steps=960, chunk=48):
-    """The periodic box of 32,768 water molecules (98,304 atoms, edge 99.3 A):
-    Ewald direct erfc (beta 0.35) and LJ within 9 A, SPME 96^3 of order 5,
-    jumps beyond a 7.5-8.5 A switch (one bound per atom type), 1 fs, friction
-    1/ps.  From a BAOAB-equilibrated state, graph-captured runs of n_steps
-    after one warm-up chunk: BAOAB (SPME every step), BOUNCE (SPME every
-    step), BOUNCE-RESPA (SPME on the 2 fs outer step) and BOUNCE-RESPA1
-    (short-range pairs on 2 fs, SPME on 6 fs).  ns/day over the chunks (CUDA events), and the means of the
-    potential energy per molecule and of the temperature after every chunk."""
+def droplet_context(bounce, device, stream, sh, rank, args):
+    """The 4,096-molecule droplet (12,288 atoms, r_c 12 A): BOUNCE with LJ
+    beyond the 4-5 A switch on the jumps (Coulomb in F_0) and BAOAB, K steps
+    each in windows of 24 after W warm-up steps (context: the paper's droplet
+    split with Coulomb on the jumps heats flexible water at 1 fs)."""
     import torch
-    from paper_2002_07109_gb300 import bounce
-    from paper_2002_07109_gb300.water import water_box
-    s = water_box(32, seed=rank)
-    n_mol = s.n_atoms // 3
-    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=1.0, dt=1.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
-               pme_order=5, max_neighbors=1024, max_short=640, device=torch.cuda.current_device())
-    eq = bounce.from_system(s, seed=500 + rank, gamma=0.05, **cfg)
+    from paper_2002_07109_gb300.water import water_droplet
+    s = water_droplet(16, seed=rank)
+    cfg = dict(r_on=4.0, r_off=5.0, r_cut=12.0, skin=1.0, dt=DT, device=device)
+    eq = bounce.from_system(s, seed=1000 + rank, gamma=0.05, **cfg)
     eq.set_state(s.q, s.v)
-    eq.run(600, bounce.BAOAB, stream=sh)
+    eq.run(1500, bounce.BAOAB, stream=sh)
     q0, v0 = eq.get_state(stream=sh)
     eq.close()
-    out = {"workload": "32,768-molecule periodic water box (98,304 atoms), erfc beta 0.35, r_c 9 A, SPME 96^3 order 5, "
-                       "switch 7.5-8.5 A, 1 fs, friction 1/ps"}
-    arms = (("baoab", bounce.BAOAB, dict(pair_bounds=False)),
-            ("bounce", bounce.BOUNCE, dict(pair_bounds=False)),
-            ("bounce_respa", bounce.BOUNCE_RESPA, dict(pair_bounds=False, respa_m=2)),
-            ("bounce_respa1", bounce.BOUNCE_RESPA1, dict(pair_bounds=False, respa_m=2, respa_m2=3)))
-    for name, integ, extra in arms:
-        ctx = bounce.from_system(s, seed=21 + rank, **cfg, **extra)
-        ctx.set_state(q0, v0, step=0)
-        ms, pe, T, done, err = 0.0, [], [], 0, None
-        try:
-            ctx.run(chunk, integ, stream=sh)
-            torch.cuda.synchronize()
-            ctx.reset_counters(stream=sh)
-            for _ in range(n_steps // chunk):
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ctx.run(chunk, integ, stream=sh)
-                b.record(stream)
-                b.synchronize()
-                ms += a.elapsed_time(b)
-                done += chunk
-                e = ctx.energies(stream=sh)
-                pe.append(e["potential"] / n_mol)
-                T.append(e["temperature"])
-            props = ctx.energies(stream=sh)["proposals"]
-        except Exception as ex:  # a blown-up state is reported, not timed
-            err = str(ex).split("(")[0].strip()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=torch.device("cuda", device))
+    out = {"workload": "4,096-molecule flexible-water droplet (12,288 atoms), r_c 12 A, switch 4-5 A, 1 fs"}
+    for name, integ, extra in (("bounce_lj_jumps", bounce.BOUNCE, dict(jump_coulomb=False)),
+                               ("baoab", bounce.BAOAB, {})):
+        ctx = bounce.from_system(s, seed=7 + rank, **cfg, **extra)
+        r = time_arm(bounce, ctx, q0, v0, integ, 1, args, flush, stream, sh, 1, device)
         ctx.close()
-        r = {"steps": done}
-        if done:
-            r.update({"ns_per_day": round(ns_per_day(done, ms / 1e3), 2), "pe_per_molecule": round(float(np.mean(pe)), 4),
-                      "temperature_K": round(float(np.mean(T)), 1)})
-            if integ != bounce.BAOAB and err is None:
-                r["proposals_per_atom_step"] = round(props / (done * s.n_atoms), 4)
-        if err:
-            r["stopped"] = err
-        out[name] = r
+        out[name] = {"value": round(ns_per_day(r["steps"], r["ms"] / 1e3), 2), "unit": "ns/day",
+                     "breakdown_ms_per_step": r["breakdown"],
+                     "temperature_end_K": round(r["energies"]["temperature"], 1)}
     return out
 
 
-def _oracle_setup(s):
+def batched_replicas(bounce, device, stream, sh, rank, n_steps=10000, n_baoab=1000):
+    """256 independent droplets of 64-1,024 molecules (seeded sizes), each
+    with its own Philox seed, in one context: every step advances every
+    replica in the same launches; run() replays one CUDA graph per 32 steps;
+    the all-pairs pair kernel is a resident grid over the static work queue
+    of (replica, 32-atom i-tile, j-block) items, its j-block length and grid
+    chosen by the autotuner.  BOUNCE with LJ beyond the 4-5 A switch on the
+    jumps (Coulomb in F_0), and BAOAB beside it; aggregate ns/day (sum over
+    replicas) and replica-steps per second."""
+    import torch
+    from paper_2002_07109_gb300.water import concat_systems, replica_sizes, water_droplet_molecules
+    sizes = replica_sizes(256, seed=rank)
+    systems = [water_droplet_molecules(int(m), seed=100 + r + 1000 * rank) for r, m in enumerate(sizes)]
+    cat, off = concat_systems(systems)
+    seeds = np.arange(256, dtype=np.uint64) + 7 + 1000 * rank
+    out = {"workload": "256 droplets of 64-1,024 molecules (%d atoms in all), no cutoff, switch 4-5 A, 1 fs"
+                       % cat.n_atoms}
+    stream = torch.cuda.current_stream(torch.device("cuda", device))
+    for name, integ, steps in (("bounce_lj_jumps", bounce.BOUNCE, n_steps), ("baoab", bounce.BAOAB, n_baoab)):
+        ctx = bounce.from_system(cat, seed=1, r_on=4.0, r_off=5.0, r_cut=math.inf, jump_coulomb=False,
+                                 max_neighbors=int(np.diff(off).max()), device=device)
+        ctx.set_replicas(off, seeds)
+        ctx.set_state(cat.q, cat.v)
+        tune = ctx.autotune(integ, stream=sh)
+        ctx.run(64, integ, stream=sh)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.run(steps, integ, stream=sh)
+        b.record(stream)
+        b.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        e = ctx.energies(stream=sh)
+        ctx.close()
+        out[name] = {"steps": steps, "aggregate_ns_per_day": round(256 * ns_per_day(steps, sec), 2),
+                     "replica_steps_per_s": round(256 * steps / sec, 1), "ms_per_step": round(sec * 1e3 / steps, 4),
+                     "tuning": {"tile_j": tune["tile_j"], "tile_blocks": tune["tile_blocks"],
+                                "pair_kernel_ms": round(tune["pair_ms"], 4)},
+                     "temperature_end_K": round(e["temperature"], 1)}
+    return out
+
+
+def force_matching(bounce, device, rank, reps=5):
+    """Forward + backward of the force-matching loss sum |F - F_t|^2 through
+    the autograd binding on the 4,096-molecule box (Ewald erfc beta 0.35 and
+    LJ within 9 A); time per evaluation (CUDA events)."""
+    import torch
+    from paper_2002_07109_gb300.water import water_box
+    s = water_box(16, seed=7 + rank)
+    dev = torch.device("cuda", device)
+    ctx = bounce.from_system(s, seed=1, r_on=4.0, r_off=5.0, r_cut=9.0, ewald_beta=BETA, skin=1.0,
+                             max_neighbors=1024, device=device)
+    ctx.set_state(s.q, s.v)
+    qt = torch.tensor([-0.834, 0.417], dtype=torch.float64, requires_grad=True)
+    sig = torch.tensor([[3.15, 0.0], [0.0, 0.0]], dtype=torch.float64, requires_grad=True)
+    eps = torch.tensor([[0.152, 0.0], [0.0, 0.0]], dtype=torch.float64, requires_grad=True)
+    q = torch.tensor(s.q, dtype=torch.float64, device=dev, requires_grad=True)
+    Fn = bounce.pair_forces_function()
+    F_t = torch.zeros((s.n_atoms, 3), dtype=torch.float64, device=dev)
+    ms = []
+    for k in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        F, E = Fn.apply(q, qt, sig, eps, ctx)
+        loss = ((F - F_t) ** 2).sum() + 0.5 * E.to(dev)
+        loss.backward()
+        b.record()
+        b.synchronize()
+        if k:
+            ms.append(a.elapsed_time(b))
+    ctx.close()
+    return {"workload": "force matching, 4,096-molecule box (12,288 atoms), r_c 9 A", "ms_per_forward_backward":
+            round(float(np.median(ms)), 3)}
+
+
+def _oracle_sample():
+    """The bounded sample of the workload: the 4,096-molecule box of the same
+    density (edge 49.7 A), the same cutoffs, switch and Ewald beta, an SPME
+    grid of the same spacing (48^3), BOUNCE-RESPA."""
     from oracle.forcefield import Params
     from oracle.integrate import OracleMD, Topology
+    from paper_2002_07109_gb300.water import water_box
+    s = water_box(16, seed=0)
     topo = Topology(s.type, s.mass, s.charge, s.molecule, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0)
-    p = Params(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps,
-               coulomb_jumps=SPLIT["jump_coulomb"])
-    return topo, p
+    p = Params(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, ewald_beta=BETA, box=s.box, lj_sigma=s.lj_sigma,
+               lj_eps=s.lj_eps, pme_grid=(48, 48, 48), pme_order=ORDER)
+    return OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN), s.n_atoms
 
 
-def oracle_sample_step(md, sample):
-    """One BJAOAJB step of the oracle restricted to the sampled atoms (the
-    other atoms stay put): rows, F_0 and both jump half-steps for `sample`."""
-    from oracle import philox
-    from oracle.forcefield import ACCEL, pair_gradients, bonded_gradients
-    from oracle.integrate import jump_half, o_step
-    from oracle.neighbors import rows, to_pairs
-    q, v, t, p = md.q, md.v, md.topo, md.p
-    r = rows(q, t.mol, md.r_list, p.box, atoms=sample)
-    ii, jj = to_pairs(r, sample)
-    h = 0.5 * md.dt
-
-    def g0():
-        g = pair_gradients(q, t.charge, t.type, ii, jj, p, "short")[sample]
-        return g + bonded_gradients(q, t.bonds, t.bond_k_r0, t.angles, t.angle_k_t0)[sample]
-
-    full_rows = [np.zeros(0, np.int64)] * len(q)
-    for a, i in enumerate(sample):
-        full_rows[i] = r[a]
-    vs = v.copy()
-    vs[sample] -= (h * ACCEL / t.mass[sample])[:, None] * g0()
-    vs, _ = jump_half(q, vs, full_rows, t, p, md.Lstar, md.beta, md.dt, md.seed, md.step_index, philox.STREAM_J1,
-                      pair_bounds=md.pair_bounds)
-    q[sample] += h * vs[sample]
-    vs[sample] = o_step(vs[sample], t.mass[sample], md.T, md.gamma, md.dt, md.seed, md.step_index, atoms=sample)
-    q[sample] += h * vs[sample]
-    vs, _ = jump_half(q, vs, full_rows, t, p, md.Lstar, md.beta, md.dt, md.seed, md.step_index, philox.STREAM_J2,
-                      pair_bounds=md.pair_bounds)
-    vs[sample] -= (h * ACCEL / t.mass[sample])[:, None] * g0()
-    md.v = vs
-    md.step_index += 1
-
-
-def cpu_baseline(s, steps=3, every=8):
-    """The FP64 oracle as it stands, single-threaded numpy, on a bounded
-    sample: `steps` BOUNCE steps of every `every`-th atom; time scaled."""
-    from oracle.integrate import OracleMD
-    topo, p = _oracle_setup(s)
-    md = OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN, pair_bounds=SPLIT["pair_bounds"])
-    sample = np.arange(0, s.n_atoms, every)
+def _oracle_blocks(n_blocks):
+    """Worker: n_blocks BOUNCE-RESPA outer steps (2 steps each) of the
+    oracle on the sample; returns the wall time."""
+    md, _ = _oracle_sample()
+    md.ensure_rows()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        oracle_sample_step(md, sample)
-    dt = (time.perf_counter() - t0) * every / steps
-    return {"value": round(ns_per_day(1, dt), 8), "unit": "ns/day", "cores": 1, "kind": "oracle",
-            "sample": "%d BOUNCE steps of every %dth atom (%d atoms) of the 12288-atom droplet; time x%d" % (
-                steps, every, len(sample), every)}
+    for _ in range(n_blocks):
+        md.block_bounce_respa(2)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(blocks=1):
+    """The oracle on the sample: one core, then one independent copy per
+    host core at once (spawned processes); ns/day of the full 98,304-atom
+    workload, scaled by the atom ratio (98,304 / 12,288 = 8)."""
+    import multiprocessing as mp
+    scale = (BOX_SIDE ** 3 * 3) / (16 ** 3 * 3)
+    t1 = _oracle_blocks(blocks)
+    single = ns_per_day(2 * blocks, t1 * scale)
+    cores = os.cpu_count() or 1
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            t0 = time.perf_counter()
+            times = pool.map(_oracle_blocks, [blocks] * cores)
+            wall = time.perf_counter() - t0
+        allcore = cores * ns_per_day(2 * blocks, max(times) * scale)
+    except Exception:
+        allcore, wall = None, None
+    return {"value": round(single, 8), "unit": "ns/day", "cores": 1, "kind": "oracle",
+            "sample": "%d BOUNCE-RESPA steps of the oracle on the 4,096-molecule box of the workload's density, "
+                      "cutoffs and grid spacing (12,288 atoms, 48^3), single-threaded numpy; time x %.0f (atom "
+                      "ratio)" % (2 * blocks, scale),
+            "all_cores": {"value": None if allcore is None else round(allcore, 8), "cores": cores,
+                          "how": "one independent copy of the sample per core at once (aggregate throughput)",
+                          "wall_s": None if wall is None else round(wall, 2)}}
 
 
 def reference_arm(args):
+    """The oracle alone: each step one BOUNCE-RESPA step of the sample (the
+    4,096-molecule box, one core); ms_per_step is the measured sample step,
+    value the ns/day of the 98,304-atom workload scaled by the atom ratio."""
     ws, rank, local = _dist()
     if rank != 0:
         return
-    from paper_2002_07109_gb300.water import water_droplet
-    from oracle.integrate import OracleMD
-    s = water_droplet(N_SIDE, seed=0)
-    topo, p = _oracle_setup(s)
-    md = OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN, pair_bounds=SPLIT["pair_bounds"])
-    every = 8
-    sample = np.arange(0, s.n_atoms, every)
-    for _ in range(args.warmup):
-        oracle_sample_step(md, sample)
+    md, n_sample = _oracle_sample()
+    md.ensure_rows()
+    scale = (BOX_SIDE ** 3 * 3) / n_sample
+    for _ in range(max(1, _round_up(args.warmup, 2) // 2)):
+        md.block_bounce_respa(2)
+    steps = _round_up(args.steps, 2)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_sample_step(md, sample)
-    dt = (time.perf_counter() - t0) * every
-    val = ns_per_day(args.steps, dt)
-    sample_txt = "each step: BOUNCE on every %dth atom (%d of %d atoms); time x%d" % (every, len(sample), s.n_atoms,
-                                                                                      every)
+    for _ in range(steps // 2):
+        md.block_bounce_respa(2)
+    dt = time.perf_counter() - t0
+    val = ns_per_day(steps, dt * scale)
+    sample = ("each step: one BOUNCE-RESPA step of the oracle on the 4,096-molecule box of the workload's density, "
+              "cutoffs and grid spacing (%d atoms), single-threaded numpy; ns/day scaled by the atom ratio %.0f"
+              % (n_sample, scale))
     print(json.dumps({
-        "impl": "reference", "metric": "ns/day & pair-evals/s, BOUNCE vs BAOAB 1fs on one GB300 at matched <E>, RDF",
-        "value": round(val, 8), "unit": "ns/day", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded lattice water droplet",
-        "config": {"workload": WORKLOAD, "atoms": s.n_atoms},
-        "cpu_baseline": {"value": round(val, 8), "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": sample_txt},
+        "impl": "reference", "metric": METRIC, "value": round(val, 8), "unit": "ns/day", "n_gpus": ws,
+        "steps": steps, "warmup": _round_up(args.warmup, 2), "ms_per_step": round(dt * 1e3 / steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded lattice water box", "config": {"workload": WORKLOAD, "atoms": BOX_SIDE ** 3 * 3},
+        "cpu_baseline": {"value": round(val, 8), "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(val, 8), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def profile_case(args):
+    """A few steps of one workload for profiler captures (no timing, no
+    JSON line): box -- the 98,304-atom box, BAOAB then BOUNCE-RESPA from a
+    short BAOAB relaxation; batch -- the 256 replica droplets, BOUNCE; droplet
+    -- the 4,096-molecule droplet, BAOAB then BOUNCE (LJ on the jumps)."""
+    import torch
+    from paper_2002_07109_gb300 import bounce
+    from paper_2002_07109_gb300.water import concat_systems, replica_sizes, water_box, water_droplet, \
+        water_droplet_molecules
+    n = _round_up(max(args.steps, 2), 2)
+    if args.profile == "box":
+        s = water_box(BOX_SIDE, seed=0)
+        eq = bounce.from_system(s, seed=500, gamma=0.05, **box_cfg(0))
+        eq.set_state(s.q, s.v)
+        eq.run(48, bounce.BAOAB)
+        q, v = eq.get_state()
+        eq.close()
+        for integ, extra in ((bounce.BAOAB, {}), (bounce.BOUNCE_RESPA, dict(JUMP_ROWS, respa_m=2))):
+            ctx = bounce.from_system(s, seed=21, **box_cfg(0, **extra))
+            ctx.set_state(q, v)
+            ctx.run(n, integ)
+            torch.cuda.synchronize()
+            ctx.close()
+    elif args.profile == "batch":
+        sizes = replica_sizes(256, seed=0)
+        cat, off = concat_systems([water_droplet_molecules(int(m), seed=100 + r) for r, m in enumerate(sizes)])
+        ctx = bounce.from_system(cat, seed=1, r_on=4.0, r_off=5.0, r_cut=math.inf, jump_coulomb=False,
+                                 max_neighbors=int(np.diff(off).max()))
+        ctx.set_replicas(off, np.arange(256, dtype=np.uint64) + 7)
+        ctx.set_state(cat.q, cat.v)
+        ctx.run(n, bounce.BOUNCE)
+        torch.cuda.synchronize()
+        ctx.close()
+    else:
+        s = water_droplet(16, seed=0)
+        cfg = dict(r_on=4.0, r_off=5.0, r_cut=12.0, skin=1.0)
+        for integ, extra in ((bounce.BAOAB, {}), (bounce.BOUNCE, dict(jump_coulomb=False))):
+            ctx = bounce.from_system(s, seed=7, **cfg, **extra)
+            ctx.set_state(s.q, s.v)
+            ctx.run(n, integ)
+            torch.cuda.synchronize()
+            ctx.close()
+    print("profile case %s done" % args.profile)
 
 
 def main():
@@ -624,10 +713,14 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", choices=["box", "batch", "droplet"], default=None,
+                    help="run a few steps of one workload for a profiler capture and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile:
+        profile_case(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         our_arm(args)
