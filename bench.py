@@ -2,16 +2,19 @@
 
 Headline workload: the periodic box of 32,768 flexible 3-site water
 molecules (98,304 atoms, edge 99.3 A): Ewald direct erfc (beta 0.35 A^-1)
-and Lennard-Jones within 9 A, SPME 96^3 of order 5, jumps beyond a 7.5-8.5 A
-switch, 1 fs, friction 1/ps.  `value` is BOUNCE-RESPA (the reciprocal part on
-a 2 fs outer step, paper Sec. V) in ns/day; `baoab` is BAOAB 1 fs on the same
-GPU; BOUNCE-RESPA1 and plain BOUNCE ride along.  One "step" is one 1 fs step
+and Lennard-Jones within 9 A, SPME 96^3 of order 5, the Lennard-Jones part
+beyond a 7.5-8.5 A switch on the jumps (Coulomb wholly in F_0, the split of
+the paper's first example, Sec. IV.A), 1 fs, friction 1/ps.  `value` is
+BOUNCE-RESPA (the reciprocal part on a 2 fs outer step, paper Sec. V) in
+ns/day; `baoab` is BAOAB 1 fs on the same GPU; BOUNCE-RESPA1, plain BOUNCE
+and BOUNCE-RESPA with Coulomb on the jumps too ride along.  One "step" is one 1 fs step
 of the whole path (row and cluster rebuild checks, pair sums, SPME where the
 integrator evaluates it, the jump half-steps, B, A, O).
 
 Protocol (our arm):
   * the box is melted from the lattice with BAOAB (friction 0.05/fs, 2 ps)
-    and relaxed at 1/ps (2 ps), all on the GPU;
+    and relaxed at 1/ps (20 ps; the potential energy is flat over the last
+    8 ps), all on the GPU;
   * each arm: W warm-up steps, then the K timed steps (rounded up to whole
     outer steps) in windows of 24 steps, one run() call each, with a 256 MB
     write before each window (L2 flushed); the trajectory continues across
@@ -27,7 +30,9 @@ Protocol (our arm):
     from the relaxed box, 1.2 ps each to decorrelate, then 4.8 ps sampled every
     0.24 ps: potential energy per molecule, kinetic temperature, O-O g(r) and
     O self-diffusion; standard errors from the spread of the four runs; a
-    second BAOAB arm with other seeds is the null control;
+    second BAOAB arm with other seeds is the null control, BAOAB at 0.5 fs
+    shows the comparator's own step-size error, and BOUNCE-RESPA without
+    jumps (switch at the cutoff) separates the RESPA split from the jumps;
   * context: the 4,096-molecule droplet (r_c 12 A) with LJ on the jumps, the
     force-matching forward + backward on a 4,096-molecule box, and 256
     replica droplets of 64-1,024 molecules advanced together for 10,000 steps;
@@ -35,7 +40,8 @@ Protocol (our arm):
     workload (the same integrator on the 4,096-molecule box of the same
     density, cutoffs and grid spacing), on one core and on every core (one
     independent copy per core), scaled by the atom ratio.
---impl reference times the oracle alone (one core) on the same sample.
+--impl reference times the oracle alone (one core), each step one step of a
+512-molecule box of the same density (the run ends within minutes).
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
 """
 import argparse
@@ -61,7 +67,7 @@ DT = 1.0
 RHO_O = 0.03343    # O atoms per A^3 at 1 g/cm^3
 WORKLOAD = ("BOUNCE-RESPA (SPME on the 2 fs outer step) vs BAOAB 1 fs, 32,768-molecule periodic flexible-water box "
             "(98,304 atoms, edge 99.3 A), Ewald erfc beta 0.35 + LJ within 9 A, SPME 96^3 order 5, "
-            "jumps beyond a 7.5-8.5 A switch, 1 fs, friction 1/ps")
+            "LJ beyond a 7.5-8.5 A switch on the jumps (Coulomb in F_0), 1 fs, friction 1/ps")
 # Algorithmic lane-operations of one pair inside the cutoff in the cluster
 # pair kernel, counted from the source: displacement 9, r^2 3, 1/r with a
 # Newton step 5, r and 1/r^2 2, Ewald erfc term (A&S 7.1.26 and its
@@ -185,21 +191,26 @@ def box_cfg(device, **kw):
 # their skin; a wider skin makes them rarer (and longer) while the cluster
 # lists of the pair sums keep a 1 A skin.  BAOAB reads no rows.
 JUMP_ROWS = dict(skin=2.5, pair_skin=1.0, max_neighbors=2048)
+# The headline split: LJ beyond the switch on the jumps, Coulomb in F_0
+# (reading of the paper's first example).  With Coulomb on the jumps too the
+# reflections heat flexible water at 1 fs (measured in matched_observables).
+LJ_JUMPS = dict(JUMP_ROWS, jump_coulomb=False)
 # (name, integrator name, extra config, outer period in steps)
-BOX_ARMS = (("bounce_respa", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2),
+BOX_ARMS = (("bounce_respa", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2), 2),
             ("baoab", "BAOAB", {}, 1),
-            ("bounce_respa1", "BOUNCE_RESPA1", dict(JUMP_ROWS, respa_m=2, respa_m2=3), 6),
-            ("bounce", "BOUNCE", dict(JUMP_ROWS), 1))
+            ("bounce_respa1", "BOUNCE_RESPA1", dict(LJ_JUMPS, respa_m=2, respa_m2=3), 6),
+            ("bounce", "BOUNCE", dict(LJ_JUMPS), 1),
+            ("bounce_respa_coulomb_jumps", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2))
 
 
-EQ_STRONG, EQ_STEPS, EQ_EVERY = 2000, 8000, 1000
+EQ_STRONG, EQ_STEPS, EQ_EVERY = 2000, 20000, 2000
 
 
 def equilibrate_box(bounce, s, device, sh, seed):
     """Lattice -> liquid: BAOAB at friction 0.05/fs for 2 ps, then at the
-    workload's 1/ps for 8 ps; returns the state and the trace of the
-    temperature and the potential energy per molecule every ps of the second
-    part (flat over its last half when the box is relaxed)."""
+    workload's 1/ps for 20 ps; returns the state and the trace of the
+    temperature and the potential energy per molecule every 2 ps of the
+    second part (flat over its last 8 ps when the box is relaxed)."""
     eq = bounce.from_system(s, seed=seed, gamma=0.05, **box_cfg(device))
     eq.set_state(s.q, s.v)
     eq.run(EQ_STRONG, bounce.BAOAB, stream=sh)
@@ -368,7 +379,7 @@ def our_arm(args):
     line["matched_observables"] = matched_observables(bounce, s, q0, v0, local, stream, sh, rank)
     line["matched_observables"]["equilibration"] = {
         "protocol": "BAOAB %d steps at friction 0.05/fs, then %d steps at 1/ps" % (EQ_STRONG, EQ_STEPS),
-        "T_K_and_Epot_per_molecule_every_ps": eq_trace}
+        "T_K_and_Epot_per_molecule_every_2ps": eq_trace}
     line["droplet_context"] = droplet_context(bounce, local, stream, sh, rank, args)
     line["force_matching"] = force_matching(bounce, local, rank)
     line["batched_replicas"] = batched_replicas(bounce, local, stream, sh, rank)
@@ -402,29 +413,35 @@ def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=4, dec
     L = float(s.box[0])
     edges = np.arange(81) * 0.1
     shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    # (name, integrator, extra config, outer period, seed base); dt from the config
     arms = (("baoab", "BAOAB", {}, 1, 100),
             ("baoab_control", "BAOAB", {}, 1, 200),
-            ("bounce_respa", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2, 100),
-            ("bounce_respa1", "BOUNCE_RESPA1", dict(JUMP_ROWS, respa_m=2, respa_m2=3), 6, 100))
+            ("baoab_half_fs", "BAOAB", dict(dt=0.5), 1, 300),
+            ("bounce_respa", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2), 2, 100),
+            ("bounce_respa1", "BOUNCE_RESPA1", dict(LJ_JUMPS, respa_m=2, respa_m2=3), 6, 100),
+            ("bounce_respa_no_jumps", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2, r_on=R_CUT, r_off=R_CUT), 2, 100),
+            ("bounce_respa_coulomb_jumps", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2, 100))
     raw = {}
     out = {"protocol": "%d runs per arm from the relaxed box, %d steps to decorrelate, then %d steps sampled every %d; "
                        "standard errors from the spread of the runs" % (runs, decor, prod, every)}
     for name, integ_name, extra, period, seed0 in arms:
         integ = getattr(bounce, integ_name)
+        dt = extra.get("dt", DT)
+        k_dt = int(round(DT / dt))      # steps per DT of simulated time
         per_run = {"pe": [], "T": [], "D": [], "g": []}
         ms, err = 0.0, None
         for r in range(runs):
             ctx = bounce.from_system(s, seed=seed0 + 17 * r + 1000 * rank, **box_cfg(device, **extra))
             try:
                 ctx.set_state(q0, v0, step=0)
-                ctx.run(decor, integ, stream=sh)
+                ctx.run(decor * k_dt, integ, stream=sh)
                 ctx.set_msd_reference(stream=sh)
                 pe, T, hist, msd = [], [], np.zeros(80), {}
                 for k in range(prod // every):
                     a = torch.cuda.Event(enable_timing=True)
                     b = torch.cuda.Event(enable_timing=True)
                     a.record(stream)
-                    ctx.run(every, integ, stream=sh)
+                    ctx.run(every * k_dt, integ, stream=sh)
                     b.record(stream)
                     b.synchronize()
                     ms += a.elapsed_time(b)
@@ -449,7 +466,7 @@ def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=4, dec
         if err:
             res["stopped"] = err
         if per_run["pe"]:
-            res["ns_per_day"] = round(ns_per_day(len(per_run["pe"]) * prod, ms / 1e3), 2)
+            res["ns_per_day"] = round(ns_per_day(len(per_run["pe"]) * prod, ms / 1e3), 2)   # simulated time
         if len(per_run["pe"]) >= 2:
             for k, unit in (("pe", "kcal/mol per molecule"), ("T", "K"), ("D", "A^2/ps")):
                 m, se = _mean_se(per_run[k])
@@ -473,6 +490,18 @@ def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=4, dec
                 z["matched"] = bool(max(z["pe"], z["T"], z["D"]) < 2.0 and z["g_oo_chi2_per_bin"] < 2.0)
                 res["z_vs_baoab"] = z
         out[name] = res
+    # each arm's offset from BAOAB at 0.5 fs (the comparator's own step-size
+    # error is BAOAB 1 fs's offset)
+    half = raw.get("baoab_half_fs")
+    if half and len(half["pe"]) >= 2:
+        for name in out:
+            if isinstance(out[name], dict) and name != "baoab_half_fs" and len(raw.get(name, {}).get("pe", [])) >= 2:
+                d = {}
+                for k in ("pe", "T"):
+                    m1, e1 = _mean_se(raw[name][k])
+                    m2, e2 = _mean_se(half[k])
+                    d[k] = {"diff": round(float(m1 - m2), 5), "se": round(float(math.hypot(e1, e2)), 5)}
+                out[name]["vs_baoab_half_fs"] = d
     return out
 
 
@@ -580,17 +609,18 @@ def force_matching(bounce, device, rank, reps=5):
             round(float(np.median(ms)), 3)}
 
 
-def _oracle_sample():
-    """The bounded sample of the workload: the 4,096-molecule box of the same
-    density (edge 49.7 A), the same cutoffs, switch and Ewald beta, an SPME
-    grid of the same spacing (48^3), BOUNCE-RESPA."""
+def _oracle_sample(side=16):
+    """A bounded sample of the workload: a box of side^3 molecules at the
+    same density (side 16: 4,096 molecules, edge 49.7 A), the same cutoffs,
+    switch and Ewald beta, an SPME grid of the same spacing (3 side), the
+    BOUNCE-RESPA split of the workload."""
     from oracle.forcefield import Params
     from oracle.integrate import OracleMD, Topology
     from paper_2002_07109_gb300.water import water_box
-    s = water_box(16, seed=0)
+    s = water_box(side, seed=0)
     topo = Topology(s.type, s.mass, s.charge, s.molecule, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0)
     p = Params(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, ewald_beta=BETA, box=s.box, lj_sigma=s.lj_sigma,
-               lj_eps=s.lj_eps, pme_grid=(48, 48, 48), pme_order=ORDER)
+               lj_eps=s.lj_eps, pme_grid=(3 * side,) * 3, pme_order=ORDER)
     return OracleMD(s.q, s.v, topo, p, seed=7, skin=SKIN), s.n_atoms
 
 
@@ -631,14 +661,20 @@ def cpu_baseline(blocks=1):
                           "wall_s": None if wall is None else round(wall, 2)}}
 
 
+REF_SIDE = 8   # the reference arm's sample: 512 molecules (1,536 atoms), ~0.5 s per oracle step
+
+
 def reference_arm(args):
     """The oracle alone: each step one BOUNCE-RESPA step of the sample (the
-    4,096-molecule box, one core); ms_per_step is the measured sample step,
-    value the ns/day of the 98,304-atom workload scaled by the atom ratio."""
+    512-molecule box of the workload's density, edge 24.8 A, one core), so
+    that the default run ends within a few minutes; ms_per_step is the
+    measured sample step, value the ns/day of the 98,304-atom workload scaled
+    by the atom ratio (the oracle's step is linear in the atoms: cell lists
+    and an SPME grid of fixed spacing)."""
     ws, rank, local = _dist()
     if rank != 0:
         return
-    md, n_sample = _oracle_sample()
+    md, n_sample = _oracle_sample(REF_SIDE)
     md.ensure_rows()
     scale = (BOX_SIDE ** 3 * 3) / n_sample
     for _ in range(max(1, _round_up(args.warmup, 2) // 2)):
@@ -649,9 +685,9 @@ def reference_arm(args):
         md.block_bounce_respa(2)
     dt = time.perf_counter() - t0
     val = ns_per_day(steps, dt * scale)
-    sample = ("each step: one BOUNCE-RESPA step of the oracle on the 4,096-molecule box of the workload's density, "
+    sample = ("each step: one BOUNCE-RESPA step of the oracle on the %d-molecule box of the workload's density, "
               "cutoffs and grid spacing (%d atoms), single-threaded numpy; ns/day scaled by the atom ratio %.0f"
-              % (n_sample, scale))
+              % (n_sample // 3, n_sample, scale))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(val, 8), "unit": "ns/day", "n_gpus": ws,
         "steps": steps, "warmup": _round_up(args.warmup, 2), "ms_per_step": round(dt * 1e3 / steps, 3),
@@ -679,7 +715,7 @@ def profile_case(args):
         eq.run(48, bounce.BAOAB)
         q, v = eq.get_state()
         eq.close()
-        for integ, extra in ((bounce.BAOAB, {}), (bounce.BOUNCE_RESPA, dict(JUMP_ROWS, respa_m=2))):
+        for integ, extra in ((bounce.BAOAB, {}), (bounce.BOUNCE_RESPA, dict(LJ_JUMPS, respa_m=2))):
             ctx = bounce.from_system(s, seed=21, **box_cfg(0, **extra))
             ctx.set_state(q, v)
             ctx.run(n, integ)

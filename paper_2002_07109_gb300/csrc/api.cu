@@ -82,6 +82,8 @@ struct bounce_ctx {
     // after BAOAB runs on clusters the step kernel did not test the rows:
     // the next row consumer tests the displacement first
     bool rows_check_due = false;
+    bool rows_partial = false;    // a run left the rows of atoms with L* = 0 empty (ROWS_ACTIVE)
+    int* d_act_order = nullptr;   // device copy of DevSys::act_order
     // tuning (bounce_autotune): cluster column edge factor, tile j-block and grid
     double cl_edge_factor = 1.0;
     bool cl_force = false;        // the next setup_clusters recomputes the grid
@@ -152,6 +154,8 @@ void free_all(bounce_ctx* c) {
     c->diff_part = nullptr;
     c->tile_items = nullptr;
     c->tile_cap = 0;
+    c->d_act_order = nullptr;
+    c->rows_partial = false;
     reset_cluster_caps(c);
 }
 
@@ -686,13 +690,36 @@ int flag_clusters(bounce_ctx* c, cudaStream_t st) {
 // flag unless forced).  After BAOAB runs on clusters the step kernel did not
 // test the rows' displacement, so it is tested here first, at the current
 // positions (the test the oracle applies before every use of the rows).
-void rebuild(bounce_ctx* c, int step_off, bool force, cudaStream_t st) {
+void rebuild(bounce_ctx* c, int step_off, bool force, cudaStream_t st, int mode = ROWS_ALL) {
     if (c->rows_check_due) {
         long long step = c->cur_step;
         if (step_off == 0) launch_flag_moved(c->ds, c->pp, (int)(step & 1), st);
         c->rows_check_due = false;
     }
-    launch_rebuild(c->ds, c->pp, step_off, force, c->bitmap_warps, c->bitmap_bytes, st);
+    launch_rebuild(c->ds, c->pp, step_off, force, c->bitmap_warps, c->bitmap_bytes, mode, st);
+}
+
+// Row-build mode of the runs of `integ`: the jump step is the rows' only
+// reader when the pair sums run over clusters or tiles (and no short rows
+// exist), so atoms of a type with L* = 0 need none.
+int rows_mode(const bounce_ctx* c, int integ) {
+    if (integ == BOUNCE_BAOAB || c->ds.rep_of || !(c->ds.cl.on || c->ds.tl.on) || c->pp.rshort2 < INFINITY ||
+        !c->ds.act_order)
+        return ROWS_ALL;
+    for (int a = 0; a < c->pp.n_types; ++a)
+        if (c->Lstar[a] == 0.0) return ROWS_ACTIVE;
+    return ROWS_ALL;
+}
+
+// Entry points that read every row (energies, histograms, gradients over
+// the rows, the rows themselves) first build the rows a run left empty, at
+// the current positions; the displacement test of the rows keeps the
+// reference positions of the last full build, so the next run's rebuilds
+// come at the same steps as without this call.
+void complete_rows(bounce_ctx* c, cudaStream_t st) {
+    if (!c->rows_partial) return;
+    launch_rebuild(c->ds, c->pp, 0, true, c->bitmap_warps, c->bitmap_bytes, ROWS_IDLE, st);
+    c->rows_partial = false;
 }
 
 int check_err(bounce_ctx* c, cudaStream_t st) {
@@ -781,7 +808,16 @@ double expected_proposals(const bounce_ctx* c, double rho) {
 // every integrator without clusters, whose pair sums run over the rows).
 void rebuild_for(bounce_ctx* c, int integ, int off, cudaStream_t st) {
     if (c->ds.cl.on) launch_cluster_rebuild(c->ds, c->pp, off, false, st);
-    if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st);
+    if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st, rows_mode(c, integ));
+}
+
+// Before a run: rows a previous run left partial are completed when this
+// run builds full rows; after it, they are partial if it built active ones.
+void rows_before_run(bounce_ctx* c, int integ, cudaStream_t st) {
+    if (rows_mode(c, integ) == ROWS_ALL) complete_rows(c, st);
+}
+void rows_after_run(bounce_ctx* c, int integ) {
+    if (rows_mode(c, integ) == ROWS_ACTIVE) c->rows_partial = true;
 }
 
 void boundary(bounce_ctx* c, int integ, int variant, int off, long long step, cudaStream_t st) {
@@ -1043,6 +1079,23 @@ int bounce_set_lj(bounce_ctx* c, int32_t T, const double* sigma, const double* e
     compute_bounds(c, sg, ep);
     fill_params(c, sg, ep);
     drop_graphs(c);
+    {
+        // atoms that can propose (L* > 0) first, for the row builder
+        std::vector<int> order;
+        order.reserve(c->n);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i < c->n; ++i)
+                if ((c->Lstar[c->type[i]] > 0.0) == (pass == 0)) order.push_back(i);
+        int nact = 0;
+        for (int i = 0; i < c->n; ++i) nact += c->Lstar[c->type[i]] > 0.0 ? 1 : 0;
+        if (!c->d_act_order) {
+            int r = dalloc(c, &c->d_act_order, c->n);
+            if (r) return r;
+        }
+        CU(cudaMemcpy(c->d_act_order, order.data(), c->n * sizeof(int), cudaMemcpyHostToDevice));
+        c->ds.act_order = c->d_act_order;
+        c->ds.n_act = nact;
+    }
     if (!c->has_pme) {
         int r = setup_pme(c);
         if (r) return r;
@@ -1171,6 +1224,7 @@ int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const int m = respa_period(c, integ);
     long long s0 = c->cur_step;
+    rows_before_run(c, integ, st);
     // head: B/2 [J] A O A at the current step
     boundary(c, integ, 0, 0, s0, st);
     launch_advance_step(c->ds, 1, st);
@@ -1189,6 +1243,7 @@ int bounce_run(bounce_ctx* c, int64_t n_steps, int32_t integ, void* stream) {
     boundary(c, integ, 2, 0, s0 + n_steps, st);
     c->cur_step = s0 + n_steps;
     if (integ == BOUNCE_BAOAB && c->ds.cl.on) c->rows_check_due = true;
+    rows_after_run(c, integ);
     CU(cudaGetLastError());
     return check_err(c, st);
 }
@@ -1204,6 +1259,7 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
     std::vector<cudaEvent_t> ev(2 * (size_t)(n_steps + 1));
     for (auto& e : ev) CU(cudaEventCreate(&e));
     const long long s0 = c->cur_step;
+    rows_before_run(c, integ, st);
     auto timed = [&](int k, int variant, int off, long long step) {
         bool pme;
         double hr, hout;
@@ -1221,6 +1277,7 @@ int bounce_profile_steps(bounce_ctx* c, int64_t n_steps, int32_t integ, void* st
     timed((int)n_steps, 2, 0, s0 + n_steps);
     c->cur_step = s0 + n_steps;
     if (integ == BOUNCE_BAOAB && c->ds.cl.on) c->rows_check_due = true;
+    rows_after_run(c, integ);
     CU(cudaStreamSynchronize(st));
     double tot = 0.0;
     for (int64_t k = 0; k <= n_steps; ++k) {
@@ -1254,6 +1311,7 @@ int bounce_profile_breakdown(bounce_ctx* c, int64_t n_steps, int32_t integ, void
         return true;
     };
     const long long s0 = c->cur_step;
+    rows_before_run(c, integ, st);
     bool ok = true;
     auto one = [&](int variant, int off, long long step) {
         bool pme;
@@ -1263,7 +1321,7 @@ int bounce_profile_breakdown(bounce_ctx* c, int64_t n_steps, int32_t integ, void
         ok = ok && mark(-1);
         if (c->ds.cl.on) launch_cluster_rebuild(c->ds, c->pp, off, false, st);
         ok = ok && mark(3);
-        if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st);
+        if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st, rows_mode(c, integ));
         ok = ok && mark(2);
         if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
         ok = ok && mark(4);
@@ -1279,6 +1337,7 @@ int bounce_profile_breakdown(bounce_ctx* c, int64_t n_steps, int32_t integ, void
     one(2, 0, s0 + n_steps);
     c->cur_step = s0 + n_steps;
     if (integ == BOUNCE_BAOAB && c->ds.cl.on) c->rows_check_due = true;
+    rows_after_run(c, integ);
     CU(cudaStreamSynchronize(st));
     for (int k = 0; k < NK; ++k) {
         ms[k] = 0.0;
@@ -1412,6 +1471,7 @@ int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     rebuild(c, 0, false, st);
+    complete_rows(c, st);
     launch_energies(c->ds, c->pp, (int)(step & 1), c->terms, st);
     double tot[5], pe[2] = {0.0, 0.0};
     if (c->has_pme) {
@@ -1460,6 +1520,7 @@ int bounce_pair_histogram(bounce_ctx* c, int32_t ta, int32_t tb, double r_max, i
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     rebuild(c, 0, false, st);
+    complete_rows(c, st);
     CU(cudaMemsetAsync(c->hist, 0, n_bins * sizeof(unsigned long long), st));
     launch_pair_hist(c->ds, c->pp, (int)(step & 1), ta, tb, r_max, n_bins, c->hist, st);
     CU(cudaMemcpyAsync(hist, c->hist, n_bins * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -1535,6 +1596,7 @@ int bounce_compute_gradient(bounce_ctx* c, int32_t part, double* grad, int32_t w
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     rebuild(c, 0, false, st);
+    complete_rows(c, st);
     const cudaMemcpyKind kind = where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (part == BOUNCE_GRAD_RECIP) {
         if (!c->has_pme) return fail(c, BOUNCE_ERR_STATE, "no SPME grid configured");
@@ -1598,6 +1660,7 @@ int bounce_get_rows(bounce_ctx* c, int32_t* counts, int32_t* rows, int32_t capac
     if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
     cudaSetDevice(c->cfg.device);
     rebuild(c, 0, false, nullptr);
+    complete_rows(c, nullptr);
     CU(cudaDeviceSynchronize());
     int r = check_err(c, nullptr);
     if (r) return r;
@@ -1699,8 +1762,10 @@ int bounce_pair_forward(bounce_ctx* c, const double* q, int32_t T, const double*
         launch_pack_positions(c->ds, c->pp, cur, st);
         if ((r = flag_clusters(c, st))) return r;
         rebuild(c, 0, true, st);
+        complete_rows(c, st);
     } else {
         rebuild(c, 0, false, st);
+        complete_rows(c, st);
     }
     double* eatom = c->terms;
     double* esum = c->terms + 6 * (size_t)n + 1024;

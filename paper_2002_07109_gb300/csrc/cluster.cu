@@ -440,6 +440,35 @@ __device__ __forceinline__ void shift_split(float& h, float& l, float sh, float 
     l = (l - sl) + err;
 }
 
+// The pairs of one list entry (atom slot sj, split position hj/lj in the
+// image of the entry) whose FP32 r^2 fell within the rounding band of r_c^2
+// (bits of `near`): each takes the exact FP64 cutoff test; a pair inside
+// adds its i side straight to the accumulator of its slot (rare) and its j
+// side to the lane's sums.
+template <int PART>
+__device__ __forceinline__ void near_pairs(const DevSys& s, const Params& p, int cur, int I, int sj, float4 hj, float4 lj,
+                                        uint32_t near, const float4* s_hi, const float4* s_lo, const float* s_c12,
+                                        const float* s_c6, float& gjx, float& gjy, float& gjz, int& npair) {
+    const DevClu& c = s.cl;
+    const size_t ns = (size_t)c.ncol * c.maxcl * CL;
+    for (; near; near &= near - 1u) {
+        const int a = __ffs(near) - 1;
+        if (!(exact_r2(s, p, cur, c.cl_atom[I * CL + a], c.cl_atom[sj]) < p.rc2_d)) continue;
+        const float4 hi = s_hi[a], lo = s_lo[a];
+        const float3 d = pair_disp(p, hi, lo, hj, lj);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        const int tp = type_of(lo) * BOUNCE_MAXT + type_of(lj);
+        const float w = pairsum_w<PART>(p, r2, p.kcoul * hi.w * hj.w, s_c12[tp], s_c6[tp]);
+        fix_add(c.acc + (size_t)I * CL + a, w * d.x);
+        fix_add(c.acc + ns + (size_t)I * CL + a, w * d.y);
+        fix_add(c.acc + 2 * ns + (size_t)I * CL + a, w * d.z);
+        gjx = fmaf(-w, d.x, gjx);
+        gjy = fmaf(-w, d.y, gjy);
+        gjz = fmaf(-w, d.z, gjz);
+        ++npair;
+    }
+}
+
 // Pair sums over the work items of list `L`.  PART 3: the F_0 share
 // (1 - chi) W'_sw + W'_fixed; PART 5: the full W'.  A warp takes an item of
 // cluster I: lanes hold one list atom j each, the 8 atoms of I are read from
@@ -451,6 +480,12 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
     chain_enter();
     __shared__ float4 s_hi[8][CL], s_lo[8][CL];
     __shared__ int s_mol[8][CL];
+    __shared__ float s_c12[BOUNCE_MAXT * BOUNCE_MAXT], s_c6[BOUNCE_MAXT * BOUNCE_MAXT];
+    if (threadIdx.x < BOUNCE_MAXT * BOUNCE_MAXT) {
+        s_c12[threadIdx.x] = p.c12[threadIdx.x];
+        s_c6[threadIdx.x] = p.c6[threadIdx.x];
+    }
+    __syncthreads();
     const DevClu& c = s.cl;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int cur = (int)((*s.step_base + step_off) & 1);
@@ -487,6 +522,7 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
                 shift_split(hj.z, lj.z, kz * p.Lhi[2], kz * p.Llo[2]);
             }
             float gjx = 0.f, gjy = 0.f, gjz = 0.f;
+            uint32_t near = 0u;  // pairs within the FP32 rounding band of r_c
 #pragma unroll
             for (int a = 0; a < CL; ++a) {
                 const float4 hi = s_hi[wl][a], lo = s_lo[wl][a];
@@ -501,11 +537,10 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
                 }
                 const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
                 const bool ok = mi >= 0 && mi != mj && sj > I * CL + a;
-                bool in = ok && r2 < p.rc2_lo;
-                if (ok && r2 >= p.rc2_lo && r2 <= p.rc2_hi)  // near r_c: exact FP64 test (rare)
-                    in = cl_exact_inside(s, p, cur, c.cl_atom[I * CL + a], c.cl_atom[sj]);
+                const bool in = ok && r2 < p.rc2_lo;
+                near |= (ok && r2 >= p.rc2_lo && r2 <= p.rc2_hi) ? 1u << a : 0u;
                 const int tp = type_of(lo) * BOUNCE_MAXT + tj;
-                const float w0 = pairsum_w<PART>(p, in ? r2 : 1.f, p.kcoul * hi.w * hj.w, p.c12[tp], p.c6[tp]);
+                const float w0 = pairsum_w<PART>(p, in ? r2 : 1.f, p.kcoul * hi.w * hj.w, s_c12[tp], s_c6[tp]);
                 const float wv = in ? w0 : 0.f;
                 npair += in ? 1 : 0;
                 gi[a][0] = fmaf(wv, d.x, gi[a][0]);
@@ -515,6 +550,8 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
                 gjy = fmaf(-wv, d.y, gjy);
                 gjz = fmaf(-wv, d.z, gjz);
             }
+            if (near) near_pairs<PART>(s, p, cur, I, sj, hj, lj, near, s_hi[wl], s_lo[wl], s_c12, s_c6, gjx, gjy, gjz,
+                                       npair);
             fix_add(c.acc + sj, gjx);
             fix_add(c.acc + ns + sj, gjy);
             fix_add(c.acc + 2 * ns + sj, gjz);

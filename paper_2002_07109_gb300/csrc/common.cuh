@@ -151,6 +151,8 @@ struct DevSys {
     const int* rep_off;      // [replicas + 1] first atom of each replica
     DevClu cl;               // cluster-pair structure (cl.on = 0: pair sums over the rows)
     DevTile tl;              // all-pairs tiles (systems without a cutoff)
+    const int* act_order;    // [n] atoms whose type has L* > 0 (ascending), then the others
+    int n_act;               // atoms that can propose
     int rows_flag;           // the step kernel raises `rebuild` for the rows (0 in BAOAB runs on clusters)
     int lite;                // thread-per-atom step kernel (rare jump proposals)
 };
@@ -413,7 +415,7 @@ __device__ __forceinline__ float chi_of(const Params& p, float r) {
 // use it (with the exp(-x^2) they need for the derivative anyway); the jump
 // step keeps the library erfcf.
 __device__ __forceinline__ float erfc_scaled_as(float x) {
-    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.f));
+    const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
     return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
                     0.254829592f);
 }
@@ -575,9 +577,12 @@ inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// Row-build modes of launch_rebuild (see k_rows_warp).
+constexpr int ROWS_ALL = 0, ROWS_ACTIVE = 1, ROWS_IDLE = 2;
+
 // Launchers implemented in the .cu files.
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int window_words, size_t bitmap_bytes,
-                    cudaStream_t st);
+                    int mode, cudaStream_t st);
 void launch_step(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
                  double hout, cudaStream_t st);
 // launch_step in two parts (for per-kernel timing): the pair sums, then the step kernel.

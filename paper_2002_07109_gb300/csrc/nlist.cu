@@ -354,7 +354,13 @@ __device__ __forceinline__ bool row_member(const DevSys& s, const Params& p, int
 // take further passes over windows below, then above it, each screening the
 // candidates again; systems numbered in spatial order need one pass, and a
 // window that spans every atom always does.
-__global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww) {
+// mode: ROWS_ALL builds every row; ROWS_ACTIVE leaves the rows of atoms
+// whose type has L* = 0 empty (they never propose: valid while the pair sums
+// run over clusters or tiles and no short rows exist); ROWS_IDLE builds only
+// those rows, at the current positions, keeping the reference positions and
+// the rebuild flag of the last build (completing ROWS_ACTIVE rows for the
+// energy, histogram and gradient entry points, which read every row).
+__global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww, int mode) {
     if (!pending(s, force)) return;
     extern __shared__ uint32_t smem_bm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -369,11 +375,33 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww)
     int* rl = rb + RANGE_MAX;
     int* rp = rl + RANGE_MAX;
     const int cur = (int)((*s.step_base + step_off) & 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && mode != ROWS_IDLE) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
     // the bitmaps start clear; after each atom only the words it touched are cleared
     for (int w = lane; w < nb * ww; w += 32) bm[w] = 0u;
     __syncwarp();
-    for (int i = blockIdx.x * wpb + warp; i < s.n; i += gridDim.x * wpb) {
+    // When the pair sums run over clusters or tiles, the rows serve only the
+    // jump step, and an atom whose type has the bound L* = 0 never proposes
+    // (its Poisson mean is 0).  act_order lists the atoms that can propose,
+    // then the others: ROWS_ACTIVE builds the rows of the first n_act (the
+    // others get empty rows and their reference positions), ROWS_IDLE the
+    // rows of the rest; the warps stride over the listed atoms only, so the
+    // work stays balanced whatever the order of the atom types.
+    const bool split = mode != ROWS_ALL && (s.cl.on || s.tl.on) && !has_short && s.act_order != nullptr;
+    const int t0 = split && mode == ROWS_IDLE ? s.n_act : 0;
+    const int t1 = split && mode == ROWS_ACTIVE ? s.n_act : s.n;
+    if (split && mode == ROWS_ACTIVE)
+        for (int t = s.n_act + blockIdx.x * blockDim.x + threadIdx.x; t < s.n; t += gridDim.x * blockDim.x) {
+            const int i = s.act_order[t];
+            if (p.typed)
+                for (int u = 0; u < nbm; ++u) s.nseg[(size_t)i * BOUNCE_MAXT + u] = 0;
+            s.nlong[i] = 0;
+            s.nshort[i] = 0;
+            s.refx[i] = s.qx[cur][i];
+            s.refy[i] = s.qy[cur][i];
+            s.refz[i] = s.qz[cur][i];
+        }
+    for (int t = t0 + blockIdx.x * wpb + warp; t < t1; t += gridDim.x * wpb) {
+        const int i = split ? s.act_order[t] : t;
         const float4 hi = s.phi[cur][i];
         const int mi = s.mol[i];
         int nr_tot;
@@ -502,13 +530,15 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww)
             if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
             s.nshort[i] = min(ns, s.caps);
             if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
-            s.refx[i] = s.qx[cur][i];
-            s.refy[i] = s.qy[cur][i];
-            s.refz[i] = s.qz[cur][i];
+            if (mode != ROWS_IDLE) {
+                s.refx[i] = s.qx[cur][i];
+                s.refy[i] = s.qy[cur][i];
+                s.refz[i] = s.qz[cur][i];
+            }
         }
         __syncwarp();
     }
-    if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
+    if (last_cta(&s.done_ctr[1]) && mode != ROWS_IDLE) *s.rebuild = 0;
 }
 
 // Rows of a batch of independent all-pairs replicas: every atom of the same
@@ -586,7 +616,7 @@ void launch_flag_moved(const DevSys& s, const Params& p, int cur, cudaStream_t s
 }
 
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int window_words, size_t bitmap_bytes,
-                    cudaStream_t st) {
+                    int mode, cudaStream_t st) {
     const int f = force ? 1 : 0;
     if (s.rep_of) {
         const int wpb = 8;
@@ -600,7 +630,7 @@ void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, 
     // warp per atom, 8 warps per CTA, a grid-stride loop over one wave of CTAs
     const int per_sm = std::max(1, std::min(8, (int)((227u << 10) / std::max<size_t>(bitmap_bytes, 1))));
     const int blocks = std::min((s.n + 7) / 8, 152 * per_sm);
-    launch_chained(k_rows_warp, blocks, 256, bitmap_bytes, st, s, p, step_off, f, window_words);
+    launch_chained(k_rows_warp, blocks, 256, bitmap_bytes, st, s, p, step_off, f, window_words, mode);
 }
 
 void nlist_set_smem_limit(size_t bytes) {

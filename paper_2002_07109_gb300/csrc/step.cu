@@ -793,8 +793,9 @@ __device__ __forceinline__ void jump_thread(const DevSys& s, const Params& p, in
                                             float4 alo, float& dvx, float& dvy, float& dvz, int& nprop, int& nacc,
                                             int& near) {
     dvx = dvy = dvz = 0.f;
-    const double sp = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
     const double Ls = p.Lstar_d[ti];
+    if (Ls == 0.0) return;  // no jump part for this type: Poisson mean 0 (skips the FP64 set-up)
+    const double sp = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
     double n;
     uint32_t acum[BOUNCE_MAXT + 1];
     int ast[BOUNCE_MAXT];

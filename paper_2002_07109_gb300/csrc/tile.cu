@@ -43,6 +43,12 @@ __global__ void __launch_bounds__(256) k_tile_pairs(DevSys s, Params p, int step
     chain_enter();
     __shared__ float4 sh_h[8][32], sh_l[8][32];
     __shared__ int sh_m[8][32];
+    __shared__ float s_c12[BOUNCE_MAXT * BOUNCE_MAXT], s_c6[BOUNCE_MAXT * BOUNCE_MAXT];
+    if (threadIdx.x < BOUNCE_MAXT * BOUNCE_MAXT) {  // LJ table: per-lane type pairs read from shared memory
+        s_c12[threadIdx.x] = p.c12[threadIdx.x];
+        s_c6[threadIdx.x] = p.c6[threadIdx.x];
+    }
+    __syncthreads();
     const DevTile& t = s.tl;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int cur = (int)((*s.step_base + step_off) & 1);
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(256) k_tile_pairs(DevSys s, Params p, int step
                 const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
                 const bool in = mj >= 0 && mi >= 0 && mi != mj && j0 + m > i;
                 const int tp = ti + type_of(lj);
-                const float w0 = pairsum_w<PART>(p, in ? r2 : 1.f, qi * hj.w, p.c12[tp], p.c6[tp]);
+                const float w0 = pairsum_w<PART>(p, in ? r2 : 1.f, qi * hj.w, s_c12[tp], s_c6[tp]);
                 const float wv = in ? w0 : 0.f;
                 npair += in ? 1 : 0;
                 gix = fmaf(wv, d.x, gix);

@@ -553,3 +553,62 @@ def test_rows_windowed_random_order(typed):
     for a, i in enumerate(sample):
         assert np.array_equal(got[i], ref[a]), i
     ctx.close()
+
+
+@pytest.mark.parametrize("coulomb_jumps", [False, True])
+def test_full_size_box_first_step_sampled(coulomb_jumps):
+    """The 98,304-atom box in the split and launch configuration the
+    benchmark times (Ewald erfc beta 0.35 and LJ within 9 A, SPME 96^3 of
+    order 5, jumps beyond a 7.5-8.5 A switch with one bound per atom type,
+    row skin 2.5 A, cluster skin 1 A, thread-per-atom step kernel): one BOUNCE
+    step through run().  The positions after it depend only on the starting
+    state (B with F_0 and the reciprocal gradient, the first jump half-step,
+    A O A), so the oracle's first half-step is computed for 3,000 sampled
+    atoms from their own rows and pairs and compared atom by atom, relative
+    to the distance travelled; near-tie atoms are left out."""
+    from oracle import ewald
+    from oracle.bounds import bound_table
+    from oracle.forcefield import ACCEL, KB, bonded_gradients, pair_gradients
+    from oracle.integrate import o_step
+    from oracle.neighbors import to_pairs
+    s = water_box(32, seed=0)
+    rng = np.random.default_rng(8)
+    q0 = s.q + rng.normal(scale=0.05, size=s.q.shape)
+    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=2.5, pair_skin=1.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
+               pme_order=5, max_neighbors=2048, jump_coulomb=coulomb_jumps)
+    ctx = bounce.from_system(s, seed=13, **cfg)
+    ctx.set_state(q0, s.v, step=0)
+    ctx.run(1, bounce.BOUNCE)
+    q1, _ = ctx.get_state()
+    ctx.close()
+    p = Params(r_on=7.5, r_off=8.5, r_cut=9.0, ewald_beta=0.35, box=s.box, lj_sigma=s.lj_sigma, lj_eps=s.lj_eps,
+               pme_grid=(96, 96, 96), pme_order=5, coulomb_jumps=coulomb_jumps)
+    topo = Topology(s.type, s.mass, s.charge, s.molecule, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0)
+    sample = np.sort(rng.choice(s.n_atoms, 3000, replace=False))
+    rows_s = oracle_rows(q0, s.molecule, 11.5, s.box, atoms=sample)
+    row_list = [np.zeros(0, np.int64)] * s.n_atoms
+    for a, i in enumerate(sample):
+        row_list[i] = rows_s[a]
+    # B: F_0 (bonded + the (1 - chi) share of the pairs) and the reciprocal gradient at q_0
+    ii, jj = to_pairs(rows_s, sample)
+    G = pair_gradients(q0, s.charge, s.type, ii, jj, p, "short") + bonded_gradients(
+        q0, s.bonds, s.bond_k_r0, s.angles, s.angle_k_t0, s.box)
+    _, g_rec = ewald.spme_recip(q0, s.charge, s.box, 0.35, (96, 96, 96), 5)
+    _, g_exc = ewald.exclusion(q0, s.charge, ewald.molecule_pairs(s.molecule), 0.35, s.box)
+    G = G + g_rec + g_exc
+    h = 0.5
+    v = s.v - ((h * ACCEL) / s.mass)[:, None] * G
+    # J over dt/2 (stream 1) with the sampled atoms' rows; the others have none
+    _, Lstar = bound_table(s.charge, s.type, 2, s.lj_sigma, s.lj_eps, p)
+    v, rec = jump_half(q0, v, row_list, topo, p, Lstar, 1.0 / (KB * 300.0), 1.0, 13, 0, philox.STREAM_J1,
+                       record=True)
+    tie = np.zeros(s.n_atoms, bool)
+    tie[rec["atom"][np.abs(rec["U"] - rec["ratio"]) < 1e-6]] = True
+    q = q0 + h * v
+    v = o_step(v, s.mass, 300.0, 0.001, 1.0, 13, 0)
+    q = q + h * v
+    keep = sample[~tie[sample]]
+    dq = np.linalg.norm(q1[keep] - q[keep], axis=1) / np.maximum(np.linalg.norm(q[keep] - q0[keep], axis=1), 1e-6)
+    assert dq.max() < TOL, (dq.max(), int(rec["M"].sum()))
+    if coulomb_jumps:
+        assert rec["M"][sample].sum() > 20         # the jump step ran on the sample

@@ -122,3 +122,41 @@ def test_one_bounce_step_lj_only(name):
     e = ctx.energies()
     assert e["proposals"] > 0
     ctx.close()
+
+
+def test_idle_rows_completed_for_readers():
+    """With LJ alone on the jumps, H atoms have L* = 0 and never propose, so a
+    run on clusters builds no rows for them.  Entry points that read every
+    row (energies, pair histogram) complete them first: their results at the
+    run's final state match the oracle's, and calling them between two runs
+    leaves the trajectory (rebuild steps included) bit for bit unchanged."""
+    s, ctx, md = _setup("box_ewald")
+    assert ctx.bounds()[1][1] == 0.0           # H: no LJ, no jump bound
+    ctx.run(30, bounce.BOUNCE)
+    q, v = ctx.get_state()
+    e = ctx.energies()
+    ref = OracleMD(q, v, md.topo, md.p, seed=21, skin=1.0, step=33)
+    er = ref.energies()
+    sc, sl = ref.energy_scale()
+    for k_gpu, k_ref, scale in (("coulomb", "coul", sc), ("lj", "lj", sl)):
+        assert abs(e[k_gpu] - er[k_ref]) < 1e-6 * scale + 1e-9, (k_gpu, e[k_gpu], er[k_ref])
+    from oracle.observables import pair_histogram
+    h = ctx.pair_histogram(0, 1, 8.0, 32)
+    assert np.array_equal(h, pair_histogram(q, s.type, s.molecule, 0, 1, 8.0, 32, s.box))
+    # the same 60 steps with and without readers in between
+    out = []
+    for readers in (True, False):
+        c2 = bounce.from_system(s, seed=21, jump_coulomb=False, **CASES["box_ewald"][1])
+        c2.set_state(s.q, s.v, step=3)
+        for _ in range(3):
+            c2.run(20, bounce.BOUNCE)
+            if readers:
+                c2.energies()
+                c2.pair_histogram(0, 0, 8.0, 32)
+        e2 = c2.energies()
+        out.append((c2.get_state(), e2["rebuilds"], e2["proposals"]))
+        c2.close()
+    (q1, v1), *c1 = out[0]
+    (q2, v2), *c2_ = out[1]
+    assert np.array_equal(q1, q2) and np.array_equal(v1, v2) and c1 == c2_
+    ctx.close()
