@@ -299,6 +299,8 @@ int setup_pme(bounce_ctx* c) {
     for (int d = 0; d < 3; ++d) {
         m.K[d] = g.pme_grid[d];
         m.L[d] = g.box[d];
+        m.iL[d] = 1.0 / g.box[d];
+        m.KL[d] = (double)m.K[d] / g.box[d];
         if (m.K[d] < g.pme_order) return fail(c, BOUNCE_ERR_INVALID_ARG, "SPME grid smaller than the order");
     }
     m.order = g.pme_order;
@@ -384,6 +386,7 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     for (int d = 0; d < 3; ++d) {
         double Lb = g.periodic ? g.box[d] : 1.0;
         p.Ld[d] = Lb;
+        p.iLd[d] = 1.0 / Lb;
         p.Lhi[d] = (float)Lb;
         p.Llo[d] = (float)(Lb - (double)p.Lhi[d]);
         p.invL[d] = (float)(1.0 / Lb);

@@ -162,6 +162,7 @@ struct DevPme {
     int K[3];
     int order;
     double L[3];
+    double iL[3], KL[3];         // 1 / L and K / L per axis (no FP64 division per atom)
     float beta, two_b_sqrtpi;
     unsigned long long* qgrid;   // int64 fixed-point charge grid (2^40 scale)
     float2* cgrid;               // complex work grid
@@ -186,7 +187,7 @@ struct Params {
     float ebeta, e2b_sqrtpi;  // Ewald beta and 2 beta / sqrt(pi); ebeta = 0: bare Coulomb
     int periodic;
     float Lhi[3], Llo[3], invL[3];
-    double Ld[3];
+    double Ld[3], iLd[3];        // box edges and their inverses (FP64)
     float rlist2_lo, rlist2_hi;  // FP32 screening band around r_list^2
     double rlist2_d;             // exact FP64 threshold r_list^2 (+inf = all)
     float rshort2;               // short-row threshold
@@ -297,6 +298,16 @@ __device__ __forceinline__ int poisson_invert_f32(float u, float mu_c) {
         cdf = cn;
     }
     return k;
+}
+
+// x wrapped into [0, L): the multiple of L from the product with 1/L (no
+// FP64 division on the per-step path), moved by one where the product's
+// rounding put x on the wrong side of a multiple.
+__device__ __forceinline__ double wrap_box(double x, double L, double iL) {
+    double w = x - L * floor(x * iL);
+    if (w < 0.0) w += L;
+    else if (w >= L) w -= L;
+    return w;
 }
 
 // ------------------------------------------------------------- pair terms

@@ -115,9 +115,9 @@ __global__ void k_pack(DevSys s, Params p, int cur) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
         double x = s.qx[cur][i], y = s.qy[cur][i], z = s.qz[cur][i];
         if (p.periodic) {
-            x -= p.Ld[0] * floor(x / p.Ld[0]);
-            y -= p.Ld[1] * floor(y / p.Ld[1]);
-            z -= p.Ld[2] * floor(z / p.Ld[2]);
+            x = wrap_box(x, p.Ld[0], p.iLd[0]);
+            y = wrap_box(y, p.Ld[1], p.iLd[1]);
+            z = wrap_box(z, p.Ld[2], p.iLd[2]);
         }
         const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
         const float4 oh = s.phi[cur][i];

@@ -201,6 +201,7 @@ extern "C" int bounce_pair_energy_noalloc(int32_t n, const double* q, const doub
         // minimum image: beyond half an edge the sum would no longer be the pair sum
         if (box && !(cut && 2.0 * r_cut <= Lb)) return BOUNCE_ERR_INVALID_ARG;
         p.Ld[d] = Lb;
+        p.iLd[d] = 1.0 / Lb;
         p.Lhi[d] = (float)Lb;
         p.Llo[d] = (float)(Lb - (double)p.Lhi[d]);
         p.invL[d] = (float)(1.0 / Lb);

@@ -29,16 +29,22 @@ constexpr int MAX_ORDER = 8;
 
 // M_n(fr + t), t = 0..n-1, and dM_n/dx at the same points, by the recursion
 // M_{k+1}(x) = (x M_k(x) + (k + 1 - x) M_k(x - 1)) / k from M_2.
-__device__ __forceinline__ void bspline_weights(float fr, int n, float* w, float* dw) {
+// (The order n is a template parameter so that every array stays in registers.)
+template <int n>
+__device__ __forceinline__ void bspline_weights(float fr, float* w, float* dw) {
     float a[MAX_ORDER + 1];
+#pragma unroll
     for (int t = 0; t <= n; ++t) a[t] = 0.f;
     a[0] = fr;
     a[1] = 1.f - fr;
+#pragma unroll
     for (int k = 2; k < n; ++k) {
         if (k == n - 1) {
             // derivative from M_{n-1}: M_n'(fr + t) = M_{n-1}(fr + t) - M_{n-1}(fr + t - 1)
+#pragma unroll
             for (int t = 0; t < n; ++t) dw[t] = a[t] - (t > 0 ? a[t - 1] : 0.f);
         }
+#pragma unroll
         for (int t = k; t >= 0; --t) {
             const float x = fr + (float)t;
             a[t] = (x * a[t] + ((float)(k + 1) - x) * (t > 0 ? a[t - 1] : 0.f)) / (float)k;
@@ -48,11 +54,12 @@ __device__ __forceinline__ void bspline_weights(float fr, int n, float* w, float
         dw[0] = 1.f;
         dw[1] = -1.f;
     }
+#pragma unroll
     for (int t = 0; t < n; ++t) w[t] = a[t];
 }
 
-__device__ __forceinline__ void frac_coord(double x, double L, int K, int& fl, float& fr) {
-    const double f = __ddiv_rn(x, L);
+__device__ __forceinline__ void frac_coord(double x, double iL, int K, int& fl, float& fr) {
+    const double f = x * iL;
     const double u = (f - floor(f)) * (double)K;
     double g = floor(u);
     fl = (int)g;
@@ -75,29 +82,33 @@ __device__ __forceinline__ unsigned long long fix40(float v) {
     return (b & 0x80000000u) ? (unsigned long long)(-(long long)r) : r;
 }
 
+template <int n>
 __global__ void k_pme_spread(DevSys s, DevPme m, int step_off) {
     const int cur = (int)((*s.step_base + step_off) & 1);
-    const int n = m.order;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
         int f[3];
         float fr[3];
-        frac_coord(s.qx[cur][i], m.L[0], m.K[0], f[0], fr[0]);
-        frac_coord(s.qy[cur][i], m.L[1], m.K[1], f[1], fr[1]);
-        frac_coord(s.qz[cur][i], m.L[2], m.K[2], f[2], fr[2]);
+        frac_coord(s.qx[cur][i], m.iL[0], m.K[0], f[0], fr[0]);
+        frac_coord(s.qy[cur][i], m.iL[1], m.K[1], f[1], fr[1]);
+        frac_coord(s.qz[cur][i], m.iL[2], m.K[2], f[2], fr[2]);
         float w[3][MAX_ORDER], dw[3][MAX_ORDER];
-        for (int d = 0; d < 3; ++d) bspline_weights(fr[d], n, w[d], dw[d]);
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) bspline_weights<n>(fr[d], w[d], dw[d]);
         const float q = s.phi[cur][i].w;
+        int ig[3][MAX_ORDER];  // grid index f - t (periodic) of every spline point
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int t = 0; t < n; ++t) ig[d][t] = f[d] - t < 0 ? f[d] - t + m.K[d] : f[d] - t;
+#pragma unroll
         for (int a = 0; a < n; ++a) {
-            const int ix = (f[0] - a + m.K[0]) % m.K[0];
             const float qa = q * w[0][a];
+#pragma unroll
             for (int b = 0; b < n; ++b) {
-                const int iy = (f[1] - b + m.K[1]) % m.K[1];
                 const float qab = qa * w[1][b];
-                const size_t row = ((size_t)ix * m.K[1] + iy) * m.K[2];
-                for (int c = 0; c < n; ++c) {
-                    const int iz = (f[2] - c + m.K[2]) % m.K[2];
-                    atomicAdd(&m.qgrid[row + iz], fix40(qab * w[2][c]));
-                }
+                const size_t row = ((size_t)ig[0][a] * m.K[1] + ig[1][b]) * m.K[2];
+#pragma unroll
+                for (int c = 0; c < n; ++c) atomicAdd(&m.qgrid[row + ig[2][c]], fix40(qab * w[2][c]));
             }
         }
     }
@@ -342,41 +353,46 @@ __global__ void k_pme_convolve(DevPme m) {
 
 // Gradient of E_recip + E_excl per atom (FP64 SoA), and the exclusion energy
 // of the pairs (i, j > i) owned by atom i (for bounce_get_energies).
+template <int n>
 __global__ void k_pme_gather(DevSys s, Params p, DevPme m, int step_off) {
     const int cur = (int)((*s.step_base + step_off) & 1);
-    const int n = m.order;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
         int f[3];
         float fr[3];
-        frac_coord(s.qx[cur][i], m.L[0], m.K[0], f[0], fr[0]);
-        frac_coord(s.qy[cur][i], m.L[1], m.K[1], f[1], fr[1]);
-        frac_coord(s.qz[cur][i], m.L[2], m.K[2], f[2], fr[2]);
+        frac_coord(s.qx[cur][i], m.iL[0], m.K[0], f[0], fr[0]);
+        frac_coord(s.qy[cur][i], m.iL[1], m.K[1], f[1], fr[1]);
+        frac_coord(s.qz[cur][i], m.iL[2], m.K[2], f[2], fr[2]);
         float w[3][MAX_ORDER], dw[3][MAX_ORDER];
-        for (int d = 0; d < 3; ++d) bspline_weights(fr[d], n, w[d], dw[d]);
+        #pragma unroll
+        for (int d = 0; d < 3; ++d) bspline_weights<n>(fr[d], w[d], dw[d]);
+        int ig[3][MAX_ORDER];  // grid index f - t (periodic) of every spline point
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int t = 0; t < n; ++t) ig[d][t] = f[d] - t < 0 ? f[d] - t + m.K[d] : f[d] - t;
         float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
         for (int a = 0; a < n; ++a) {
-            const int ix = (f[0] - a + m.K[0]) % m.K[0];
+#pragma unroll
             for (int b = 0; b < n; ++b) {
-                const int iy = (f[1] - b + m.K[1]) % m.K[1];
-                const size_t row = ((size_t)ix * m.K[1] + iy) * m.K[2];
-                float sx = 0.f, sy = 0.f, sz = 0.f;
+                const size_t row = ((size_t)ig[0][a] * m.K[1] + ig[1][b]) * m.K[2];
+                float sx = 0.f, sz = 0.f;
+#pragma unroll
                 for (int c = 0; c < n; ++c) {
-                    const int iz = (f[2] - c + m.K[2]) % m.K[2];
-                    const float cv = m.cgrid[row + iz].x;
+                    const float cv = m.cgrid[row + ig[2][c]].x;
                     sx += cv * w[2][c];
                     sz += cv * dw[2][c];
                 }
                 gx += dw[0][a] * w[1][b] * sx;
                 gy += w[0][a] * dw[1][b] * sx;
                 gz += w[0][a] * w[1][b] * sz;
-                (void)sy;
             }
         }
         const float4 hi = s.phi[cur][i], lo = s.plo[cur][i];
         const double kq = KCOUL_D * (double)hi.w;
-        double Gx = kq * (double)gx * (m.K[0] / m.L[0]);
-        double Gy = kq * (double)gy * (m.K[1] / m.L[1]);
-        double Gz = kq * (double)gz * (m.K[2] / m.L[2]);
+        double Gx = kq * (double)gx * m.KL[0];
+        double Gy = kq * (double)gy * m.KL[1];
+        double Gz = kq * (double)gz * m.KL[2];
         // same-molecule pairs: -k q_i q_j erf(beta r)/r
         double ex = 0.0;
         for (int t = m.ex_off[i]; t < m.ex_off[i + 1]; ++t) {
@@ -399,6 +415,60 @@ __global__ void k_pme_gather(DevSys s, Params p, DevPme m, int step_off) {
         m.grad[s.n + i] = Gy;
         m.grad[2 * (size_t)s.n + i] = Gz;
         m.eexcl[i] = ex;
+    }
+}
+
+// Lines of K = 32 M points (M = 1..5): one warp per line, no shared-memory
+// stages and no barriers.  With n = 32 n1 + n2 and k = k1 + M k2
+// (Cooley-Tukey, N1 = M, N2 = 32):
+//   X[k1 + M k2] = sum_n2 W_32^(n2 k2) [ W_K^(n2 k1) sum_n1 x[32 n1 + n2] W_M^(n1 k1) ],
+// so lane n2 holds x[32 n1 + n2] for n1 < M in registers, takes the M-point
+// DFTs in registers, multiplies by the twiddles W_K^(n2 k1), and the warp
+// takes the 32-point DFTs across its lanes by shuffles (decimation in
+// frequency: 5 butterfly stages, output in bit-reversed lane order).
+// Twiddles W_K^e = exp(sign 2 pi i e / K) come from a table in shared memory.
+template <int M>
+__global__ void __launch_bounds__(256) k_pme_fft_w(DevPme m, int axis, float sign) {
+    constexpr int K = 32 * M;
+    __shared__ float2 tw[K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)K, &sn, &cs);
+        tw[k] = make_float2(cs, sign * sn);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nlines = (int)((size_t)m.K[0] * m.K[1] * m.K[2] / K);
+    size_t stride;
+    if (axis == 2) stride = 1;
+    else if (axis == 1) stride = m.K[2];
+    else stride = (size_t)m.K[1] * m.K[2];
+    const int rev = (int)(__brev((unsigned)lane) >> 27);
+    for (int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < nlines; l += gridDim.x * (blockDim.x >> 5)) {
+        size_t b0;
+        if (axis == 2) b0 = (size_t)l * m.K[2];
+        else if (axis == 1) b0 = (size_t)(l / m.K[2]) * m.K[1] * m.K[2] + (l % m.K[2]);
+        else b0 = (size_t)l;
+        float2 v[M > 1 ? M : 2];
+#pragma unroll
+        for (int n1 = 0; n1 < M; ++n1) v[n1] = m.cgrid[b0 + (size_t)(32 * n1 + lane) * stride];
+        if (M > 1) small_dft(v, M, sign);
+#pragma unroll
+        for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], tw[(lane * k1) % K]);
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) {
+            const bool low = (lane & sh) != 0;
+            const float2 w = tw[(lane & (sh - 1)) * (K / (2 * sh))];
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) {
+                float2 b;
+                b.x = __shfl_xor_sync(0xffffffffu, v[k1].x, sh);
+                b.y = __shfl_xor_sync(0xffffffffu, v[k1].y, sh);
+                v[k1] = low ? cmul(csub(b, v[k1]), w) : cadd(v[k1], b);
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) m.cgrid[b0 + (size_t)(k1 + M * rev) * stride] = v[k1];
     }
 }
 
@@ -429,13 +499,29 @@ constexpr int PME_CONV_CTAS = 256;
 
 void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st) {
     const int tb = 128;
-    k_pme_spread<<<(s.n + tb - 1) / tb, tb, 0, st>>>(s, m, step_off);
+    const int nb = (s.n + tb - 1) / tb;
+    switch (m.order) {
+        case 3: k_pme_spread<3><<<nb, tb, 0, st>>>(s, m, step_off); break;
+        case 4: k_pme_spread<4><<<nb, tb, 0, st>>>(s, m, step_off); break;
+        case 5: k_pme_spread<5><<<nb, tb, 0, st>>>(s, m, step_off); break;
+        case 6: k_pme_spread<6><<<nb, tb, 0, st>>>(s, m, step_off); break;
+        case 7: k_pme_spread<7><<<nb, tb, 0, st>>>(s, m, step_off); break;
+        default: k_pme_spread<8><<<nb, tb, 0, st>>>(s, m, step_off); break;
+    }
     const size_t N = (size_t)m.K[0] * m.K[1] * m.K[2];
     k_pme_load<<<(int)std::min<size_t>((N + 255) / 256, 4096), 256, 0, st>>>(m);
     const int lines[3] = {m.K[1] * m.K[2], m.K[0] * m.K[2], m.K[0] * m.K[1]};
     auto transform = [&](int axis, float sign) {
         FftPlan pl;
-        if (fft_plan(m.K[axis], pl)) {
+        const int K = m.K[axis], Mw = K / 32, nl = lines[axis];
+        const int wb = std::min((nl + 7) / 8, 152 * 8);
+        if (K % 32 == 0 && Mw >= 1 && Mw <= 5) {
+            if (Mw == 1) k_pme_fft_w<1><<<wb, 256, 0, st>>>(m, axis, sign);
+            else if (Mw == 2) k_pme_fft_w<2><<<wb, 256, 0, st>>>(m, axis, sign);
+            else if (Mw == 3) k_pme_fft_w<3><<<wb, 256, 0, st>>>(m, axis, sign);
+            else if (Mw == 4) k_pme_fft_w<4><<<wb, 256, 0, st>>>(m, axis, sign);
+            else k_pme_fft_w<5><<<wb, 256, 0, st>>>(m, axis, sign);
+        } else if (fft_plan(m.K[axis], pl)) {
             const size_t smem = (2 * (size_t)FFT_B + 1) * m.K[axis] * sizeof(float2);
             k_pme_fft<<<(lines[axis] + FFT_B - 1) / FFT_B, 128, smem, st>>>(m, axis, sign, pl);
         } else {
@@ -445,7 +531,14 @@ void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off,
     for (int axis = 2; axis >= 0; --axis) transform(axis, -1.f);
     k_pme_convolve<<<PME_CONV_CTAS, 256, 0, st>>>(m);
     for (int axis = 2; axis >= 0; --axis) transform(axis, 1.f);
-    k_pme_gather<<<(s.n + tb - 1) / tb, tb, 0, st>>>(s, p, m, step_off);
+    switch (m.order) {
+        case 3: k_pme_gather<3><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
+        case 4: k_pme_gather<4><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
+        case 5: k_pme_gather<5><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
+        case 6: k_pme_gather<6><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
+        case 7: k_pme_gather<7><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
+        default: k_pme_gather<8><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
+    }
 }
 
 void launch_pme_energy(const DevPme& m, int n, double* out, cudaStream_t st) {

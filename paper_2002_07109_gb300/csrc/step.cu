@@ -737,9 +737,9 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
             s.qz[nxt][i] = z;
             double wx = x, wy = y, wz = z;
             if (p.periodic) {
-                wx -= p.Ld[0] * floor(x / p.Ld[0]);
-                wy -= p.Ld[1] * floor(y / p.Ld[1]);
-                wz -= p.Ld[2] * floor(z / p.Ld[2]);
+                wx = wrap_box(x, p.Ld[0], p.iLd[0]);
+                wy = wrap_box(y, p.Ld[1], p.iLd[1]);
+                wz = wrap_box(z, p.Ld[2], p.iLd[2]);
             }
             const float hx = __double2float_rn(wx), hy = __double2float_rn(wy), hz = __double2float_rn(wz);
             const float4 ph = make_float4(hx, hy, hz, sHw[lane]);
@@ -919,9 +919,12 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
     chain_enter();
     if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     int nprop = 0, nacc = 0, near = 0;
-    if (i < s.n) {
+    if (t < s.n) {
+        // atoms that can propose first (act_order): whole warps of atoms
+        // without a jump bound then skip the FP64 set-up of the jump step
+        const int i = (BOUNCE && s.act_order) ? s.act_order[t] : t;
         const long long step = *s.step_base + step_off;
         const int cur = (int)(step & 1), nxt = cur ^ 1;
         const bool do_j2 = BOUNCE && variant != 0;
@@ -1010,9 +1013,9 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
             s.qz[nxt][i] = z;
             double wx = x, wy = y, wz = z;
             if (p.periodic) {
-                wx -= p.Ld[0] * floor(x / p.Ld[0]);
-                wy -= p.Ld[1] * floor(y / p.Ld[1]);
-                wz -= p.Ld[2] * floor(z / p.Ld[2]);
+                wx = wrap_box(x, p.Ld[0], p.iLd[0]);
+                wy = wrap_box(y, p.Ld[1], p.iLd[1]);
+                wz = wrap_box(z, p.Ld[2], p.iLd[2]);
             }
             const float hx = __double2float_rn(wx), hy = __double2float_rn(wy), hz = __double2float_rn(wz);
             const float4 ph = make_float4(hx, hy, hz, ahi.w);

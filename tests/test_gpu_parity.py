@@ -612,3 +612,25 @@ def test_full_size_box_first_step_sampled(coulomb_jumps):
     assert dq.max() < TOL, (dq.max(), int(rec["M"].sum()))
     if coulomb_jumps:
         assert rec["M"][sample].sum() > 20         # the jump step ran on the sample
+
+
+@pytest.mark.parametrize("grid", [(32, 64, 96), (40, 128, 160)])
+def test_recip_fft_line_lengths(grid):
+    """SPME with grid lines of every kind the FFT takes: lengths 32 M
+    (M = 1..5) go to the warp-shuffle transform, others (40) to the batched
+    Stockham transform; the reciprocal gradient and energy against the
+    oracle's FFT on the same grid."""
+    from oracle import ewald
+    s = water_box(6, seed=3)
+    cfg = dict(r_on=7.0, r_off=8.0, r_cut=9.0, skin=1.0, ewald_beta=0.35, pme_grid=grid, pme_order=5)
+    ctx = bounce.from_system(s, seed=1, **cfg)
+    ctx.set_state(s.q, s.v, step=0)
+    g = ctx.gradient(bounce.GRAD_RECIP)
+    er, gr = ewald.spme_recip(s.q, s.charge, s.box, 0.35, grid, 5)
+    ex, gx = ewald.exclusion(s.q, s.charge, ewald.molecule_pairs(s.molecule), 0.35, s.box)
+    scale = np.linalg.norm(gr, axis=1) + np.linalg.norm(gx, axis=1)
+    _check_sum(g, gr + gx, scale)
+    e = ctx.energies()
+    es = ewald.self_energy(s.charge, 0.35)
+    assert abs(e["recip"] - (er + ex + es)) < 1e-6 * (abs(er) + abs(ex) + abs(es)), (e["recip"], er + ex + es)
+    ctx.close()
