@@ -63,6 +63,7 @@ METRIC = "ns/day & pair-evals/s, BOUNCE vs BAOAB 1fs on one GB300 at matched <E>
 WINDOW = 24        # steps per timed window (a multiple of every arm's outer step)
 BOX_SIDE = 32      # 32^3 = 32,768 molecules
 R_CUT, R_ON, R_OFF, SKIN, BETA, GRID, ORDER = 9.0, 7.5, 8.5, 1.0, 0.35, 96, 5
+PAIR_SKIN = 2.0
 DT = 1.0
 RHO_O = 0.03343    # O atoms per A^3 at 1 g/cm^3
 WORKLOAD = ("BOUNCE-RESPA (SPME on the 2 fs outer step) vs BAOAB 1 fs, 32,768-molecule periodic flexible-water box "
@@ -181,16 +182,18 @@ def ns_per_day(steps, seconds):
 
 
 def box_cfg(device, **kw):
-    cfg = dict(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, skin=SKIN, dt=DT, ewald_beta=BETA, pme_grid=(GRID,) * 3,
-               pme_order=ORDER, max_neighbors=1024, device=device)
+    # cluster lists with a 2 A skin (rebuilt rarely; the pair kernel reads
+    # lists pruned to r_c + 0.5 A every few steps)
+    cfg = dict(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, skin=SKIN, pair_skin=PAIR_SKIN, dt=DT, ewald_beta=BETA,
+               pme_grid=(GRID,) * 3, pme_order=ORDER, max_neighbors=1024, device=device)
     cfg.update(kw)
     return cfg
 
 
 # The jump step's candidate rows are rebuilt when an atom has moved half
-# their skin; a wider skin makes them rarer (and longer) while the cluster
-# lists of the pair sums keep a 1 A skin.  BAOAB reads no rows.
-JUMP_ROWS = dict(skin=2.5, pair_skin=1.0, max_neighbors=2048)
+# their skin; a wider skin makes them rarer (and longer).  BAOAB reads no
+# rows.
+JUMP_ROWS = dict(skin=2.5, max_neighbors=2048)
 # The headline split: LJ beyond the switch on the jumps, Coulomb in F_0
 # (reading of the paper's first example).  With Coulomb on the jumps too the
 # reflections heat flexible water at 1 fs (measured in matched_observables).
@@ -550,11 +553,20 @@ def batched_replicas(bounce, device, stream, sh, rank, n_steps=10000, n_baoab=10
     out = {"workload": "256 droplets of 64-1,024 molecules (%d atoms in all), no cutoff, switch 4-5 A, 1 fs"
                        % cat.n_atoms}
     stream = torch.cuda.current_stream(torch.device("cuda", device))
+    cfg = dict(r_on=4.0, r_off=5.0, r_cut=math.inf, jump_coulomb=False, max_neighbors=int(np.diff(off).max()),
+               device=device)
+    # the lattice droplets melted with BAOAB at friction 0.05/fs (2 ps), both arms from there
+    eq = bounce.from_system(cat, seed=1, gamma=0.05, **cfg)
+    eq.set_replicas(off, seeds)
+    eq.set_state(cat.q, cat.v)
+    eq.run(2000, bounce.BAOAB, stream=sh)
+    q0, v0 = eq.get_state(stream=sh)
+    eq.close()
+    out["start"] = "BAOAB at friction 0.05/fs for 2 ps from the lattice droplets"
     for name, integ, steps in (("bounce_lj_jumps", bounce.BOUNCE, n_steps), ("baoab", bounce.BAOAB, n_baoab)):
-        ctx = bounce.from_system(cat, seed=1, r_on=4.0, r_off=5.0, r_cut=math.inf, jump_coulomb=False,
-                                 max_neighbors=int(np.diff(off).max()), device=device)
+        ctx = bounce.from_system(cat, seed=1, **cfg)
         ctx.set_replicas(off, seeds)
-        ctx.set_state(cat.q, cat.v)
+        ctx.set_state(q0, v0)
         tune = ctx.autotune(integ, stream=sh)
         ctx.run(64, integ, stream=sh)
         torch.cuda.synchronize()

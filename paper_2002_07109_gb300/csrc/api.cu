@@ -505,6 +505,11 @@ int setup_grid(bounce_ctx* c, const double* q) {
 // positions with margins (an overflow during a run is reported as
 // BOUNCE_ERR_LIST_OVERFLOW).  A droplet keeps its grid while every atom
 // stays inside it, so that captured graphs stay valid.
+// Largest prune skin of the cluster lists (A).
+#ifndef CL_PRUNE_SKIN
+#define CL_PRUNE_SKIN 0.8
+#endif
+
 int setup_clusters(bounce_ctx* c, const double* q) {
     DevClu& k = c->ds.cl;
     const bounce_config& g = c->cfg;
@@ -610,14 +615,27 @@ int setup_clusters(bounce_ctx* c, const double* q) {
         nk.rsx[L] = (float)rm;
         nk.rs2[L] = (float)(rm * rm);
     }
-    nk.capitems = ncl * (nk.capj[0] / BOUNCE_CL_EPW + 1);
     nk.cskin_half2 = 0.25 * cskin * cskin;
+    nk.capitems = ncl * (nk.capj[0] / BOUNCE_CL_EPW + 1);
+    // pruned lists: entries within r + dp of some atom of I, dp = half the
+    // cluster skin up to CL_PRUNE_SKIN (10 mA margin for the FP32 test),
+    // pruned again when an atom has moved dp / 2 (1 mA margin)
+    {
+        const double dp = std::min(0.5 * cskin, (double)CL_PRUNE_SKIN);
+        for (int L = 0; L < 2; ++L) {
+            const double rp = rr[L] - cskin + dp + 0.01;
+            nk.prs2[L] = (float)(rp * rp);
+        }
+        const double hp = 0.5 * dp - 0.001;
+        nk.pdisp2 = (float)(hp * hp);
+    }
     int r;
     if (!c->cl_atoms_alloc) {
         if ((r = dalloc(c, &nk.col_atoms, n)) || (r = dalloc(c, &nk.atom_col, n)) || (r = dalloc(c, &nk.a2s, n)) ||
             (r = dalloc(c, &nk.crefx, n)) || (r = dalloc(c, &nk.crefy, n)) || (r = dalloc(c, &nk.crefz, n)) ||
             (r = dalloc(c, &nk.cofx, n)) || (r = dalloc(c, &nk.cofy, n)) || (r = dalloc(c, &nk.cofz, n)) ||
-            (r = dalloc(c, &nk.nitems, 2)) || (r = dalloc(c, &nk.rebuild, 1)) || (r = dalloc(c, &nk.done_ctr, 2)))
+            (r = dalloc(c, &nk.rebuild, 1)) || (r = dalloc(c, &nk.done_ctr, 3)) || (r = dalloc(c, &nk.prune, 1)) ||
+            (r = dalloc(c, &nk.pnitems, 4)))
             return r;
         c->cl_atoms_alloc = true;
     }
@@ -632,17 +650,20 @@ int setup_clusters(bounce_ctx* c, const double* q) {
         if ((r = dalloc(c, &nk.cl_atom, sl)) || (r = dalloc(c, &nk.sphi[0], sl)) || (r = dalloc(c, &nk.sphi[1], sl)) ||
             (r = dalloc(c, &nk.splo[0], sl)) || (r = dalloc(c, &nk.splo[1], sl)) || (r = dalloc(c, &nk.smol, sl)) ||
             (r = dalloc(c, &nk.bb_lo, ncl)) || (r = dalloc(c, &nk.bb_hi, ncl)) || (r = dalloc(c, &nk.lcnt[0], ncl)) ||
-            (r = dalloc(c, &nk.lcnt[1], ncl)) || (r = dalloc(c, &nk.acc, 3 * sl)))
+            (r = dalloc(c, &nk.lcnt[1], ncl)) || (r = dalloc(c, &nk.acc, 3 * sl)) || (r = dalloc(c, &nk.pref, sl)) ||
+            (r = dalloc(c, &nk.pcnt[0], ncl)) || (r = dalloc(c, &nk.pcnt[1], ncl)))
             return r;
         c->cl_cap_ncl = ncl;
     }
     for (int L = 0; L < 2; ++L)
         if ((size_t)ncl * nk.capj[L] > c->cl_cap_lst[L]) {
-            if ((r = dalloc(c, &nk.lst[L], (size_t)ncl * nk.capj[L]))) return r;
+            if ((r = dalloc(c, &nk.lst[L], (size_t)ncl * nk.capj[L])) ||
+                (r = dalloc(c, &nk.plst[L], (size_t)ncl * nk.capj[L])))
+                return r;
             c->cl_cap_lst[L] = (size_t)ncl * nk.capj[L];
         }
     if (nk.capitems > c->cl_cap_items) {
-        if ((r = dalloc(c, &nk.items[0], nk.capitems)) || (r = dalloc(c, &nk.items[1], nk.capitems))) return r;
+        if ((r = dalloc(c, &nk.pitems[0], nk.capitems)) || (r = dalloc(c, &nk.pitems[1], nk.capitems))) return r;
         c->cl_cap_items = nk.capitems;
     }
     k = nk;
@@ -1448,9 +1469,9 @@ int64_t bounce_run_launch_count(const bounce_ctx* c, int64_t n, int32_t integ) {
     // one kernel for a batch of replicas) + the fused step kernel, and the
     // pair-sum kernel wherever the boundary has pair sums over the long rows
     const bool clu = c->ds.cl.on != 0;
-    // gated rebuilds: the clusters (4), the rows (3, or 1 for a batch) unless
-    // BAOAB runs on clusters; then the step kernel
-    const int64_t per_boundary = (clu ? 4 : 0) + ((clu && integ == BOUNCE_BAOAB) ? 0 : (c->ds.rep_of ? 1 : 3)) + 1;
+    // gated rebuilds: the clusters (4, and the list prune), the rows (3, or 1
+    // for a batch) unless BAOAB runs on clusters; then the step kernel
+    const int64_t per_boundary = (clu ? 5 : 0) + ((clu && integ == BOUNCE_BAOAB) ? 0 : (c->ds.rep_of ? 1 : 3)) + 1;
     const bool ext = integ >= BOUNCE_BOUNCE_RESPA_EXT;
     const bool short_f0 = !clu && integ != BOUNCE_BAOAB && c->pp.rshort2 < INFINITY;
     const int64_t pme_launches = 10; // spread, load, 3 + 3 transforms, convolve, gather
@@ -1478,7 +1499,7 @@ int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     launch_energies(c->ds, c->pp, (int)(step & 1), c->terms, st);
     double tot[5], pe[2] = {0.0, 0.0};
     if (c->has_pme) {
-        launch_pme(c->ds, c->pp, c->pme, 0, st);
+        launch_pme(c->ds, c->pp, c->pme, 0, st, true);
         launch_pme_energy(c->pme, c->n, c->terms + 6 * (size_t)c->n + 1024, st);
         CU(cudaMemcpyAsync(pe, c->terms + 6 * (size_t)c->n + 1024, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     }

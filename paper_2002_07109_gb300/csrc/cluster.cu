@@ -15,9 +15,15 @@
 //   4. one warp per cluster I collects the atoms of the clusters J >= I of
 //      the columns in reach that lie within the search radius of I's box
 //      (minimum image per axis), in a fixed order, with the periodic image
-//      of each; the CTA finishing last cuts the lists into work items of
-//      BOUNCE_CL_EPW entries and clears the flag.
-// Pair kernel: one warp per work item; lane = one list atom j, the 8 atoms
+//      of each; the CTA finishing last clears the flag and raises the prune
+//      flag.
+// Prune (a fifth gated launch, also raised by the step kernel when an atom
+// has moved half the prune skin since the last prune): the entries of each
+// list within r + prune skin of some atom of I at the current positions,
+// so that the pair kernel reads a list close to the pairs it must evaluate
+// while the outer lists, with a larger skin, are rebuilt rarely.
+// Pair kernel: one warp per work item (cluster I, chunk of BOUNCE_CL_EPW
+// pruned entries); lane = one list atom j, the 8 atoms
 // of cluster I in turn from shared memory.  Every unordered pair inside the
 // cutoff is evaluated once (Newton's third law): the j-side sum of a lane is
 // added once per item, the i-side sums are reduced over the warp at the end
@@ -249,33 +255,15 @@ __device__ __forceinline__ void column_span(int n, float a, float b, float org, 
     }
 }
 
-// Cuts the per-cluster lists into work items of EPW entries (one CTA).
-__device__ void build_items(const DevClu& c) {
-    const int ncl = c.ncol * c.maxcl;
-    for (int L = 0; L < c.nlists; ++L) {
-        int carry = 0;
-        for (int b = 0; b < ncl; b += blockDim.x) {
-            const int I = b + threadIdx.x;
-            const int cnt = I < ncl ? __ldcg(&c.lcnt[L][I]) : 0;
-            const int nch = (cnt + EPW - 1) / EPW;
-            int tot;
-            const int ex = block_scan(nch, &tot);
-            for (int k = 0; k < nch; ++k) {
-                const int it = carry + ex + k;
-                if (it < c.capitems) c.items[L][it] = make_int2(I, k * EPW);
-            }
-            carry += tot;
-        }
-        if (threadIdx.x == 0) c.nitems[L] = min(carry, c.capitems);
-    }
-}
-
-// The work items did not fit (reported as a list overflow, never dropped silently).
-__device__ void check_items(const DevSys& s) {
-    const DevClu& c = s.cl;
-    if (threadIdx.x == 0)
-        for (int L = 0; L < c.nlists; ++L)
-            if (c.nitems[L] >= c.capitems) atomicOr(s.err, BERR_LIST_OVERFLOW);
+// q_j - k L in split form (sh, sl: the high and low parts of k L): the high
+// part rounded, its rounding error moved into the low part (two-sum), so the
+// pair stays an exact split of the shifted coordinate.
+__device__ __forceinline__ void shift_split(float& h, float& l, float sh, float sl) {
+    const float t = h - sh;
+    const float bb = t - h;
+    const float err = (h - (t - bb)) + (-sh - bb);
+    h = t;
+    l = (l - sl) + err;
 }
 
 // 4. neighbour lists (warp per cluster I): every atom j of a cluster
@@ -398,10 +386,96 @@ __global__ void __launch_bounds__(256) k_cl_search(DevSys s, Params p, int step_
     }
     if (overflow) atomicOr(s.err, BERR_LIST_OVERFLOW);
     if (!cl_last_cta(&c.done_ctr[1])) return;
-    build_items(c);
-    __syncthreads();
-    check_items(s);
-    if (threadIdx.x == 0) *c.rebuild = 0;
+    if (threadIdx.x == 0) {
+        *c.rebuild = 0;
+        *c.prune = 1;  // new lists: prune them before the next pair sums
+    }
+}
+
+// 5. pruned lists (warp per cluster I), gated by the prune flag: the
+// entries of each list whose atom j lies within the prune radius of at least
+// one atom of I at the current positions (same images as the pair kernel;
+// FP32 with a margin, so that no pair the exact test would keep is dropped),
+// in list order.  The step kernel raises the flag when an atom's slot copy has moved half the
+// prune skin since this launch, which it records here.
+__global__ void __launch_bounds__(256) k_cl_prune(DevSys s, Params p, int step_off, int force) {
+    chain_enter();
+    if (!(force || *s.cl.prune)) return;
+    const DevClu& c = s.cl;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, wl = threadIdx.x >> 5;
+    __shared__ float4 s_hi[8][CL], s_lo[8][CL];
+    const int ncl = c.ncol * c.maxcl;
+    const int cur = (int)((*s.step_base + step_off) & 1);
+    const uint32_t below = (1u << lane) - 1u;
+    for (int I = blockIdx.x * wpb + wl; I < ncl; I += gridDim.x * wpb) {
+        __syncwarp();
+        if (lane < CL) {
+            s_hi[wl][lane] = c.sphi[cur][I * CL + lane];
+            s_lo[wl][lane] = c.splo[cur][I * CL + lane];
+            c.pref[I * CL + lane] = c.sphi[cur][I * CL + lane];
+        }
+        __syncwarp();
+        for (int L = 0; L < c.nlists; ++L) {
+            const int n = c.lcnt[L][I];
+            const int* src = c.lst[L] + (size_t)I * c.capj[L];
+            int* dst = c.plst[L] + (size_t)I * c.capj[L];
+            int m = 0;
+            for (int e0 = 0; e0 < n; e0 += 32) {
+                const int e = e0 + lane;
+                bool keep = false;
+                int ent = 0;
+                if (e < n) {
+                    ent = src[e];
+                    const int sj = ent & 0x07FFFFFF, code = (int)((uint32_t)ent >> 27);
+                    float4 hj = c.sphi[cur][sj], lj = c.splo[cur][sj];
+                    if (code != NO_SHIFT && code != PER_PAIR) {
+                        const float kx = (float)(code / 9 - 1), ky = (float)((code / 3) % 3 - 1),
+                                    kz = (float)(code % 3 - 1);
+                        shift_split(hj.x, lj.x, kx * p.Lhi[0], kx * p.Llo[0]);
+                        shift_split(hj.y, lj.y, ky * p.Lhi[1], ky * p.Llo[1]);
+                        shift_split(hj.z, lj.z, kz * p.Lhi[2], kz * p.Llo[2]);
+                    }
+                    float best = INFINITY;
+                    if (code == PER_PAIR) {
+                        for (int a = 0; a < CL; ++a) {
+                            const float3 d = pair_disp(p, s_hi[wl][a], s_lo[wl][a], hj, lj);
+                            best = fminf(best, d.x * d.x + d.y * d.y + d.z * d.z);
+                        }
+                    } else {
+                        // high parts suffice here: the radius carries a margin far
+                        // above their rounding (the low parts are below 1e-5 A)
+#pragma unroll
+                        for (int a = 0; a < CL; ++a) {
+                            const float dx = s_hi[wl][a].x - hj.x, dy = s_hi[wl][a].y - hj.y,
+                                        dz = s_hi[wl][a].z - hj.z;
+                            best = fminf(best, dx * dx + dy * dy + dz * dz);
+                        }
+                    }
+                    keep = best < c.prs2[L];
+                }
+                const uint32_t bk = __ballot_sync(0xffffffffu, keep);
+                if (keep) dst[m + __popc(bk & below)] = ent;
+                m += __popc(bk);
+            }
+            if (lane == 0) {
+                c.pcnt[L][I] = m;
+                // work items of I's pruned list, at slots taken from a counter
+                // (their order does not matter: the sums are fixed point)
+                const int nch = (m + EPW - 1) / EPW;
+                const int b = nch ? atomicAdd(&c.pnitems[2 + L], nch) : 0;
+                for (int k = 0; k < nch; ++k)
+                    if (b + k < c.capitems) c.pitems[L][b + k] = make_int2(I, k * EPW);
+            }
+        }
+    }
+    if (!cl_last_cta(&c.done_ctr[2])) return;
+    if (threadIdx.x < 2) {
+        const int L = threadIdx.x;
+        const int n = atomicExch(&c.pnitems[2 + L], 0);
+        c.pnitems[L] = min(n, c.capitems);
+        if (n > c.capitems) atomicOr(s.err, BERR_LIST_OVERFLOW);
+    }
+    if (threadIdx.x == 0) *c.prune = 0;
 }
 
 // round(v 2^32) as a 64-bit integer from the bits of the FP32 value, with
@@ -429,16 +503,6 @@ __device__ __noinline__ bool cl_exact_inside(const DevSys& s, const Params& p, i
     return exact_r2(s, p, cur, a, b) < p.rc2_d;
 }
 
-// q_j - k L in split form (sh, sl: the high and low parts of k L): the high
-// part rounded, its rounding error moved into the low part (two-sum), so the
-// pair stays an exact split of the shifted coordinate.
-__device__ __forceinline__ void shift_split(float& h, float& l, float sh, float sl) {
-    const float t = h - sh;
-    const float bb = t - h;
-    const float err = (h - (t - bb)) + (-sh - bb);
-    h = t;
-    l = (l - sl) + err;
-}
 
 // The pairs of one list entry (atom slot sj, split position hj/lj in the
 // image of the entry) whose FP32 r^2 fell within the rounding band of r_c^2
@@ -469,6 +533,45 @@ __device__ __forceinline__ void near_pairs(const DevSys& s, const Params& p, int
     }
 }
 
+// The 8 pairs of one list entry j (split position hj/lj in the entry's
+// image, molecule mj, type tj, slot sj) with the atoms of cluster I (shared
+// memory): i sides into gi, the j side into gj, in-cutoff pairs counted,
+// pairs within the rounding band of r_c flagged in `near` for the exact
+// test.  PER: minimum image per pair (clusters near half a box edge).
+template <int PART, bool PER>
+__device__ __forceinline__ void entry_pairs(const Params& p, const float4* shi, const float4* slo, const int* smol,
+                                            const float* c12t, const float* c6t, float4 hj, float4 lj, int mj, int tj,
+                                            int sj, int I, float (&gi)[CL][3], float& gjx, float& gjy, float& gjz,
+                                            uint32_t& near, int& npair) {
+#pragma unroll
+    for (int a = 0; a < CL; ++a) {
+        const float4 hi = shi[a], lo = slo[a];
+        const int mi = smol[a];
+        float3 d;
+        if (PER) {
+            d = pair_disp(p, hi, lo, hj, lj);
+        } else {
+            d.x = (hi.x - hj.x) + (lo.x - lj.x);
+            d.y = (hi.y - hj.y) + (lo.y - lj.y);
+            d.z = (hi.z - hj.z) + (lo.z - lj.z);
+        }
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        const bool ok = mi >= 0 && mi != mj && sj > I * CL + a;
+        const bool in = ok && r2 < p.rc2_lo;
+        near |= (ok && r2 >= p.rc2_lo && r2 <= p.rc2_hi) ? 1u << a : 0u;
+        const int tp = type_of(lo) * BOUNCE_MAXT + tj;
+        const float w0 = pairsum_w<PART>(p, in ? r2 : 1.f, p.kcoul * hi.w * hj.w, c12t[tp], c6t[tp]);
+        const float wv = in ? w0 : 0.f;
+        npair += in ? 1 : 0;
+        gi[a][0] = fmaf(wv, d.x, gi[a][0]);
+        gi[a][1] = fmaf(wv, d.y, gi[a][1]);
+        gi[a][2] = fmaf(wv, d.z, gi[a][2]);
+        gjx = fmaf(-wv, d.x, gjx);
+        gjy = fmaf(-wv, d.y, gjy);
+        gjz = fmaf(-wv, d.z, gjz);
+    }
+}
+
 // Pair sums over the work items of list `L`.  PART 3: the F_0 share
 // (1 - chi) W'_sw + W'_fixed; PART 5: the full W'.  A warp takes an item of
 // cluster I: lanes hold one list atom j each, the 8 atoms of I are read from
@@ -489,15 +592,16 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
     const DevClu& c = s.cl;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int cur = (int)((*s.step_base + step_off) & 1);
-    const int nit = c.nitems[L], capj = c.capj[L];
-    const int* lst = c.lst[L];
-    const int* lcnt = c.lcnt[L];
+    const int capj = c.capj[L];
+    const int* lst = c.plst[L];
+    const int* lcnt = c.pcnt[L];
+    const int nit = c.pnitems[L];
     const size_t ns = (size_t)c.ncol * c.maxcl * CL;
     const float4* sphi = c.sphi[cur];
     const float4* splo = c.splo[cur];
     int npair = 0;
     for (int it = blockIdx.x * 8 + wl; it < nit; it += gridDim.x * 8) {
-        const int2 w = c.items[L][it];
+        const int2 w = c.pitems[L][it];
         const int I = w.x, e1 = min(w.y + EPW, lcnt[I]);
         __syncwarp();
         if (lane < CL) {
@@ -523,33 +627,14 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
             }
             float gjx = 0.f, gjy = 0.f, gjz = 0.f;
             uint32_t near = 0u;  // pairs within the FP32 rounding band of r_c
-#pragma unroll
-            for (int a = 0; a < CL; ++a) {
-                const float4 hi = s_hi[wl][a], lo = s_lo[wl][a];
-                const int mi = s_mol[wl][a];
-                float3 d;
-                if (code == PER_PAIR) {
-                    d = pair_disp(p, hi, lo, hj, lj);
-                } else {
-                    d.x = (hi.x - hj.x) + (lo.x - lj.x);
-                    d.y = (hi.y - hj.y) + (lo.y - lj.y);
-                    d.z = (hi.z - hj.z) + (lo.z - lj.z);
-                }
-                const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-                const bool ok = mi >= 0 && mi != mj && sj > I * CL + a;
-                const bool in = ok && r2 < p.rc2_lo;
-                near |= (ok && r2 >= p.rc2_lo && r2 <= p.rc2_hi) ? 1u << a : 0u;
-                const int tp = type_of(lo) * BOUNCE_MAXT + tj;
-                const float w0 = pairsum_w<PART>(p, in ? r2 : 1.f, p.kcoul * hi.w * hj.w, s_c12[tp], s_c6[tp]);
-                const float wv = in ? w0 : 0.f;
-                npair += in ? 1 : 0;
-                gi[a][0] = fmaf(wv, d.x, gi[a][0]);
-                gi[a][1] = fmaf(wv, d.y, gi[a][1]);
-                gi[a][2] = fmaf(wv, d.z, gi[a][2]);
-                gjx = fmaf(-wv, d.x, gjx);
-                gjy = fmaf(-wv, d.y, gjy);
-                gjz = fmaf(-wv, d.z, gjz);
-            }
+            // the rare per-pair minimum image takes its own copy of the loop,
+            // so that the common one carries no minimum-image arithmetic
+            if (code == PER_PAIR)
+                entry_pairs<PART, true>(p, s_hi[wl], s_lo[wl], s_mol[wl], s_c12, s_c6, hj, lj, mj, tj, sj, I, gi, gjx,
+                                        gjy, gjz, near, npair);
+            else
+                entry_pairs<PART, false>(p, s_hi[wl], s_lo[wl], s_mol[wl], s_c12, s_c6, hj, lj, mj, tj, sj, I, gi, gjx,
+                                         gjy, gjz, near, npair);
             if (near) near_pairs<PART>(s, p, cur, I, sj, hj, lj, near, s_hi[wl], s_lo[wl], s_c12, s_c6, gjx, gjy, gjz,
                                        npair);
             fix_add(c.acc + sj, gjx);
@@ -598,6 +683,7 @@ void launch_cluster_rebuild(const DevSys& s, const Params& p, int step_off, bool
     launch_chained(k_cl_sort, std::min(s.cl.ncol, 152 * 8), SORT_NT, 0, st, s, p, step_off, f);
     const int ncl = s.cl.ncol * s.cl.maxcl;
     launch_chained(k_cl_search, std::min((ncl + 7) / 8, 152 * 8), 256, 0, st, s, p, step_off, f);
+    launch_chained(k_cl_prune, std::min((ncl + 7) / 8, 152 * 8), 256, 0, st, s, p, step_off, f);
 }
 
 void launch_cluster_pairs(const DevSys& s, const Params& p, int step_off, int part, int list, cudaStream_t st) {

@@ -50,7 +50,6 @@ struct DevClu {
     int capj[2];             // entries per cluster of each list
     float rs2[2];            // squared search radii of the lists (with margins)
     float rsx[2];            // the radii themselves
-    int capitems;            // work items per list
     double cskin_half2;      // rebuild when an atom moved more than skin/2 since the build
     int* col_count;          // [ncol]
     int* col_start;          // [ncol + 1]
@@ -67,8 +66,6 @@ struct DevClu {
     float4* bb_hi;
     int* lst[2];             // [ncl * capj] slot of j | image code << 27
     int* lcnt[2];            // [ncl] entries of each cluster
-    int2* items[2];          // (I, first entry) of each work item
-    int* nitems;             // [2]
     unsigned long long* acc; // [3 * ncl * CL] fixed-point gradient sums (x, y, z blocks)
     double* crefx;           // [n] positions at the build
     double* crefy;
@@ -77,7 +74,18 @@ struct DevClu {
     double* cofy;            //     the slot copies keep q - cof until the next build, so that the
     double* cofz;            //     image codes of the lists stay valid when atoms cross a face
     int* rebuild;            // 1 = the clusters must be rebuilt before the next pair sums
-    unsigned int* done_ctr;  // [2] finished-CTA counters (zero between launches)
+    unsigned int* done_ctr;  // [3] finished-CTA counters (zero between launches)
+    // pruned lists: the entries of lst within r + prune skin of some atom of
+    // I at the last prune, valid while no atom moved half the prune skin
+    int* plst[2];            // [ncl * capj] same layout as lst
+    int* pcnt[2];            // [ncl]
+    int2* pitems[2];         // (I, first entry) of each work item of the pruned lists, in allocation order
+    int* pnitems;            // [2] work items, and [2..3] their allocation counters
+    int capitems;            // work items per list
+    float4* pref;            // [ncl * CL] slot positions (high parts) at the last prune
+    float prs2[2];           // squared prune radii (r_c or r'' plus the prune skin, with a margin)
+    float pdisp2;            // squared displacement that triggers the next prune
+    int* prune;              // 1 = prune before the next pair sums
 };
 
 // All-pairs sums (systems without a cutoff): static items (first i, count,
@@ -600,7 +608,8 @@ void launch_step(const DevSys& s, const Params& p, int integrator, int variant, 
 int launch_step_pairs(const DevSys& s, const Params& p, int integrator, int step_off, double hout, cudaStream_t st);
 void launch_step_kernel(const DevSys& s, const Params& p, int integrator, int variant, int step_off, double hr,
                         double hout, int pre, cudaStream_t st);
-void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st);
+// energy: also the FP64 energy partials of the convolution (bounce_get_energies)
+void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st, bool energy = false);
 void launch_pme_energy(const DevPme& m, int n, double* out, cudaStream_t st);
 void launch_gradient(const DevSys& s, const Params& p, int part, int cur, double* out, cudaStream_t st);
 void launch_jump_half(const DevSys& s, const Params& p, int cur, long long step, int stream_id, int* M, int* nacc,

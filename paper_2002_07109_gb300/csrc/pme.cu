@@ -332,6 +332,8 @@ bool fft_plan(int K, FftPlan& pl) {
 }
 
 // F(Q) <- B C F(Q); energy partial sum B C |F(Q)|^2 of this CTA into eterm.
+// ENERGY = false (the steps): the product only, no FP64 energy partials.
+template <bool ENERGY>
 __global__ void k_pme_convolve(DevPme m) {
     __shared__ double red[256];
     const size_t N = (size_t)m.K[0] * m.K[1] * m.K[2];
@@ -339,9 +341,10 @@ __global__ void k_pme_convolve(DevPme m) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
         const float2 c = m.cgrid[k];
         const float b = m.bc[k];
-        e += (double)b * ((double)c.x * c.x + (double)c.y * c.y);
+        if (ENERGY) e += (double)b * ((double)c.x * c.x + (double)c.y * c.y);
         m.cgrid[k] = make_float2(b * c.x, b * c.y);
     }
+    if (!ENERGY) return;
     red[threadIdx.x] = e;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -497,7 +500,7 @@ __global__ void k_pme_energy_sum(DevPme m, int nparts, int n, double* out) {
 
 constexpr int PME_CONV_CTAS = 256;
 
-void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st) {
+void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off, cudaStream_t st, bool energy) {
     const int tb = 128;
     const int nb = (s.n + tb - 1) / tb;
     switch (m.order) {
@@ -529,7 +532,8 @@ void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off,
         }
     };
     for (int axis = 2; axis >= 0; --axis) transform(axis, -1.f);
-    k_pme_convolve<<<PME_CONV_CTAS, 256, 0, st>>>(m);
+    if (energy) k_pme_convolve<true><<<PME_CONV_CTAS, 256, 0, st>>>(m);
+    else k_pme_convolve<false><<<PME_CONV_CTAS, 256, 0, st>>>(m);
     for (int axis = 2; axis >= 0; --axis) transform(axis, 1.f);
     switch (m.order) {
         case 3: k_pme_gather<3><<<nb, tb, 0, st>>>(s, p, m, step_off); break;

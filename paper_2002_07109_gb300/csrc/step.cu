@@ -759,6 +759,10 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
                 s.cl.splo[nxt][sl] = cw;
                 const double cx = x - sCref[lane][0], cy = y - sCref[lane][1], cz = z - sCref[lane][2];
                 if (cx * cx + cy * cy + cz * cz > s.cl.cskin_half2) atomicOr(s.cl.rebuild, 1);
+                // displacement since the last prune of the lists
+                const float4 pr = s.cl.pref[sl];
+                const float px = ch.x - pr.x, py = ch.y - pr.y, pz = ch.z - pr.z;
+                if (px * px + py * py + pz * pz > s.cl.pdisp2) atomicOr(s.cl.prune, 1);
             }
         }
         s.vx[i] = vx;
@@ -1032,6 +1036,9 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
                 s.cl.splo[nxt][sl] = cw;
                 const double cx = x - s.cl.crefx[i], cy = y - s.cl.crefy[i], cz = z - s.cl.crefz[i];
                 if (cx * cx + cy * cy + cz * cz > s.cl.cskin_half2) atomicOr(s.cl.rebuild, 1);
+                const float4 pr = s.cl.pref[sl];
+                const float px = ch.x - pr.x, py = ch.y - pr.y, pz = ch.z - pr.z;
+                if (px * px + py * py + pz * pz > s.cl.pdisp2) atomicOr(s.cl.prune, 1);
             }
         }
         s.vx[i] = vx;

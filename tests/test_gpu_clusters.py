@@ -139,3 +139,30 @@ def test_thread_per_atom_step_kernel_is_bitwise(integrator, split):
     assert c1 == c2
     if integrator != "baoab":
         assert c1[0] > 100 and c1[1] > 0
+
+
+@pytest.mark.parametrize("pair_skin", [1.0, 2.0])
+def test_pruned_lists_after_a_run(pair_skin):
+    """After steps that moved the atoms (cluster lists built once or twice,
+    pruned again several times), the pair sums read the current pruned lists
+    and still hold every pair inside the cutoff: the full gradient at the
+    run's final state against the oracle's."""
+    build, cfg = CASES["box_14_coulomb_jumps"]
+    s = build()
+    cfg = dict(cfg, pair_skin=pair_skin)
+    ctx = bounce.from_system(s, seed=3, **cfg)
+    ctx.set_state(s.q, s.v, step=0)
+    ctx.run(60, bounce.BAOAB)
+    q, v = ctx.get_state()
+    p = Params(r_on=cfg["r_on"], r_off=cfg["r_off"], r_cut=cfg["r_cut"], ewald_beta=cfg["ewald_beta"], box=s.box,
+               lj_sigma=s.lj_sigma, lj_eps=s.lj_eps)
+    md = OracleMD(q, v, _topo(s), p, seed=3, skin=cfg["skin"], step=60)
+    md.ensure_rows()
+    g = ctx.gradient(bounce.GRAD_FULL)
+    ref = md.grad_full()
+    d = np.linalg.norm(g - ref, axis=1)
+    assert (d / md.grad_scale("full")).max() < TOL
+    assert np.percentile(d / np.linalg.norm(ref, axis=1), 99) < 2 * TOL
+    e = ctx.energies()
+    assert e["full_pairs"] > 0
+    ctx.close()

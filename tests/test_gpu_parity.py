@@ -560,7 +560,7 @@ def test_full_size_box_first_step_sampled(coulomb_jumps):
     """The 98,304-atom box in the split and launch configuration the
     benchmark times (Ewald erfc beta 0.35 and LJ within 9 A, SPME 96^3 of
     order 5, jumps beyond a 7.5-8.5 A switch with one bound per atom type,
-    row skin 2.5 A, cluster skin 1 A, thread-per-atom step kernel): one BOUNCE
+    row skin 2.5 A, cluster skin 2 A, thread-per-atom step kernel): one BOUNCE
     step through run().  The positions after it depend only on the starting
     state (B with F_0 and the reciprocal gradient, the first jump half-step,
     A O A), so the oracle's first half-step is computed for 3,000 sampled
@@ -574,7 +574,7 @@ def test_full_size_box_first_step_sampled(coulomb_jumps):
     s = water_box(32, seed=0)
     rng = np.random.default_rng(8)
     q0 = s.q + rng.normal(scale=0.05, size=s.q.shape)
-    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=2.5, pair_skin=1.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
+    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=2.5, pair_skin=2.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
                pme_order=5, max_neighbors=2048, jump_coulomb=coulomb_jumps)
     ctx = bounce.from_system(s, seed=13, **cfg)
     ctx.set_state(q0, s.v, step=0)
