@@ -75,10 +75,10 @@ WORKLOAD = ("BOUNCE-RESPA (SPME on the 2 fs outer step) vs BAOAB 1 fs, 32,768-mo
 # exponential) 22, LJ 6, both sides' accumulation 6, charge product 2; the
 # F_0 share adds the switching function and its weight (11).
 OPS_PER_PAIR = {"f0": 66, "full": 55}
-# DRAM traffic of one pair-kernel launch on this machine (ncu
-# dram__bytes_read.sum + dram__bytes_write.sum, BAOAB full pairs at the
-# lattice start), None until measured on the current kernel
-PAIR_TRAFFIC = None
+# DRAM traffic of one launch of the F_0 pair kernel on this machine (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of k_cl_pairs<3>, the
+# BOUNCE-RESPA part of `bench.py --profile box --steps 8`; cold caches)
+PAIR_TRAFFIC = 24.08e6 + 3.1e3
 
 
 def _peaks():

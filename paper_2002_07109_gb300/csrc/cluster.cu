@@ -410,8 +410,12 @@ __global__ void __launch_bounds__(256) k_cl_prune(DevSys s, Params p, int step_o
     for (int I = blockIdx.x * wpb + wl; I < ncl; I += gridDim.x * wpb) {
         __syncwarp();
         if (lane < CL) {
-            s_hi[wl][lane] = c.sphi[cur][I * CL + lane];
-            s_lo[wl][lane] = c.splo[cur][I * CL + lane];
+            // padding slots (no atom) are placed out of reach: their copies in
+            // the buffer the step kernel writes are never refreshed
+            const bool real = c.smol[I * CL + lane] >= 0;
+            const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            s_hi[wl][lane] = real ? c.sphi[cur][I * CL + lane] : far;
+            s_lo[wl][lane] = real ? c.splo[cur][I * CL + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             c.pref[I * CL + lane] = c.sphi[cur][I * CL + lane];
         }
         __syncwarp();

@@ -166,3 +166,24 @@ def test_pruned_lists_after_a_run(pair_skin):
     e = ctx.energies()
     assert e["full_pairs"] > 0
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["box_14_coulomb_jumps", "droplet_rc12"])
+def test_reused_context_repeats_a_fresh_one(name):
+    """set_state resets everything a run leaves behind (cluster lists and
+    their pruned copies, slot copies in both position buffers): a context
+    that ran 70 steps and is set back to the start follows the fresh
+    context's next 70 steps bit for bit."""
+    build, cfg = CASES[name]
+    s = build()
+    out = []
+    for warm in (0, 70):
+        ctx = bounce.from_system(s, seed=11, **cfg)
+        ctx.set_state(s.q, s.v, step=7)
+        if warm:
+            ctx.run(warm, bounce.BAOAB)
+            ctx.set_state(s.q, s.v, step=7)
+        ctx.run(70, bounce.BAOAB)
+        out.append(ctx.get_state())
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])

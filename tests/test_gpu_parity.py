@@ -153,6 +153,9 @@ def test_jump_half(name, stream_id):
 def test_one_step(name, integrator):
     s, ctx, md = _setup(name)
     q0 = md.q.copy()
+    # velocity error scale: |v| plus the kicks' own error scale (an atom
+    # nearly at rest carries the FP32 error of its kicks, not of |v|)
+    kscale = _kick_scale(md, "full" if integrator == "baoab" else "short", False)
     code = bounce.BOUNCE if integrator == "bounce" else bounce.BAOAB
     ctx.run(1, code)
     if integrator == "bounce":
@@ -166,7 +169,9 @@ def test_one_step(name, integrator):
     q, v = ctx.get_state()
     dq = np.linalg.norm(q - md.q, axis=1) / np.maximum(np.linalg.norm(md.q - q0, axis=1), 1e-6)
     assert dq[~tie].max() < TOL, dq[~tie].max()
-    assert _rel_err(v, md.v)[~tie].max() < TOL
+    dv = np.linalg.norm(v - md.v, axis=1)
+    assert (dv / (np.linalg.norm(md.v, axis=1) + kscale))[~tie].max() < TOL
+    assert np.percentile((dv / np.linalg.norm(md.v, axis=1))[~tie], 99) < 2 * TOL
     ctx.close()
 
 
@@ -182,20 +187,28 @@ def test_run_is_deterministic():
 
 
 def test_chunked_runs_equal_one_run():
-    """Graph-replayed chunks and direct launches follow one trajectory; split
-    runs differ only by the rounding of two half kicks against one kick."""
+    """Graph-replayed chunks and direct launches follow one trajectory bit
+    for bit: run(70) replays two captured 32-step chunks, the profiling
+    entry point launches the same 70 steps one boundary at a time.  A run
+    split at other boundaries (1 + 33 + 36 steps) differs first by the
+    rounding of two half kicks against one kick; with FP32 pair terms such
+    differences occasionally move a term by one unit in the last place and
+    then grow with the divergence of nearby trajectories, so that comparison
+    takes a bound of 1e-5 A on positions and 1e-5 A/fs on velocities (the
+    rms speed is ~1e-2 A/fs) after 70 steps."""
     s, ctx, md = _setup("droplet_cutoff")
     ctx.run(70, bounce.BAOAB)
     q1, v1 = ctx.get_state()
     ctx.set_state(md.q, md.v, step=7)
+    ctx.profile_steps(70, bounce.BAOAB)
+    q3, v3 = ctx.get_state()
+    assert np.array_equal(q1, q3) and np.array_equal(v1, v3)
+    ctx.set_state(md.q, md.v, step=7)
     for n in (1, 33, 36):
         ctx.run(n, bounce.BAOAB)
     q2, v2 = ctx.get_state()
-    assert np.allclose(q1, q2, rtol=0, atol=1e-5) and np.allclose(v1, v2, rtol=1e-4, atol=1e-7)
-    ctx.set_state(md.q, md.v, step=7)
-    ctx.run(70, bounce.BAOAB)
-    q3, v3 = ctx.get_state()
-    assert np.array_equal(q1, q3) and np.array_equal(v1, v3)
+    dq, dv = np.abs(q1 - q2).max(), np.abs(v1 - v2).max()
+    assert dq < 1e-5 and dv < 1e-5, (dq, dv)
     ctx.close()
 
 

@@ -154,8 +154,9 @@ def test_mean_kick_first_order():
 @pytest.mark.slow
 def test_two_atom_boltzmann_marginal():
     """Bond in F_0, Coulomb-like repulsion entirely on jumps: the sampled mean
-    r matches r^2 exp(-beta(U_b + W)) by quadrature; with the jump sign
-    flipped it would sample exp(+beta W) and fail."""
+    r matches r^2 exp(-beta(U_b + W)) by quadrature (with the jump sign
+    flipped it would sample exp(+beta W) and fail), and the velocity
+    marginal is Maxwellian (unit variance and kurtosis 3 per component)."""
     nrep = 96
     kq, r0, kb = 0.25, 3.0, 2.0
     q = np.zeros((2 * nrep, 3))
@@ -171,13 +172,24 @@ def test_two_atom_boltzmann_marginal():
     rng = np.random.default_rng(0)
     v = rng.standard_normal(q.shape) * math.sqrt(KB * 300 * ACCEL / 10.0)
     md = OracleMD(q, v, topo, p, seed=4, gamma=0.01, dt=1.0, skin=10.0)
-    rs = []
+    rs, vs = [], []
     for k in range(2500):
         md.step_bounce()
         if k >= 300 and k % 5 == 0:
             d = md.q[0::2] - md.q[1::2]
             rs.append(np.linalg.norm(d, axis=1))
+            vs.append(md.v / math.sqrt(KB * 300 * ACCEL / 10.0))
     rs = np.array(rs)
+    # the velocity marginal stays Maxwellian (each reflection keeps |v|; a
+    # biased thinning or a reflection that changed |v| would heat or cool):
+    # unit variance and kurtosis 3 per component, errors from 20 blocks
+    z = np.array(vs)
+    zb = z[: len(z) // 20 * 20].reshape(20, -1)
+    var_b = (zb ** 2).mean(1)
+    kurt_b = (zb ** 4).mean(1) / var_b ** 2
+    for stat, ref in ((var_b, 1.0), (kurt_b, 3.0)):
+        se_s = stat.std(ddof=1) / math.sqrt(len(stat))
+        assert abs(stat.mean() - ref) < max(4 * se_s, 0.01 * ref), (stat.mean(), ref, se_s)
     beta = 1.0 / (KB * 300.0)
     x = np.linspace(0.9, 8.0, 400001)
     U = kb * (x - r0) ** 2 + 332.063713 * kq / x
