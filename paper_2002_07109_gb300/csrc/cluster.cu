@@ -392,6 +392,36 @@ __global__ void __launch_bounds__(256) k_cl_search(DevSys s, Params p, int step_
     }
 }
 
+// Whether list entry `ent` (high part hj of the j atom's slot copy) lies
+// within sqrt(R2) of some atom of the cluster in shi/slo: high parts with the
+// entry's periodic image (their rounding is far below the radius's margin),
+// or the per-pair minimum image from the split positions (rare).
+__device__ __forceinline__ bool prune_keep(const DevSys& s, const Params& p, int cur, int ent, float4 hj,
+                                           const float4* shi, const float4* slo, float R2) {
+    const DevClu& c = s.cl;
+    const int sj = ent & 0x07FFFFFF, code = (int)((uint32_t)ent >> 27);
+    float best = INFINITY;
+    if (code == PER_PAIR) {
+        const float4 lj = c.splo[cur][sj];
+        for (int a = 0; a < CL; ++a) {
+            const float3 d = pair_disp(p, shi[a], slo[a], hj, lj);
+            best = fminf(best, d.x * d.x + d.y * d.y + d.z * d.z);
+        }
+    } else {
+        if (code != NO_SHIFT) {
+            hj.x -= (float)(code / 9 - 1) * p.Lhi[0];
+            hj.y -= (float)((code / 3) % 3 - 1) * p.Lhi[1];
+            hj.z -= (float)(code % 3 - 1) * p.Lhi[2];
+        }
+#pragma unroll
+        for (int a = 0; a < CL; ++a) {
+            const float dx = shi[a].x - hj.x, dy = shi[a].y - hj.y, dz = shi[a].z - hj.z;
+            best = fminf(best, dx * dx + dy * dy + dz * dz);
+        }
+    }
+    return best < R2;
+}
+
 // 5. pruned lists (warp per cluster I), gated by the prune flag: the
 // entries of each list whose atom j lies within the prune radius of at least
 // one atom of I at the current positions (same images as the pair kernel;
@@ -424,42 +454,22 @@ __global__ void __launch_bounds__(256) k_cl_prune(DevSys s, Params p, int step_o
             const int* src = c.lst[L] + (size_t)I * c.capj[L];
             int* dst = c.plst[L] + (size_t)I * c.capj[L];
             int m = 0;
-            for (int e0 = 0; e0 < n; e0 += 32) {
-                const int e = e0 + lane;
-                bool keep = false;
-                int ent = 0;
-                if (e < n) {
-                    ent = src[e];
-                    const int sj = ent & 0x07FFFFFF, code = (int)((uint32_t)ent >> 27);
-                    float4 hj = c.sphi[cur][sj], lj = c.splo[cur][sj];
-                    if (code != NO_SHIFT && code != PER_PAIR) {
-                        const float kx = (float)(code / 9 - 1), ky = (float)((code / 3) % 3 - 1),
-                                    kz = (float)(code % 3 - 1);
-                        shift_split(hj.x, lj.x, kx * p.Lhi[0], kx * p.Llo[0]);
-                        shift_split(hj.y, lj.y, ky * p.Lhi[1], ky * p.Llo[1]);
-                        shift_split(hj.z, lj.z, kz * p.Lhi[2], kz * p.Llo[2]);
-                    }
-                    float best = INFINITY;
-                    if (code == PER_PAIR) {
-                        for (int a = 0; a < CL; ++a) {
-                            const float3 d = pair_disp(p, s_hi[wl][a], s_lo[wl][a], hj, lj);
-                            best = fminf(best, d.x * d.x + d.y * d.y + d.z * d.z);
-                        }
-                    } else {
-                        // high parts suffice here: the radius carries a margin far
-                        // above their rounding (the low parts are below 1e-5 A)
-#pragma unroll
-                        for (int a = 0; a < CL; ++a) {
-                            const float dx = s_hi[wl][a].x - hj.x, dy = s_hi[wl][a].y - hj.y,
-                                        dz = s_hi[wl][a].z - hj.z;
-                            best = fminf(best, dx * dx + dy * dy + dz * dz);
-                        }
-                    }
-                    keep = best < c.prs2[L];
-                }
-                const uint32_t bk = __ballot_sync(0xffffffffu, keep);
-                if (keep) dst[m + __popc(bk & below)] = ent;
-                m += __popc(bk);
+            const float R2 = c.prs2[L];
+            // two passes of 32 entries per iteration: their loads are in flight together
+            for (int e0 = 0; e0 < n; e0 += 64) {
+                // (an entry's image code fills its top bits: validity comes from the index)
+                const int ea = e0 + lane, eb = ea + 32;
+                const bool va = ea < n, vb = eb < n;
+                const int enta = va ? src[ea] : 0, entb = vb ? src[eb] : 0;
+                const float4 ha = va ? c.sphi[cur][enta & 0x07FFFFFF] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 hb = vb ? c.sphi[cur][entb & 0x07FFFFFF] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool ka = va && prune_keep(s, p, cur, enta, ha, s_hi[wl], s_lo[wl], R2);
+                const bool kb = vb && prune_keep(s, p, cur, entb, hb, s_hi[wl], s_lo[wl], R2);
+                const uint32_t ba = __ballot_sync(0xffffffffu, ka), bb = __ballot_sync(0xffffffffu, kb);
+                if (ka) dst[m + __popc(ba & below)] = enta;
+                m += __popc(ba);
+                if (kb) dst[m + __popc(bb & below)] = entb;
+                m += __popc(bb);
             }
             if (lane == 0) {
                 c.pcnt[L][I] = m;
