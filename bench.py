@@ -26,10 +26,10 @@ Protocol (our arm):
   * per-kernel breakdown and the roofline of the pair kernel (the dominant
     kernel) from CUDA events around each group of launches
     (bounce_profile_breakdown) over 24 steps of the same trajectory;
-  * matched observables: four independent runs per arm (own Philox seeds)
+  * matched observables: eight independent runs per arm (own Philox seeds)
     from the relaxed box, 1.2 ps each to decorrelate, then 4.8 ps sampled every
     0.24 ps: potential energy per molecule, kinetic temperature, O-O g(r) and
-    O self-diffusion; standard errors from the spread of the four runs; a
+    O self-diffusion; standard errors from the spread of the eight runs; a
     second BAOAB arm with other seeds is the null control, BAOAB at 0.5 fs
     shows the comparator's own step-size error, and BOUNCE-RESPA without
     jumps (switch at the cutoff) separates the RESPA split from the jumps;
@@ -399,10 +399,13 @@ def _mean_se(x):
     return x.mean(0), x.std(0, ddof=1) / math.sqrt(len(x))
 
 
-def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=4, decor=1200, prod=4800, every=240):
-    """Four independent runs per arm from the relaxed box (own Philox
+def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=8, decor=1200, prod=4800, every=240):
+    """Eight independent runs per arm from the relaxed box (own Philox
     seeds): `decor` steps, then `prod` steps sampled every `every` steps
-    (all multiples of every arm's outer step).
+    (all multiples of every arm's outer step).  Eight runs, so that the
+    per-bin standard errors of g(r) taken from the spread of the runs are
+    themselves stable (with four runs a few bins get a small error estimate
+    by chance and dominate the chi^2 even between two BAOAB arms).
     Per run: mean potential energy per molecule, mean kinetic temperature,
     O-O pair-distance histogram (0-8 A, 0.1 A bins) as g(r), and the O
     self-diffusion D from the mean squared displacement over the production
@@ -579,10 +582,19 @@ def batched_replicas(bounce, device, stream, sh, rank, n_steps=10000, n_baoab=10
         sec = a.elapsed_time(b) / 1e3
         e = ctx.energies(stream=sh)
         ctx.close()
+        # the tile pair kernel's roofline: every pair of different molecules
+        # of each replica once, at the algorithmic lane-operations per pair
+        n_pairs = float(sum(9 * int(m) * (int(m) - 1) // 2 for m in sizes))
+        ops = OPS_PER_PAIR["f0" if integ != bounce.BAOAB else "full"]
+        ach = n_pairs * ops / (tune["pair_ms"] / 1e3) / 1e12
+        peak = 152 * 128 * 2070e6 / 1e12
         out[name] = {"steps": steps, "aggregate_ns_per_day": round(256 * ns_per_day(steps, sec), 2),
                      "replica_steps_per_s": round(256 * steps / sec, 1), "ms_per_step": round(sec * 1e3 / steps, 4),
                      "tuning": {"tile_j": tune["tile_j"], "tile_blocks": tune["tile_blocks"],
                                 "pair_kernel_ms": round(tune["pair_ms"], 4)},
+                     "pair_kernel_roofline": {"bound": "alu", "pairs_per_launch": n_pairs, "achieved": round(ach, 3),
+                                              "peak": round(peak, 3), "unit": "Tops/s", "frac": round(ach / peak, 4),
+                                              "peak_source": "152 SMs x 128 lanes x 2,070 MHz (max SM clock)"},
                      "temperature_end_K": round(e["temperature"], 1)}
     return out
 
