@@ -916,28 +916,82 @@ __device__ __forceinline__ void jump_thread(const DevSys& s, const Params& p, in
     }
 }
 
+// The jump half-steps of the CTA's atoms that can propose (type with L* >
+// 0), taken by the CTA's first threads after a compaction, so that the
+// warps whose atoms have no jump part skip the FP64 set-up as a whole while
+// every other phase keeps one thread per atom in atom order (coalesced).
+// v: the CTA's velocities in shared memory (read and updated in place).
+#ifndef LITE_JUMP_INLINE
+#define LITE_JUMP_INLINE 1
+#endif
+#if LITE_JUMP_INLINE
+__device__ __forceinline__
+#else
+__device__ __noinline__
+#endif
+void jump_phase_lite(const DevSys& s, const Params& p, int cur, long long step,
+                                                uint32_t stream, const short* act, int nact, double (*v)[256],
+                                                int& nprop, int& nacc, int& near) {
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+        const int j = act[k];
+        const int i = blockIdx.x * blockDim.x + j;
+        const float4 ahi = s.phi[cur][i], alo = s.plo[cur][i];
+        float dx, dy, dz;
+        jump_thread(s, p, cur, i, s.type[i], v[0][j], v[1][j], v[2][j], step, stream, ahi, alo, dx, dy, dz, nprop,
+                    nacc, near);
+        v[0][j] += (double)dx;
+        v[1][j] += (double)dy;
+        v[2][j] += (double)dz;
+    }
+}
+
+// Resident CTAs per SM the thread-per-atom kernel is compiled for: three
+// fit the 98,304-atom box's 384 CTAs in one wave (the register cap costs a
+// few spills around the jump phases, less than a second wave).
+#ifndef LITE_MIN_CTAS
+#define LITE_MIN_CTAS 3
+#endif
+
 template <int BOUNCE>
-__global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int variant, int step_off, double hr, int ext,
-                                                   double hout) {
+__global__ void __launch_bounds__(256, LITE_MIN_CTAS) k_step_lite(DevSys s, Params p, int variant, int step_off,
+                                                                  double hr, int ext, double hout) {
     __shared__ unsigned long long cnt[4];
+    __shared__ double sv[3][256];   // velocities between the phases (jump steps)
+    __shared__ short sact[256];     // CTA-local indices of the atoms that can propose
+    __shared__ int swc[8];          // per-warp counts of those atoms
     chain_enter();
     if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < s.n;
     int nprop = 0, nacc = 0, near = 0;
-    if (t < s.n) {
-        // atoms that can propose first (act_order): whole warps of atoms
-        // without a jump bound then skip the FP64 set-up of the jump step
-        const int i = (BOUNCE && s.act_order) ? s.act_order[t] : t;
-        const long long step = *s.step_base + step_off;
-        const int cur = (int)(step & 1), nxt = cur ^ 1;
-        const bool do_j2 = BOUNCE && variant != 0;
-        const bool do_j1 = BOUNCE && variant != 2;
-        const bool do_aoa = variant != 2;
-        const double hk = variant == 1 ? p.dt : 0.5 * p.dt;
-        // pair sums of the pair kernel (absent between the outer kicks of the extended splits)
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-        int sl = i;
+    const long long step = *s.step_base + step_off;
+    const int cur = (int)(step & 1), nxt = cur ^ 1;
+    const bool do_j2 = BOUNCE && variant != 0;
+    const bool do_j1 = BOUNCE && variant != 2;
+    const bool do_aoa = variant != 2;
+    const double hk = variant == 1 ? p.dt : 0.5 * p.dt;
+    // compaction of the atoms that can propose (in atom order: deterministic)
+    int nact = 0;
+    if (BOUNCE) {
+        const bool act = live && p.Lstar_d[s.type[i]] != 0.0;
+        const uint32_t bal = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) swc[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            off += w < wid ? swc[w] : 0;
+            nact += swc[w];
+        }
+        if (act) sact[off + __popc(bal & ((1u << lane) - 1u))] = (short)threadIdx.x;
+    }
+    __syncthreads();
+    // pair sums of the pair kernel (absent between the outer kicks of the extended splits)
+    float gx = 0.f, gy = 0.f, gz = 0.f, Gx = 0.f, Gy = 0.f, Gz = 0.f;
+    int sl = i;
+    float4 ahi = make_float4(0.f, 0.f, 0.f, 0.f), alo = ahi;
+    double kick = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
+    if (live) {
         if (s.cl.on) sl = s.cl.a2s[i];
         if (!(ext && hout == 0.0)) {
             const size_t ns = s.cl.on ? (size_t)s.cl.ncol * s.cl.maxcl * BOUNCE_CL : (size_t)s.n;
@@ -949,7 +1003,9 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
             acc[ns + sl] = 0ull;
             acc[2 * ns + sl] = 0ull;
         }
-        float Gx = ext ? 0.f : gx, Gy = ext ? 0.f : gy, Gz = ext ? 0.f : gz;
+        Gx = ext ? 0.f : gx;
+        Gy = ext ? 0.f : gy;
+        Gz = ext ? 0.f : gz;
         // bonded terms of the atom, in list order
         float bx = 0.f, by = 0.f, bz = 0.f;
         for (int t = s.bt_off[i]; t < s.bt_off[i + 1]; ++t) {
@@ -961,18 +1017,25 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
         Gx += bx;
         Gy += by;
         Gz += bz;
-        const float4 ahi = s.phi[cur][i], alo = s.plo[cur][i];
-        const int ti = s.type[i];
-        const double kick = s.kick[i];
-        double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
-        float dx, dy, dz;
-        if (do_j2) {
-            jump_thread(s, p, cur, i, ti, vx, vy, vz, step - 1, BOUNCE_STREAM_J2, ahi, alo, dx, dy, dz, nprop, nacc,
-                        near);
-            vx += (double)dx;
-            vy += (double)dy;
-            vz += (double)dz;
-        }
+        ahi = s.phi[cur][i];
+        alo = s.plo[cur][i];
+        kick = s.kick[i];
+        vx = s.vx[i];
+        vy = s.vy[i];
+        vz = s.vz[i];
+    }
+    if (do_j2) {
+        sv[0][threadIdx.x] = vx;
+        sv[1][threadIdx.x] = vy;
+        sv[2][threadIdx.x] = vz;
+        __syncthreads();
+        jump_phase_lite(s, p, cur, step - 1, BOUNCE_STREAM_J2, sact, nact, sv, nprop, nacc, near);
+        __syncthreads();
+        vx = sv[0][threadIdx.x];
+        vy = sv[1][threadIdx.x];
+        vz = sv[2][threadIdx.x];
+    }
+    if (live) {
         const double c = hk * kick;
         vx -= c * (double)Gx;
         vy -= c * (double)Gy;
@@ -989,12 +1052,20 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
             vy -= co * (double)gy;
             vz -= co * (double)gz;
         }
-        if (do_j1) {
-            jump_thread(s, p, cur, i, ti, vx, vy, vz, step, BOUNCE_STREAM_J1, ahi, alo, dx, dy, dz, nprop, nacc, near);
-            vx += (double)dx;
-            vy += (double)dy;
-            vz += (double)dz;
-        }
+    }
+    if (do_j1) {
+        __syncthreads();  // the J2 phase's reads of sv are done
+        sv[0][threadIdx.x] = vx;
+        sv[1][threadIdx.x] = vy;
+        sv[2][threadIdx.x] = vz;
+        __syncthreads();
+        jump_phase_lite(s, p, cur, step, BOUNCE_STREAM_J1, sact, nact, sv, nprop, nacc, near);
+        __syncthreads();
+        vx = sv[0][threadIdx.x];
+        vy = sv[1][threadIdx.x];
+        vz = sv[2][threadIdx.x];
+    }
+    if (live) {
         if (do_aoa) {
             const double h = 0.5 * p.dt;
             double x = s.qx[cur][i] + h * vx, y = s.qy[cur][i] + h * vy, z = s.qz[cur][i] + h * vz;
@@ -1049,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_step_lite(DevSys s, Params p, int varia
         nprop = warp_sum_i(nprop);
         nacc = warp_sum_i(nacc);
         near = warp_sum_i(near);
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             if (nprop) atomicAdd(&cnt[0], (unsigned long long)nprop);
             if (nacc) atomicAdd(&cnt[1], (unsigned long long)nacc);
             if (near) atomicAdd(&cnt[2], (unsigned long long)near);
