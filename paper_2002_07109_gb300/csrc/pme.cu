@@ -475,6 +475,66 @@ __global__ void __launch_bounds__(256) k_pme_fft_w(DevPme m, int axis, float sig
     }
 }
 
+// The same transform for four neighbouring lines of a strided axis (axis 0
+// or 1: lines l..l+3 are neighbours along the contiguous axis), one warp for
+// all four: each lane loads and stores 32 contiguous bytes (four complex
+// values) per point instead of 8, so the strided passes use whole sectors.
+template <int M>
+__global__ void __launch_bounds__(256) k_pme_fft_w4(DevPme m, int axis, float sign) {
+    constexpr int K = 32 * M;
+    __shared__ float2 tw[K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)K, &sn, &cs);
+        tw[k] = make_float2(cs, sign * sn);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int ngroups = (int)((size_t)m.K[0] * m.K[1] * m.K[2] / K / 4);
+    const size_t stride = axis == 1 ? (size_t)m.K[2] : (size_t)m.K[1] * m.K[2];
+    const int rev = (int)(__brev((unsigned)lane) >> 27);
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < ngroups; g += gridDim.x * (blockDim.x >> 5)) {
+        const int l = 4 * g;
+        const size_t b0 = axis == 1 ? (size_t)(l / m.K[2]) * m.K[1] * m.K[2] + (l % m.K[2]) : (size_t)l;
+        float2 v[4][M > 1 ? M : 2];
+#pragma unroll
+        for (int n1 = 0; n1 < M; ++n1) {
+            const float4* src = reinterpret_cast<const float4*>(m.cgrid + b0 + (size_t)(32 * n1 + lane) * stride);
+            const float4 a = src[0], b = src[1];
+            v[0][n1] = make_float2(a.x, a.y);
+            v[1][n1] = make_float2(a.z, a.w);
+            v[2][n1] = make_float2(b.x, b.y);
+            v[3][n1] = make_float2(b.z, b.w);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (M > 1) small_dft(v[q], M, sign);
+#pragma unroll
+            for (int k1 = 1; k1 < M; ++k1) v[q][k1] = cmul(v[q][k1], tw[(lane * k1) % K]);
+        }
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) {
+            const bool low = (lane & sh) != 0;
+            const float2 w = tw[(lane & (sh - 1)) * (K / (2 * sh))];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1) {
+                    float2 b;
+                    b.x = __shfl_xor_sync(0xffffffffu, v[q][k1].x, sh);
+                    b.y = __shfl_xor_sync(0xffffffffu, v[q][k1].y, sh);
+                    v[q][k1] = low ? cmul(csub(b, v[q][k1]), w) : cadd(v[q][k1], b);
+                }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) {
+            float4* dst = reinterpret_cast<float4*>(m.cgrid + b0 + (size_t)(k1 + M * rev) * stride);
+            dst[0] = make_float4(v[0][k1].x, v[0][k1].y, v[1][k1].x, v[1][k1].y);
+            dst[1] = make_float4(v[2][k1].x, v[2][k1].y, v[3][k1].x, v[3][k1].y);
+        }
+    }
+}
+
 __global__ void k_pme_energy_sum(DevPme m, int nparts, int n, double* out) {
     __shared__ double red[2][256];
     double a = 0.0, b = 0.0;
@@ -518,7 +578,17 @@ void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off,
         FftPlan pl;
         const int K = m.K[axis], Mw = K / 32, nl = lines[axis];
         const int wb = std::min((nl + 7) / 8, 152 * 8);
-        if (K % 32 == 0 && Mw >= 1 && Mw <= 5) {
+        // four lines per warp along a strided axis (lines grouped by four
+        // along the contiguous axis, 32-byte aligned)
+        const bool four = axis != 2 && m.K[2] % 4 == 0;
+        const int wb4 = std::min((nl / 4 + 7) / 8, 152 * 8);
+        if (four && K % 32 == 0 && Mw >= 1 && Mw <= 5) {
+            if (Mw == 1) k_pme_fft_w4<1><<<wb4, 256, 0, st>>>(m, axis, sign);
+            else if (Mw == 2) k_pme_fft_w4<2><<<wb4, 256, 0, st>>>(m, axis, sign);
+            else if (Mw == 3) k_pme_fft_w4<3><<<wb4, 256, 0, st>>>(m, axis, sign);
+            else if (Mw == 4) k_pme_fft_w4<4><<<wb4, 256, 0, st>>>(m, axis, sign);
+            else k_pme_fft_w4<5><<<wb4, 256, 0, st>>>(m, axis, sign);
+        } else if (K % 32 == 0 && Mw >= 1 && Mw <= 5) {
             if (Mw == 1) k_pme_fft_w<1><<<wb, 256, 0, st>>>(m, axis, sign);
             else if (Mw == 2) k_pme_fft_w<2><<<wb, 256, 0, st>>>(m, axis, sign);
             else if (Mw == 3) k_pme_fft_w<3><<<wb, 256, 0, st>>>(m, axis, sign);
