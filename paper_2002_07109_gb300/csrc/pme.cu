@@ -8,10 +8,12 @@
 //             fixed-point grid (2^40 scale), so the grid is bit-identical
 //             whatever the atomic order;
 //   load      fixed point -> FP32 complex grid; clears the int64 grid;
-//   fft x3    forward transform along each axis: batched mixed-radix
-//             (4, 2, 3, 5) Stockham FFT of 16 lines per CTA in shared memory
-//             (K log K work per line, FP32); grid sizes with another prime
-//             factor take a direct sum per line instead (K^2 work);
+//   fft x3    forward transform along each axis (K log K work per line,
+//             FP32): lines of 32 M points (M <= 5) in registers, one warp
+//             per line (four neighbouring lines per warp along the strided
+//             axes); other lengths a batched mixed-radix (4, 2, 3, 5)
+//             Stockham FFT of 16 lines per CTA in shared memory; grid sizes
+//             with another prime factor a direct sum per line (K^2 work);
 //   convolve  multiply by the influence function B(m) C(m) (FP32 table made
 //             on the host in FP64) and accumulate the energy partials
 //             sum B C |F(Q)|^2 per CTA (FP64);
