@@ -28,7 +28,7 @@
 // cutoff is evaluated once (Newton's third law): the j-side sum of a lane is
 // added once per item, the i-side sums are reduced over the warp at the end
 // of the item, both into int64 fixed-point accumulators (2^-32 kcal/mol/A)
-// converted from FP32 with integer operations: integer addition is
+// rounded from FP32 by the int64 conversion: integer addition is
 // associative, so the result does not depend on the order in which warps
 // finish.
 #include <cstdint>
@@ -492,24 +492,8 @@ __global__ void __launch_bounds__(256) k_cl_prune(DevSys s, Params p, int step_o
     if (threadIdx.x == 0) *c.prune = 0;
 }
 
-// round(v 2^32) as a 64-bit integer from the bits of the FP32 value, with
-// integer operations only (|v| < 2^31; halves round away from zero): the
-// significand shifted by (exponent - 118).
-__device__ __forceinline__ unsigned long long f2fix(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xFFu);
-    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int sh = min(e - 118, 38);  // saturates at |v| = 2^31 (a blown-up state)
-    unsigned long long r;
-    if (e == 0) r = 0ull;
-    else if (sh >= 0) r = m << sh;
-    else if (sh > -25) r = (m + (1ull << (-sh - 1))) >> (-sh);
-    else r = 0ull;
-    return (b & 0x80000000u) ? (unsigned long long)(-(long long)r) : r;
-}
-
 __device__ __forceinline__ void fix_add(unsigned long long* a, float v) {
-    if (v != 0.f) atomicAdd(a, f2fix(v));
+    if (v != 0.f) atomicAdd(a, fix_round<32>(v));
 }
 
 // Exact FP64 cutoff test of one pair near r_c, out of line (rare).

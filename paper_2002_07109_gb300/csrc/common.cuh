@@ -518,6 +518,18 @@ __device__ __forceinline__ bool inside_cut(const DevSys& s, const Params& p, int
 
 __device__ __forceinline__ int type_of(float4 lo) { return __float_as_int(lo.w); }
 
+// round(v 2^S) as a two's-complement 64-bit integer for the fixed-point
+// accumulators: the FP32 product with 2^S is exact, the conversion rounds to
+// nearest (ties to even); |v| is clamped to 2^(63 - S), where the conversion
+// would saturate.  Integer sums of these do not depend on the order of the
+// additions.
+template <int S>
+__device__ __forceinline__ unsigned long long fix_round(float v) {
+    constexpr float scale = (float)(1ull << S);
+    constexpr float vmax = (float)(1ull << (63 - S));
+    return (unsigned long long)__float2ll_rn(fminf(fmaxf(v, -vmax), vmax) * scale);
+}
+
 __device__ __forceinline__ float warp_sum_f(float x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

@@ -69,21 +69,6 @@ __device__ __forceinline__ void frac_coord(double x, double iL, int K, int& fl, 
     if (fl >= K) fl -= K;
 }
 
-// round(v 2^40) as a 64-bit integer from the bits of the FP32 value, with
-// integer operations only (|v| < 2^23; halves round away from zero).
-__device__ __forceinline__ unsigned long long fix40(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xFFu);
-    const unsigned long long mant = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int sh = min(e - 110, 38);  // v 2^40 = mant 2^(e - 150 + 40)
-    unsigned long long r;
-    if (e == 0) r = 0ull;
-    else if (sh >= 0) r = mant << sh;
-    else if (sh > -25) r = (mant + (1ull << (-sh - 1))) >> (-sh);
-    else r = 0ull;
-    return (b & 0x80000000u) ? (unsigned long long)(-(long long)r) : r;
-}
-
 template <int n>
 __global__ void k_pme_spread(DevSys s, DevPme m, int step_off) {
     const int cur = (int)((*s.step_base + step_off) & 1);
@@ -110,7 +95,7 @@ __global__ void k_pme_spread(DevSys s, DevPme m, int step_off) {
                 const float qab = qa * w[1][b];
                 const size_t row = ((size_t)ig[0][a] * m.K[1] + ig[1][b]) * m.K[2];
 #pragma unroll
-                for (int c = 0; c < n; ++c) atomicAdd(&m.qgrid[row + ig[2][c]], fix40(qab * w[2][c]));
+                for (int c = 0; c < n; ++c) atomicAdd(&m.qgrid[row + ig[2][c]], fix_round<40>(qab * w[2][c]));
             }
         }
     }

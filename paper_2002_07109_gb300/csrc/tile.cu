@@ -13,29 +13,16 @@
 // summed once (Newton's third law): the i side in the lane's registers, the j
 // side in a register that moves to the next lane after every sub-step, so
 // that after 32 sub-steps lane l holds the sum of atom l of the stage; both
-// go to int64 fixed-point accumulators (2^-32 kcal/mol/A) converted from FP32
-// with integer operations, so the result does not depend on the order in
+// go to int64 fixed-point accumulators (2^-32 kcal/mol/A) rounded from FP32
+// by the int64 conversion, so the result does not depend on the order in
 // which warps finish.  The j-block length tj is chosen by the autotuner
 // (bounce_autotune).
 #include "common.cuh"
 
 namespace {
 
-__device__ __forceinline__ unsigned long long tl_fix(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xFFu);
-    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int sh = min(e - 118, 38);  // round(v 2^32); saturates at |v| = 2^31
-    unsigned long long r;
-    if (e == 0) r = 0ull;
-    else if (sh >= 0) r = m << sh;
-    else if (sh > -25) r = (m + (1ull << (-sh - 1))) >> (-sh);
-    else r = 0ull;
-    return (b & 0x80000000u) ? (unsigned long long)(-(long long)r) : r;
-}
-
 __device__ __forceinline__ void tl_add(unsigned long long* a, float v) {
-    if (v != 0.f) atomicAdd(a, tl_fix(v));
+    if (v != 0.f) atomicAdd(a, fix_round<32>(v));
 }
 
 template <int PART>
