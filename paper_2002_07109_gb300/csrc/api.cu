@@ -634,8 +634,8 @@ int setup_clusters(bounce_ctx* c, const double* q) {
         if ((r = dalloc(c, &nk.col_atoms, n)) || (r = dalloc(c, &nk.atom_col, n)) || (r = dalloc(c, &nk.a2s, n)) ||
             (r = dalloc(c, &nk.crefx, n)) || (r = dalloc(c, &nk.crefy, n)) || (r = dalloc(c, &nk.crefz, n)) ||
             (r = dalloc(c, &nk.cofx, n)) || (r = dalloc(c, &nk.cofy, n)) || (r = dalloc(c, &nk.cofz, n)) ||
-            (r = dalloc(c, &nk.rebuild, 1)) || (r = dalloc(c, &nk.done_ctr, 3)) || (r = dalloc(c, &nk.prune, 1)) ||
-            (r = dalloc(c, &nk.pnitems, 4)))
+            (r = dalloc(c, &nk.rebuild, 1)) || (r = dalloc(c, &nk.done_ctr, 4)) || (r = dalloc(c, &nk.prune, 1)) ||
+            (r = dalloc(c, &nk.pnitems, 6)))
             return r;
         c->cl_atoms_alloc = true;
     }
@@ -666,6 +666,7 @@ int setup_clusters(bounce_ctx* c, const double* q) {
         if ((r = dalloc(c, &nk.pitems[0], nk.capitems)) || (r = dalloc(c, &nk.pitems[1], nk.capitems))) return r;
         c->cl_cap_items = nk.capitems;
     }
+    prepare_cluster_pairs();
     k = nk;
     return BOUNCE_OK;
 }

@@ -31,6 +31,7 @@
 // rounded from FP32 by the int64 conversion: integer addition is
 // associative, so the result does not depend on the order in which warps
 // finish.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -598,7 +599,13 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
     const float4* sphi = c.sphi[cur];
     const float4* splo = c.splo[cur];
     int npair = 0;
-    for (int it = blockIdx.x * 8 + wl; it < nit; it += gridDim.x * 8) {
+    // items are fetched from a counter, so that no warp idles while its
+    // CTA's other warps still work (the items differ in length)
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&c.pnitems[4 + L], 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nit) break;
         const int2 w = c.pitems[L][it];
         const int I = w.x, e1 = min(w.y + EPW, lcnt[I]);
         __syncwarp();
@@ -654,6 +661,8 @@ __global__ void __launch_bounds__(256, CL_PAIRS_MIN_CTAS) k_cl_pairs(DevSys s, P
     }
     npair = warp_sum_i(npair);
     if (lane == 0 && npair) atomicAdd(&s.cnt[PART == 3 ? CNT_SHORT_PAIRS : CNT_FULL_PAIRS], (unsigned long long)npair);
+    // every warp has seen the counter past the last item: the last CTA resets it
+    if (cl_last_cta(&c.done_ctr[3]) && threadIdx.x == 0) c.pnitems[4 + L] = 0;
 }
 
 // The accumulated pair sums of every atom added to out (n x 3, FP64), and
@@ -684,10 +693,29 @@ void launch_cluster_rebuild(const DevSys& s, const Params& p, int step_off, bool
     launch_chained(k_cl_prune, std::min((ncl + 7) / 8, 152 * 8), 256, 0, st, s, p, step_off, f);
 }
 
+// CTAs of the pair kernel that fit on the GPU at once (the warps fetch their
+// work items, so one resident wave covers any number of items)
+template <int PART>
+static int cl_pairs_grid() {
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cl_pairs<PART>, 256, 0);
+        blocks = std::max(1, sms * std::max(per, 1));
+    }
+    return blocks;
+}
+
+void prepare_cluster_pairs() {
+    cl_pairs_grid<3>();
+    cl_pairs_grid<5>();
+}
+
 void launch_cluster_pairs(const DevSys& s, const Params& p, int step_off, int part, int list, cudaStream_t st) {
-    const int blocks = 152 * 6;  // resident grid; warps stride over the work items
-    if (part == 3) launch_chained(k_cl_pairs<3>, blocks, 256, 0, st, s, p, step_off, list);
-    else launch_chained(k_cl_pairs<5>, blocks, 256, 0, st, s, p, step_off, list);
+    if (part == 3) launch_chained(k_cl_pairs<3>, cl_pairs_grid<3>(), 256, 0, st, s, p, step_off, list);
+    else launch_chained(k_cl_pairs<5>, cl_pairs_grid<5>(), 256, 0, st, s, p, step_off, list);
 }
 
 void launch_cluster_collect(const DevSys& s, double* out, cudaStream_t st) {

@@ -74,13 +74,14 @@ struct DevClu {
     double* cofy;            //     the slot copies keep q - cof until the next build, so that the
     double* cofz;            //     image codes of the lists stay valid when atoms cross a face
     int* rebuild;            // 1 = the clusters must be rebuilt before the next pair sums
-    unsigned int* done_ctr;  // [3] finished-CTA counters (zero between launches)
+    unsigned int* done_ctr;  // [4] finished-CTA counters (zero between launches)
     // pruned lists: the entries of lst within r + prune skin of some atom of
     // I at the last prune, valid while no atom moved half the prune skin
     int* plst[2];            // [ncl * capj] same layout as lst
     int* pcnt[2];            // [ncl]
     int2* pitems[2];         // (I, first entry) of each work item of the pruned lists, in allocation order
-    int* pnitems;            // [2] work items, and [2..3] their allocation counters
+    int* pnitems;            // [2] work items, [2..3] their allocation counters, [4..5] the
+                             //     pair kernel's fetch counters (zero between launches)
     int capitems;            // work items per list
     float4* pref;            // [ncl * CL] slot positions (high parts) at the last prune
     float prs2[2];           // squared prune radii (r_c or r'' plus the prune skin, with a margin)
@@ -639,6 +640,8 @@ void launch_flag_moved(const DevSys& s, const Params& p, int cur, cudaStream_t s
 // into the fixed-point accumulators, and their read-out (added to out[3n],
 // accumulators cleared).
 void launch_cluster_rebuild(const DevSys& s, const Params& p, int step_off, bool force, cudaStream_t st);
+// sizes the pair kernel's resident grid once (outside any graph capture)
+void prepare_cluster_pairs();
 void launch_cluster_pairs(const DevSys& s, const Params& p, int step_off, int part, int list, cudaStream_t st);
 void launch_cluster_collect(const DevSys& s, double* out, cudaStream_t st);
 // All-pairs tiles (tile.cu): the pair sums of `part` into the atom-indexed
