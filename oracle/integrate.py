@@ -20,6 +20,12 @@ Readings of the paper used here (all listed in the design notes):
   * L is the per-type row maximum L*_{t_i} (oracle.bounds), or, with
     per-type-pair bounds, Lt_{t_i t_j} with the two-stage partner choice
     (jump_half, oracle.bounds.pair_weights).
+  * Candidates (Sec. V: J is drawn among the particles interacting with i):
+    when the jumps carry only the LJ part (Coulomb wholly in F_0) with one
+    bound per type, a pair of types without LJ parameters does not interact
+    through the jump part, so the row of an atom keeps only the partners its
+    type has LJ with, and the rows are rebuilt on the displacement of the
+    atoms that can take part in a jump (jump_partners).
   * Random numbers: Philox4x32-10 keyed by the run seed with counter
     (slot, atom, step, stream); stream 1 for the J after the first B,
     stream 2 for the J before the last B, stream 0 for O.  Proposal k
@@ -94,6 +100,37 @@ def two_stage_pick(t, C, S, Lq_a):
     b = (C[:, 1:] <= t[:, None]).sum(1)
     rows = np.arange(len(t))
     return S[rows, b] + (t - C[rows, b]) // Lq_a[rows, b]
+
+
+def jump_partners(typ, Lstar, p, pair_bounds=None):
+    """Which candidates a jump can draw (reading of Sec. V: the partner J of
+    atom i is drawn among the particles interacting with i through the jump
+    part).  With LJ alone on the jumps (p.coulomb_jumps False) and one bound
+    per type, atom i of type a proposes only if L*_a > 0, and only atoms of a
+    type b with LJ parameters for (a, b) interact with it through the jump
+    part.  Returns None when that keeps every candidate (Coulomb on the jumps,
+    per-type-pair bounds, or no pair of present types without LJ), else
+    (partner [T, T] bool: type b is a candidate of type a; moving [T] bool:
+    types whose displacement can change a row, owners and their partners)."""
+    if pair_bounds is not None or p.coulomb_jumps:
+        return None
+    T = len(Lstar)
+    lj = (np.asarray(p.lj_eps)[:T, :T] != 0) & (np.asarray(p.lj_sigma)[:T, :T] != 0)
+    present = np.zeros(T, bool)
+    present[np.unique(typ)] = True
+    owner = (np.asarray(Lstar) > 0) & present
+    partner = owner[:, None] & lj
+    if not np.any(owner[:, None] & present[None, :] & ~partner):
+        return None
+    return partner, owner | partner.any(0)
+
+
+def filter_rows(row_list, typ, partner):
+    """Rows restricted to the candidates a jump can draw: member j of atom i
+    stays if partner[t_i, t_j] (ascending order kept; atoms whose type has
+    no partner get empty rows)."""
+    typ = np.asarray(typ)
+    return [r[partner[typ[i], typ[r]]] for i, r in enumerate(row_list)]
 
 
 def jump_half(q, v, row_list, topo, p, Lstar_row, beta, dt, seed, step, stream, record=False, pair_bounds=None):
@@ -198,6 +235,10 @@ class OracleMD:
         T = int(max(topo.type.max() + 1, p.lj_sigma.shape[0]))
         self.L, self.Lstar = bound_table(topo.charge, topo.type, T, p.lj_sigma, p.lj_eps, p)
         self.pair_bounds = pair_weights(self.L, self.Lstar) if pair_bounds else None
+        # rows of the jump step when they differ from the full rows (jump_partners)
+        self.jp = jump_partners(topo.type, self.Lstar, p, self.pair_bounds)
+        self.jrows = None
+        self.jq_ref = None
 
     @property
     def r_list(self):
@@ -207,7 +248,26 @@ class OracleMD:
         if self.row_list is None or (math.isfinite(self.r_list) and needs_rebuild(self.q, self.q_ref, self.skin)):
             self.row_list = build_rows(self.q, self.topo.mol, self.r_list, self.p.box)
             self.q_ref = self.q.copy()
+            if self.jp is None:
+                self.rebuilds += 1
+
+    def jump_rows(self):
+        """The candidate rows of the jump step at the current positions: the
+        full rows, or (jump_partners) the rows restricted to the partners a
+        jump can draw, rebuilt when an atom of a moving type has moved half
+        the skin since their build (atoms of other types neither propose nor
+        are drawn)."""
+        if self.jp is None:
+            self.ensure_rows()
+            return self.row_list
+        partner, moving = self.jp
+        mv = moving[self.topo.type]
+        if self.jrows is None or (math.isfinite(self.r_list) and needs_rebuild(self.q[mv], self.jq_ref[mv], self.skin)):
+            full = build_rows(self.q, self.topo.mol, self.r_list, self.p.box)
+            self.jrows = filter_rows(full, self.topo.type, partner)
+            self.jq_ref = self.q.copy()
             self.rebuilds += 1
+        return self.jrows
 
     def pairs(self):
         return to_pairs(self.row_list)
@@ -282,7 +342,7 @@ class OracleMD:
         self.q = self.q + h * self.v
 
     def jump(self, stream, record=False):
-        self.v, rec = jump_half(self.q, self.v, self.row_list, self.topo, self.p, self.Lstar, self.beta,
+        self.v, rec = jump_half(self.q, self.v, self.jump_rows(), self.topo, self.p, self.Lstar, self.beta,
                                 self.dt, self.seed, self.step_index, stream, record=True,
                                 pair_bounds=self.pair_bounds)
         self.proposals += int(rec['M'].sum())
