@@ -83,6 +83,20 @@ struct bounce_ctx {
     // the next row consumer tests the displacement first
     bool rows_check_due = false;
     bool rows_partial = false;    // a run left the rows of atoms with L* = 0 empty (ROWS_ACTIVE)
+    // jump rows that keep only the partners a jump can draw (LJ alone on the
+    // jumps, one bound per type): the rows buffers then hold the jump step's
+    // rows, and the entry points that read every row get full rows in a
+    // second set of buffers, so that reading leaves the run's rows alone
+    bool jfilter = false;
+    unsigned jmove = ~0u;         // types whose displacement can change a jump row
+    int rows_kind = 0;            // what the rows buffers hold: 0 nothing usable, 1 full rows, 2 jump rows
+    bool rows_swapped = false;    // ds.rows / ds.nlong point at the readers' buffers
+    int* rows_main = nullptr;     // the run's buffers while swapped
+    int* nlong_main = nullptr;
+    int* rows_alt = nullptr;      // the readers' buffers (allocated on first use)
+    int* nlong_alt = nullptr;
+    long long pos_version = 0;    // bumped whenever the positions change
+    long long reader_version = -1;  // positions the readers' rows were built at
     int* d_act_order = nullptr;   // device copy of DevSys::act_order
     // tuning (bounce_autotune): cluster column edge factor, tile j-block and grid
     double cl_edge_factor = 1.0;
@@ -156,6 +170,10 @@ void free_all(bounce_ctx* c) {
     c->tile_cap = 0;
     c->d_act_order = nullptr;
     c->rows_partial = false;
+    c->rows_kind = 0;
+    c->rows_swapped = false;
+    c->rows_main = c->nlong_main = c->rows_alt = c->nlong_alt = nullptr;
+    c->reader_version = -1;
     reset_cluster_caps(c);
 }
 
@@ -429,6 +447,8 @@ void fill_params(bounce_ctx* c, const std::vector<double>& sig, const std::vecto
     }
     p.beta = 1.0 / (KB_D * g.temperature_K);
     p.dt = g.dt_fs;
+    p.beta_f = (float)p.beta;
+    p.dt_half_f = (float)(0.5 * p.dt);
     p.c1 = std::exp(-g.gamma_per_fs * g.dt_fs);
     p.skin_half2 = std::isfinite(rl) ? 0.25 * g.skin * g.skin : INFINITY;
     p.key0 = (uint32_t)(g.seed & 0xFFFFFFFFull);
@@ -711,6 +731,39 @@ int flag_clusters(bounce_ctx* c, cudaStream_t st) {
     return BOUNCE_OK;
 }
 
+// Partners a jump can draw.  With LJ alone on the jumps (Coulomb wholly in
+// F_0) and one bound per type, an atom of type a proposes only if L*_a > 0,
+// and only the types b with LJ parameters for (a, b) interact with it
+// through the jump part (the partner J is drawn among the particles
+// interacting with i, Sec. V).  When that leaves out some present type, the
+// jump rows keep only those partners (Params::jpart) and follow the
+// displacement of the types that propose or are drawn.
+void set_rows_kind(bounce_ctx* c, int kind);
+
+void set_jump_partners(bounce_ctx* c, const std::vector<double>& sg, const std::vector<double>& ep) {
+    const int T = c->n_types;
+    bool present[BOUNCE_MAXT] = {};
+    for (int i = 0; i < c->n; ++i) present[c->type[i]] = true;
+    unsigned cells = 0, owners = 0;
+    bool drops = false;
+    for (int a = 0; a < BOUNCE_MAXT; ++a) {
+        int m = 0;
+        const bool owner = a < T && present[a] && c->Lstar[a] > 0.0;
+        for (int b = 0; owner && b < T; ++b) {
+            const bool lj = sg[a * T + b] != 0.0 && ep[a * T + b] != 0.0;
+            if (lj) m |= 1 << b;
+            else if (present[b]) drops = true;
+        }
+        c->pp.jpart[a] = m;
+        cells |= (unsigned)m;
+        if (owner) owners |= 1u << a;
+    }
+    c->pp.jcells = (int)cells;
+    c->jfilter = !c->cfg.jump_coulomb && !c->cfg.pair_bounds && drops;
+    c->jmove = owners | cells;
+    set_rows_kind(c, 0);
+}
+
 // Launch the rebuild sequence of the candidate rows (gated by the device
 // flag unless forced).  After BAOAB runs on clusters the step kernel did not
 // test the rows' displacement, so it is tested here first, at the current
@@ -745,6 +798,67 @@ void complete_rows(bounce_ctx* c, cudaStream_t st) {
     if (!c->rows_partial) return;
     launch_rebuild(c->ds, c->pp, 0, true, c->bitmap_warps, c->bitmap_bytes, ROWS_IDLE, st);
     c->rows_partial = false;
+}
+
+// Whether the runs of `integ` read jump rows that keep only the partners a
+// jump can draw (the jump step is then the rows' only reader).
+bool jump_filtered(const bounce_ctx* c, int integ) {
+    return c->jfilter && integ != BOUNCE_BAOAB && (c->ds.cl.on || c->ds.tl.on || c->ds.rep_of) &&
+           !(c->pp.rshort2 < INFINITY);
+}
+
+// Row-build mode of the gated rebuilds inside the runs of `integ`.
+int run_rows_mode(const bounce_ctx* c, int integ) {
+    return rows_mode(c, integ) | (jump_filtered(c, integ) ? ROWS_FILTER : 0);
+}
+
+// What the rows buffers hold (0 nothing usable, 1 full rows, 2 jump rows);
+// the displacement test follows the types that can change them.
+void set_rows_kind(bounce_ctx* c, int kind) {
+    c->rows_kind = kind;
+    c->ds.rows_move = kind == 2 ? c->jmove : ~0u;
+}
+
+// Exchange the run's row buffers and the readers' ones.
+void swap_rows(bounce_ctx* c) {
+    if (!c->rows_swapped) {
+        c->rows_main = c->ds.rows;
+        c->nlong_main = c->ds.nlong;
+        c->ds.rows = c->rows_alt;
+        c->ds.nlong = c->nlong_alt;
+    } else {
+        c->ds.rows = c->rows_main;
+        c->ds.nlong = c->nlong_main;
+    }
+    c->rows_swapped = !c->rows_swapped;
+}
+
+// Rows for the entry points that read every row (energies, histograms,
+// gradients, the rows themselves, the pair forward, the stand-alone jump
+// half-step); `replaced`: the positions were just set.  With jump rows that
+// keep only the jump partners, the full rows are built at the current
+// positions into the readers' buffers, so that the run's rows, their
+// reference positions and the rebuild flag stay as the last run left them.
+int prepare_readers(bounce_ctx* c, cudaStream_t st, bool replaced = false) {
+    if (!c->jfilter) {
+        rebuild(c, 0, replaced, st);
+        complete_rows(c, st);
+        return BOUNCE_OK;
+    }
+    if (replaced) {
+        ++c->pos_version;
+        set_rows_kind(c, 0);  // the next run builds its rows afresh
+    }
+    if (c->rows_swapped && c->reader_version == c->pos_version) return BOUNCE_OK;
+    if (!c->rows_alt) {
+        int r;
+        if ((r = dalloc(c, &c->rows_alt, (size_t)c->n * c->ds.cap)) || (r = dalloc(c, &c->nlong_alt, c->n)))
+            return r;
+    }
+    if (!c->rows_swapped) swap_rows(c);
+    launch_rebuild(c->ds, c->pp, 0, true, c->bitmap_warps, c->bitmap_bytes, ROWS_READER, st);
+    c->reader_version = c->pos_version;
+    return BOUNCE_OK;
 }
 
 int check_err(bounce_ctx* c, cudaStream_t st) {
@@ -820,10 +934,18 @@ double expected_proposals(const bounce_ctx* c, double rho) {
     const double beta = 1.0 / (KB_D * g.temperature_K);
     const double rl = r_list(g);
     const double nbar = std::isfinite(rl) ? std::min((double)c->n, rho * 4.18879 * rl * rl * rl) : (double)c->n;
+    // jump rows that keep only the jump partners: the share of the atoms of a partner type
+    double share[BOUNCE_MAXT];
+    for (int a = 0; a < BOUNCE_MAXT; ++a) {
+        int k = 0;
+        if (c->jfilter)
+            for (int i = 0; i < c->n; ++i) k += (c->pp.jpart[a] >> c->type[i]) & 1;
+        share[a] = c->jfilter && c->n ? (double)k / c->n : 1.0;
+    }
     double sum = 0.0;
     for (int i = 0; i < c->n; ++i) {
         const double vbar = std::sqrt(8.0 * KB_D * g.temperature_K * ACCEL_D / (M_PI * c->mass[i]));
-        sum += beta * vbar * c->Lstar[c->type[i]] * nbar * g.dt_fs;
+        sum += beta * vbar * c->Lstar[c->type[i]] * nbar * share[c->type[i]] * g.dt_fs;
     }
     return sum / c->n;
 }
@@ -833,15 +955,30 @@ double expected_proposals(const bounce_ctx* c, double rho) {
 // every integrator without clusters, whose pair sums run over the rows).
 void rebuild_for(bounce_ctx* c, int integ, int off, cudaStream_t st) {
     if (c->ds.cl.on) launch_cluster_rebuild(c->ds, c->pp, off, false, st);
-    if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st, rows_mode(c, integ));
+    if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st, run_rows_mode(c, integ));
 }
 
 // Before a run: rows a previous run left partial are completed when this
 // run builds full rows; after it, they are partial if it built active ones.
+// With jump rows that keep only the jump partners, the run's buffers come
+// back from the readers, and rows of the other kind (full rows for a run
+// that reads them, jump rows for a BOUNCE run) are rebuilt at once.
 void rows_before_run(bounce_ctx* c, int integ, cudaStream_t st) {
-    if (rows_mode(c, integ) == ROWS_ALL) complete_rows(c, st);
+    if (c->rows_swapped) swap_rows(c);
+    if (!c->jfilter) {
+        if (rows_mode(c, integ) == ROWS_ALL) complete_rows(c, st);
+        return;
+    }
+    if (c->ds.cl.on && integ == BOUNCE_BAOAB) return;  // reads no rows
+    const int kind = jump_filtered(c, integ) ? 2 : 1;
+    if (c->rows_kind != kind) {
+        set_rows_kind(c, kind);
+        rebuild(c, 0, true, st, kind == 2 ? run_rows_mode(c, integ) : ROWS_ALL);
+        c->rows_partial = false;
+    }
 }
 void rows_after_run(bounce_ctx* c, int integ) {
+    ++c->pos_version;
     if (rows_mode(c, integ) == ROWS_ACTIVE) c->rows_partial = true;
 }
 
@@ -1047,6 +1184,7 @@ int bounce_set_topology(bounce_ctx* c, int32_t n, const int32_t* type, const dou
     s.bt_par = bpar;
     s.step_base = c->d_step;
     s.rows_flag = 1;
+    s.rows_move = ~0u;
     std::vector<double> hk(n), ho(n);
     const double c1 = std::exp(-c->cfg.gamma_per_fs * c->cfg.dt_fs);
     for (int i = 0; i < n; ++i) {
@@ -1103,6 +1241,7 @@ int bounce_set_lj(bounce_ctx* c, int32_t T, const double* sigma, const double* e
         }
     compute_bounds(c, sg, ep);
     fill_params(c, sg, ep);
+    set_jump_partners(c, sg, ep);
     drop_graphs(c);
     {
         // atoms that can propose (L* > 0) first, for the row builder
@@ -1213,6 +1352,7 @@ int bounce_set_state(bounce_ctx* c, const double* q, const double* v, int64_t st
     c->step0 = step;
     c->cur_step = step;
     c->have_state = true;
+    ++c->pos_version;
     return BOUNCE_OK;
 }
 
@@ -1346,7 +1486,7 @@ int bounce_profile_breakdown(bounce_ctx* c, int64_t n_steps, int32_t integ, void
         ok = ok && mark(-1);
         if (c->ds.cl.on) launch_cluster_rebuild(c->ds, c->pp, off, false, st);
         ok = ok && mark(3);
-        if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st, rows_mode(c, integ));
+        if (!c->ds.cl.on || integ != BOUNCE_BAOAB) rebuild(c, off, false, st, run_rows_mode(c, integ));
         ok = ok && mark(2);
         if (pme) launch_pme(c->ds, c->pp, c->pme, off, st);
         ok = ok && mark(4);
@@ -1495,8 +1635,7 @@ int bounce_get_energies(bounce_ctx* c, bounce_energies* out, void* stream) {
     long long step;
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    rebuild(c, 0, false, st);
-    complete_rows(c, st);
+    if (int r0 = prepare_readers(c, st)) return r0;
     launch_energies(c->ds, c->pp, (int)(step & 1), c->terms, st);
     double tot[5], pe[2] = {0.0, 0.0};
     if (c->has_pme) {
@@ -1544,8 +1683,7 @@ int bounce_pair_histogram(bounce_ctx* c, int32_t ta, int32_t tb, double r_max, i
     long long step;
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    rebuild(c, 0, false, st);
-    complete_rows(c, st);
+    if (int r0 = prepare_readers(c, st)) return r0;
     CU(cudaMemsetAsync(c->hist, 0, n_bins * sizeof(unsigned long long), st));
     launch_pair_hist(c->ds, c->pp, (int)(step & 1), ta, tb, r_max, n_bins, c->hist, st);
     CU(cudaMemcpyAsync(hist, c->hist, n_bins * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -1620,8 +1758,7 @@ int bounce_compute_gradient(bounce_ctx* c, int32_t part, double* grad, int32_t w
     long long step;
     CU(cudaMemcpyAsync(&step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    rebuild(c, 0, false, st);
-    complete_rows(c, st);
+    if (int r0 = prepare_readers(c, st)) return r0;
     const cudaMemcpyKind kind = where == BOUNCE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (part == BOUNCE_GRAD_RECIP) {
         if (!c->has_pme) return fail(c, BOUNCE_ERR_STATE, "no SPME grid configured");
@@ -1664,7 +1801,12 @@ int bounce_jump_half(bounce_ctx* c, int64_t step, int32_t stream_id, int32_t* M,
     long long cur_step;
     CU(cudaMemcpyAsync(&cur_step, c->d_step, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    rebuild(c, 0, false, st);
+    if (c->jfilter) {
+        // the stand-alone half-step draws over the full rows
+        if (int r0 = prepare_readers(c, st)) return r0;
+    } else {
+        rebuild(c, 0, false, st);
+    }
     int* dM = nullptr;
     int* dA = nullptr;
     if (M || nacc) {
@@ -1684,8 +1826,7 @@ int bounce_get_rows(bounce_ctx* c, int32_t* counts, int32_t* rows, int32_t capac
     if (!c || !counts || !rows || capacity < 1) return fail(c, BOUNCE_ERR_INVALID_ARG, "bad row arguments");
     if (!c->have_state) return fail(c, BOUNCE_ERR_STATE, "no state");
     cudaSetDevice(c->cfg.device);
-    rebuild(c, 0, false, nullptr);
-    complete_rows(c, nullptr);
+    if (int r0 = prepare_readers(c, nullptr)) return r0;
     CU(cudaDeviceSynchronize());
     int r = check_err(c, nullptr);
     if (r) return r;
@@ -1746,6 +1887,8 @@ int bounce_set_replicas(bounce_ctx* c, int32_t n_rep, const int32_t* off, const 
     if ((rr = setup_tiles(c))) return rr;
     drop_graphs(c);
     c->rows_valid = false;
+    set_rows_kind(c, 0);
+    ++c->pos_version;
     return BOUNCE_OK;
 }
 
@@ -1786,11 +1929,9 @@ int bounce_pair_forward(bounce_ctx* c, const double* q, int32_t T, const double*
                              cudaMemcpyDeviceToDevice, st));
         launch_pack_positions(c->ds, c->pp, cur, st);
         if ((r = flag_clusters(c, st))) return r;
-        rebuild(c, 0, true, st);
-        complete_rows(c, st);
+        if ((r = prepare_readers(c, st, true))) return r;
     } else {
-        rebuild(c, 0, false, st);
-        complete_rows(c, st);
+        if ((r = prepare_readers(c, st))) return r;
     }
     double* eatom = c->terms;
     double* esum = c->terms + 6 * (size_t)n + 1024;

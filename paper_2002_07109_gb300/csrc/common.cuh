@@ -163,6 +163,8 @@ struct DevSys {
     const int* act_order;    // [n] atoms whose type has L* > 0 (ascending), then the others
     int n_act;               // atoms that can propose
     int rows_flag;           // the step kernel raises `rebuild` for the rows (0 in BAOAB runs on clusters)
+    unsigned rows_move;      // types whose displacement raises `rebuild` (all of them unless the
+                             //     jump rows keep only the partners a jump can draw)
     int lite;                // thread-per-atom step kernel (rare jump proposals)
 };
 
@@ -203,6 +205,8 @@ struct Params {
     float rcull;                 // r_list with a safety margin for cell culling (+inf = all)
     int coul_jump;               // 1: Coulomb is switched by chi like LJ; 0: Coulomb wholly in F_0
     int typed;                   // per-type-pair bounds with the two-stage partner choice
+    int jpart[BOUNCE_MAXT];      // jump rows (ROWS_FILTER): types an atom of type a can draw, as a bitmask
+    int jcells;                  // jump rows: types placed in the cells (every type some row can hold)
     int n_types;
     uint32_t lq[BOUNCE_MAXT * BOUNCE_MAXT];  // integer weights Lq_ab of the partner types
     uint32_t lq_m[BOUNCE_MAXT * BOUNCE_MAXT];  // x / Lq_ab = (t + ((x - t) >> 1)) >> lq_s, t = umulhi(lq_m, x)
@@ -212,6 +216,7 @@ struct Params {
     double Lstar_d[BOUNCE_MAXT];
     double beta;
     double dt;
+    float beta_f, dt_half_f;     // beta and dt / 2 in FP32 (the jump step's bound of the Poisson mean)
     double c1;
     double skin_half2;
     uint32_t key0, key1;
@@ -609,8 +614,10 @@ inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Row-build modes of launch_rebuild (see k_rows_warp).
-constexpr int ROWS_ALL = 0, ROWS_ACTIVE = 1, ROWS_IDLE = 2;
+// Row-build modes of launch_rebuild (see k_rows_warp); ROWS_FILTER may be
+// added to ROWS_ALL or ROWS_ACTIVE: rows of the jump step that keep only the
+// partners a jump can draw (Params::jpart).
+constexpr int ROWS_ALL = 0, ROWS_ACTIVE = 1, ROWS_IDLE = 2, ROWS_READER = 3, ROWS_FILTER = 8;
 
 // Launchers implemented in the .cu files.
 void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, int window_words, size_t bitmap_bytes,

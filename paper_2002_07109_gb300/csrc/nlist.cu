@@ -104,10 +104,16 @@ __device__ void cells_scan(const DevSys& s) {
 }
 
 // Cell counts; the CTA that finishes last scans them.
-__global__ void k_cells_count(DevSys s, Params p, int step_off, int force) {
+// Atom i goes into the cells (ROWS_FILTER: only the types some jump row can hold).
+__device__ __forceinline__ bool in_cells(const DevSys& s, const Params& p, int mode, int i) {
+    return !(mode & ROWS_FILTER) || ((p.jcells >> s.type[i]) & 1);
+}
+
+__global__ void k_cells_count(DevSys s, Params p, int step_off, int force, int mode) {
     if (!pending(s, force)) return;
     int cur = (int)((*s.step_base + step_off) & 1);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        if (!in_cells(s, p, mode, i)) continue;
         int cx, cy, cz;
         cell_of(s, p, s.phi[cur][i], cx, cy, cz);
         atomicAdd(&s.cell_count[(cz * s.ncy + cy) * s.ncx + cx], 1);
@@ -115,10 +121,11 @@ __global__ void k_cells_count(DevSys s, Params p, int step_off, int force) {
     if (last_cta(&s.done_ctr[0])) cells_scan(s);
 }
 
-__global__ void k_cells_scatter(DevSys s, Params p, int step_off, int force) {
+__global__ void k_cells_scatter(DevSys s, Params p, int step_off, int force, int mode) {
     if (!pending(s, force)) return;
     int cur = (int)((*s.step_base + step_off) & 1);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
+        if (!in_cells(s, p, mode, i)) continue;
         int cx, cy, cz;
         const float4 hi = s.phi[cur][i];
         cell_of(s, p, hi, cx, cy, cz);
@@ -359,8 +366,12 @@ __device__ __forceinline__ bool row_member(const DevSys& s, const Params& p, int
 // run over clusters or tiles and no short rows exist); ROWS_IDLE builds only
 // those rows, at the current positions, keeping the reference positions and
 // the rebuild flag of the last build (completing ROWS_ACTIVE rows for the
-// energy, histogram and gradient entry points, which read every row).
-__global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww, int mode) {
+// energy, histogram and gradient entry points, which read every row);
+// ROWS_READER builds every row the same way, into the readers' own row
+// buffers.  ROWS_FILTER (with ROWS_ALL or ROWS_ACTIVE): the rows of the
+// jump step keep only the partner types of the row's atom (Params::jpart),
+// and the cells hold only the types some row can hold.
+__global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww, int mode_in) {
     if (!pending(s, force)) return;
     extern __shared__ uint32_t smem_bm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -375,7 +386,12 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
     int* rl = rb + RANGE_MAX;
     int* rp = rl + RANGE_MAX;
     const int cur = (int)((*s.step_base + step_off) & 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && mode != ROWS_IDLE) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
+    const int mode = mode_in & 7;
+    const bool filt = (mode_in & ROWS_FILTER) != 0;
+    // ROWS_IDLE and ROWS_READER builds leave the reference positions, the
+    // rebuild flag and the rebuild count to the run's own builds
+    const bool own = mode != ROWS_IDLE && mode != ROWS_READER;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && own) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
     // the bitmaps start clear; after each atom only the words it touched are cleared
     for (int w = lane; w < nb * ww; w += 32) bm[w] = 0u;
     __syncwarp();
@@ -386,7 +402,8 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
     // others get empty rows and their reference positions), ROWS_IDLE the
     // rows of the rest; the warps stride over the listed atoms only, so the
     // work stays balanced whatever the order of the atom types.
-    const bool split = mode != ROWS_ALL && (s.cl.on || s.tl.on) && !has_short && s.act_order != nullptr;
+    const bool split =
+        mode != ROWS_ALL && mode != ROWS_READER && (s.cl.on || s.tl.on) && !has_short && s.act_order != nullptr;
     const int t0 = split && mode == ROWS_IDLE ? s.n_act : 0;
     const int t1 = split && mode == ROWS_ACTIVE ? s.n_act : s.n;
     if (split && mode == ROWS_ACTIVE)
@@ -404,6 +421,7 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
         const int i = split ? s.act_order[t] : t;
         const float4 hi = s.phi[cur][i];
         const int mi = s.mol[i];
+        const int pm = filt ? p.jpart[s.type[i]] : -1;  // partner types of the row (all without the filter)
         int nr_tot;
         const int total_c = candidate_runs(s, p, hi, rb, rl, rp, nr_tot);
         __syncwarp();
@@ -420,7 +438,7 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
             while (lo_r + 1 < nr_tot && rp[lo_r + 1] <= t) ++lo_r;
             const int idx = rb[lo_r] + (t - rp[lo_r]);
             const int j = s.cell_atoms[idx];
-            if (j == i || s.cell_mol[idx] == mi) continue;
+            if (j == i || s.cell_mol[idx] == mi || !((pm >> s.cell_type[idx]) & 1)) continue;
             float r2;
             if (!row_member(s, p, cur, i, hi, s.cell_phi[idx], j, r2)) continue;
             const int ty = p.typed ? s.cell_type[idx] : 0, w = j >> 5;
@@ -498,7 +516,8 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
                         const int idx = rb[lo_r] + (t - rp[lo_r]);
                         const int j = s.cell_atoms[idx];
                         const int w = j >> 5;
-                        if (w < w0 || w >= w1 || j == i || s.cell_mol[idx] == mi) continue;
+                        if (w < w0 || w >= w1 || j == i || s.cell_mol[idx] == mi || !((pm >> s.cell_type[idx]) & 1))
+                            continue;
                         float r2;
                         if (!row_member(s, p, cur, i, hi, s.cell_phi[idx], j, r2)) continue;
                         const int ty = p.typed ? s.cell_type[idx] : 0;
@@ -530,7 +549,7 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
             if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
             s.nshort[i] = min(ns, s.caps);
             if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
-            if (mode != ROWS_IDLE) {
+            if (own) {
                 s.refx[i] = s.qx[cur][i];
                 s.refy[i] = s.qy[cur][i];
                 s.refz[i] = s.qz[cur][i];
@@ -538,19 +557,22 @@ __global__ void k_rows_warp(DevSys s, Params p, int step_off, int force, int ww,
         }
         __syncwarp();
     }
-    if (last_cta(&s.done_ctr[1]) && mode != ROWS_IDLE) *s.rebuild = 0;
+    if (last_cta(&s.done_ctr[1]) && own) *s.rebuild = 0;
 }
 
 // Rows of a batch of independent all-pairs replicas: every atom of the same
 // replica outside the own molecule, ascending (no distance test: replicas
 // have no cutoff), then the short rows and reference positions as above.
-__global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
+__global__ void k_rows_batch(DevSys s, Params p, int step_off, int force, int mode_in) {
     if (!pending(s, force)) return;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int cur = (int)((*s.step_base + step_off) & 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
+    const bool filt = (mode_in & ROWS_FILTER) != 0;
+    const bool own = (mode_in & 7) != ROWS_IDLE && (mode_in & 7) != ROWS_READER;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && own) atomicAdd(&s.cnt[CNT_REBUILDS], 1ull);
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < s.n; i += gridDim.x * wpb) {
         const int r = s.rep_of[i], b = s.rep_off[r], e = s.rep_off[r + 1], mi = s.mol[i];
+        const int pm = filt ? p.jpart[s.type[i]] : -1;  // partner types of the row (all without the filter)
         int* row = s.rows + (size_t)i * s.cap;
         int total = 0;
         const int ngroups = p.typed ? p.n_types : 1;
@@ -558,7 +580,7 @@ __global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
             const int before = total;
             for (int j0 = b; j0 < e; j0 += 32) {
                 const int j = j0 + lane;
-                const bool keep = j < e && s.mol[j] != mi && (!p.typed || s.type[j] == tb);
+                const bool keep = j < e && s.mol[j] != mi && (!p.typed || s.type[j] == tb) && ((pm >> s.type[j]) & 1);
                 const uint32_t m = __ballot_sync(0xffffffffu, keep);
                 const int pos = total + __popc(m & ((1u << lane) - 1u));
                 if (keep && pos < s.cap) row[pos] = j;
@@ -593,19 +615,21 @@ __global__ void k_rows_batch(DevSys s, Params p, int step_off, int force) {
             if (total > s.cap) atomicOr(s.err, BERR_LIST_OVERFLOW);
             s.nshort[i] = min(ns, s.caps);
             if (ns > s.caps) atomicOr(s.err, BERR_SHORT_OVERFLOW);
-            s.refx[i] = s.qx[cur][i];
-            s.refy[i] = s.qy[cur][i];
-            s.refz[i] = s.qz[cur][i];
+            if (own) {
+                s.refx[i] = s.qx[cur][i];
+                s.refy[i] = s.qy[cur][i];
+                s.refz[i] = s.qz[cur][i];
+            }
         }
         __syncwarp();
     }
-    if (last_cta(&s.done_ctr[1])) *s.rebuild = 0;
+    if (last_cta(&s.done_ctr[1]) && own) *s.rebuild = 0;
 }
 
 __global__ void k_flag_moved(DevSys s, Params p, int cur) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x) {
         const double ex = s.qx[cur][i] - s.refx[i], ey = s.qy[cur][i] - s.refy[i], ez = s.qz[cur][i] - s.refz[i];
-        if (ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+        if (((s.rows_move >> s.type[i]) & 1) && ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
     }
 }
 
@@ -620,13 +644,13 @@ void launch_rebuild(const DevSys& s, const Params& p, int step_off, bool force, 
     const int f = force ? 1 : 0;
     if (s.rep_of) {
         const int wpb = 8;
-        launch_chained(k_rows_batch, (s.n + wpb - 1) / wpb, wpb * 32, 0, st, s, p, step_off, f);
+        launch_chained(k_rows_batch, (s.n + wpb - 1) / wpb, wpb * 32, 0, st, s, p, step_off, f, mode);
         return;
     }
     const int tb = 1024;
     const int gb = (s.n + tb - 1) / tb;
-    launch_chained(k_cells_count, gb, tb, 0, st, s, p, step_off, f);
-    launch_chained(k_cells_scatter, gb, tb, 0, st, s, p, step_off, f);
+    launch_chained(k_cells_count, gb, tb, 0, st, s, p, step_off, f, mode);
+    launch_chained(k_cells_scatter, gb, tb, 0, st, s, p, step_off, f, mode);
     // warp per atom, 8 warps per CTA, a grid-stride loop over one wave of CTAs
     const int per_sm = std::max(1, std::min(8, (int)((227u << 10) / std::max<size_t>(bitmap_bytes, 1))));
     const int blocks = std::min((s.n + 7) / 8, 152 * per_sm);

@@ -748,7 +748,9 @@ __global__ void __launch_bounds__(NW * 32, 3) k_step(DevSys s, Params p, int var
             s.phi[nxt][i] = ph;
             s.plo[nxt][i] = pl;
             const double ex = x - sRef[lane][0], ey = y - sRef[lane][1], ez = z - sRef[lane][2];
-            if (s.rows_flag && ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+            if (s.rows_flag && ((s.rows_move >> __float_as_int(sLw[lane])) & 1) &&
+                ex * ex + ey * ey + ez * ez > p.skin_half2)
+                atomicOr(s.rebuild, 1);
             if (s.cl.on) {
                 // slot-ordered copy for the cluster pair kernel (in the image of the
                 // build); displacement since the cluster build
@@ -799,6 +801,20 @@ __device__ __forceinline__ void jump_thread(const DevSys& s, const Params& p, in
     dvx = dvy = dvz = 0.f;
     const double Ls = p.Lstar_d[ti];
     if (Ls == 0.0) return;  // no jump part for this type: Poisson mean 0 (skips the FP64 set-up)
+    if (!p.typed) {
+        // Most atoms draw no proposal.  An FP32 upper bound mu_f of the mean
+        // (every rounding covered by the factor 1 + 1e-5) and the same first
+        // Poisson draw settle M = 0 without the FP64 set-up: expneg_f32 is
+        // within 1e-6 of exp(-x), so u <= expneg_f32(mu_f) (1 - 4e-6) implies
+        // u <= expneg_f32(float(mu)), which is the exact path's M = 0.
+        const float fx = __double2float_rn(vx), fy = __double2float_rn(vy), fz = __double2float_rn(vz);
+        const float spf = sqrtf(fx * fx + fy * fy + fz * fz);
+        const float muf = p.beta_f * spf * p.Lstar_f[ti] * (float)s.nlong[i] * p.dt_half_f * 1.00001f;
+        if (muf < 1.f) {
+            const float u = u24(rng_atom(s, p, BOUNCE_POISSON_SLOT, i, step, stream).x);
+            if (u <= __fmul_rn(expneg_f32(muf), 0.999996f)) return;
+        }
+    }
     const double sp = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
     double n;
     uint32_t acum[BOUNCE_MAXT + 1];
@@ -1099,7 +1115,8 @@ __global__ void __launch_bounds__(256, LITE_MIN_CTAS) k_step_lite(DevSys s, Para
             s.phi[nxt][i] = ph;
             s.plo[nxt][i] = pl;
             const double ex = x - s.refx[i], ey = y - s.refy[i], ez = z - s.refz[i];
-            if (s.rows_flag && ex * ex + ey * ey + ez * ez > p.skin_half2) atomicOr(s.rebuild, 1);
+            if (s.rows_flag && ((s.rows_move >> type_of(alo)) & 1) && ex * ex + ey * ey + ez * ez > p.skin_half2)
+                atomicOr(s.rebuild, 1);
             if (s.cl.on) {
                 float4 ch = ph, cw = pl;
                 if (p.periodic) split_pos(x, y, z, s.cl.cofx[i], s.cl.cofy[i], s.cl.cofz[i], ph.w, pl.w, ch, cw);

@@ -582,7 +582,7 @@ def test_full_size_box_first_step_sampled(coulomb_jumps):
     from oracle import ewald
     from oracle.bounds import bound_table
     from oracle.forcefield import ACCEL, KB, bonded_gradients, pair_gradients
-    from oracle.integrate import o_step
+    from oracle.integrate import filter_rows, jump_partners, o_step
     from oracle.neighbors import to_pairs
     s = water_box(32, seed=0)
     rng = np.random.default_rng(8)
@@ -612,8 +612,12 @@ def test_full_size_box_first_step_sampled(coulomb_jumps):
     h = 0.5
     v = s.v - ((h * ACCEL) / s.mass)[:, None] * G
     # J over dt/2 (stream 1) with the sampled atoms' rows; the others have none
+    # (LJ alone on the jumps: the rows keep only the partners a jump can draw)
     _, Lstar = bound_table(s.charge, s.type, 2, s.lj_sigma, s.lj_eps, p)
-    v, rec = jump_half(q0, v, row_list, topo, p, Lstar, 1.0 / (KB * 300.0), 1.0, 13, 0, philox.STREAM_J1,
+    jp = jump_partners(s.type, Lstar, p)
+    assert (jp is None) == coulomb_jumps
+    jrows = row_list if jp is None else filter_rows(row_list, s.type, jp[0])
+    v, rec = jump_half(q0, v, jrows, topo, p, Lstar, 1.0 / (KB * 300.0), 1.0, 13, 0, philox.STREAM_J1,
                        record=True)
     tie = np.zeros(s.n_atoms, bool)
     tie[rec["atom"][np.abs(rec["U"] - rec["ratio"]) < 1e-6]] = True

@@ -124,6 +124,51 @@ def test_one_bounce_step_lj_only(name):
     ctx.close()
 
 
+def test_jump_rows_keep_the_lj_partners_over_rebuilds():
+    """LJ alone on the jumps with one bound per type: the jump rows keep only
+    the O partners of O atoms and are rebuilt when an O atom has moved half
+    the skin (H atoms neither propose nor are drawn).  Ten BOUNCE steps of the
+    droplet with a 0.2 A row skin, so that the jump rows are rebuilt within
+    them, against the oracle's ten steps: the same rebuilds and proposals,
+    and positions within the several-step bound (1e-4, as for the 20-step
+    trajectory test) relative to the length of the path travelled (atoms
+    with a near tie, and their row partners, left out)."""
+    build, cfg = CASES["droplet"]
+    s = build()
+    cfg = dict(cfg, skin=0.2)
+    ctx = bounce.from_system(s, seed=21, jump_coulomb=False, **cfg)
+    ctx.set_state(s.q, s.v, step=3)
+    p = Params(r_on=cfg["r_on"], r_off=cfg["r_off"], r_cut=cfg["r_cut"], box=s.box, lj_sigma=s.lj_sigma,
+               lj_eps=s.lj_eps, coulomb_jumps=False)
+    md = OracleMD(s.q, s.v, _topo(s), p, seed=21, skin=0.2, step=3)
+    assert md.jp is not None
+    ctx.run(10, bounce.BOUNCE)
+    tie = np.zeros(s.n_atoms, bool)
+    path = np.zeros(s.n_atoms)
+    for _ in range(10):
+        qp = md.q.copy()
+        recs = md.step_bounce(record=True)
+        path += np.linalg.norm(md.q - qp, axis=1)
+        for r in recs:
+            t = r["atom"][np.abs(r["U"] - r["ratio"]) < 1e-6]
+            tie[t] = True
+            for i in t:
+                tie[md.jrows[i]] = True
+    e = ctx.energies()
+    assert md.rebuilds >= 2, md.rebuilds
+    assert e["rebuilds"] == md.rebuilds
+    assert e["proposals"] == md.proposals and md.proposals > 0
+    q, v = ctx.get_state()
+    dq = np.linalg.norm(q - md.q, axis=1) / np.maximum(path, 1e-6)
+    assert dq[~tie].max() < 10 * TOL, dq[~tie].max()
+    # the readers got full rows; the run's jump rows hold O partners only
+    rows = ctx.rows()
+    o = int(np.nonzero(s.type == 0)[0][0])
+    assert np.any(s.type[rows[o]] == 1)
+    assert all(np.all(s.type[md.jrows[i]] == 0) for i in range(s.n_atoms) if s.type[i] == 0)
+    ctx.close()
+
+
 def test_idle_rows_completed_for_readers():
     """With LJ alone on the jumps, H atoms have L* = 0 and never propose, so a
     run on clusters builds no rows for them.  Entry points that read every
