@@ -63,7 +63,7 @@ METRIC = "ns/day & pair-evals/s, BOUNCE vs BAOAB 1fs on one GB300 at matched <E>
 WINDOW = 24        # steps per timed window (a multiple of every arm's outer step)
 BOX_SIDE = 32      # 32^3 = 32,768 molecules
 R_CUT, R_ON, R_OFF, SKIN, BETA, GRID, ORDER = 9.0, 7.5, 8.5, 1.0, 0.35, 96, 5
-PAIR_SKIN = 2.0
+PAIR_SKIN = 3.0
 DT = 1.0
 RHO_O = 0.03343    # O atoms per A^3 at 1 g/cm^3
 WORKLOAD = ("BOUNCE-RESPA (SPME on the 2 fs outer step) vs BAOAB 1 fs, 32,768-molecule periodic flexible-water box "
@@ -182,7 +182,7 @@ def ns_per_day(steps, seconds):
 
 
 def box_cfg(device, **kw):
-    # cluster lists with a 2 A skin (rebuilt rarely; the pair kernel reads
+    # cluster lists with a 3 A skin (rebuilt rarely; the pair kernel reads
     # lists pruned to r_c + 0.5 A every few steps)
     cfg = dict(r_on=R_ON, r_off=R_OFF, r_cut=R_CUT, skin=SKIN, pair_skin=PAIR_SKIN, dt=DT, ewald_beta=BETA,
                pme_grid=(GRID,) * 3, pme_order=ORDER, max_neighbors=1024, device=device)

@@ -932,33 +932,16 @@ __device__ __forceinline__ void jump_thread(const DevSys& s, const Params& p, in
     }
 }
 
-// The jump half-steps of the CTA's atoms that can propose (type with L* >
-// 0), taken by the CTA's first threads after a compaction, so that the
-// warps whose atoms have no jump part skip the FP64 set-up as a whole while
-// every other phase keeps one thread per atom in atom order (coalesced).
-// v: the CTA's velocities in shared memory (read and updated in place).
-#ifndef LITE_JUMP_INLINE
-#define LITE_JUMP_INLINE 1
-#endif
-#if LITE_JUMP_INLINE
-__device__ __forceinline__
-#else
-__device__ __noinline__
-#endif
-void jump_phase_lite(const DevSys& s, const Params& p, int cur, long long step,
-                                                uint32_t stream, const short* act, int nact, double (*v)[256],
-                                                int& nprop, int& nacc, int& near) {
-    for (int k = threadIdx.x; k < nact; k += blockDim.x) {
-        const int j = act[k];
-        const int i = blockIdx.x * blockDim.x + j;
-        const float4 ahi = s.phi[cur][i], alo = s.plo[cur][i];
-        float dx, dy, dz;
-        jump_thread(s, p, cur, i, s.type[i], v[0][j], v[1][j], v[2][j], step, stream, ahi, alo, dx, dy, dz, nprop,
-                    nacc, near);
-        v[0][j] += (double)dx;
-        v[1][j] += (double)dy;
-        v[2][j] += (double)dz;
-    }
+// The jump half-step of atom i in the thread-per-atom kernel: the velocity
+// in FP64 registers, updated by the FP32 increment of jump_thread.
+__device__ __forceinline__ void jump_lite(const DevSys& s, const Params& p, int cur, int i, long long step,
+                                          uint32_t stream, float4 ahi, float4 alo, double& vx, double& vy,
+                                          double& vz, int& nprop, int& nacc, int& near) {
+    float dx, dy, dz;
+    jump_thread(s, p, cur, i, type_of(alo), vx, vy, vz, step, stream, ahi, alo, dx, dy, dz, nprop, nacc, near);
+    vx += (double)dx;
+    vy += (double)dy;
+    vz += (double)dz;
 }
 
 // Resident CTAs per SM the thread-per-atom kernel is compiled for: three
@@ -972,12 +955,9 @@ template <int BOUNCE>
 __global__ void __launch_bounds__(256, LITE_MIN_CTAS) k_step_lite(DevSys s, Params p, int variant, int step_off,
                                                                   double hr, int ext, double hout) {
     __shared__ unsigned long long cnt[4];
-    __shared__ double sv[3][256];   // velocities between the phases (jump steps)
-    __shared__ short sact[256];     // CTA-local indices of the atoms that can propose
-    __shared__ int swc[8];          // per-warp counts of those atoms
     chain_enter();
     if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < s.n;
     int nprop = 0, nacc = 0, near = 0;
@@ -987,21 +967,7 @@ __global__ void __launch_bounds__(256, LITE_MIN_CTAS) k_step_lite(DevSys s, Para
     const bool do_j1 = BOUNCE && variant != 2;
     const bool do_aoa = variant != 2;
     const double hk = variant == 1 ? p.dt : 0.5 * p.dt;
-    // compaction of the atoms that can propose (in atom order: deterministic)
-    int nact = 0;
-    if (BOUNCE) {
-        const bool act = live && p.Lstar_d[s.type[i]] != 0.0;
-        const uint32_t bal = __ballot_sync(0xffffffffu, act);
-        if (lane == 0) swc[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            off += w < wid ? swc[w] : 0;
-            nact += swc[w];
-        }
-        if (act) sact[off + __popc(bal & ((1u << lane) - 1u))] = (short)threadIdx.x;
-    }
-    __syncthreads();
+    __syncthreads();  // the counters are cleared
     // pair sums of the pair kernel (absent between the outer kicks of the extended splits)
     float gx = 0.f, gy = 0.f, gz = 0.f, Gx = 0.f, Gy = 0.f, Gz = 0.f;
     int sl = i;
@@ -1040,17 +1006,9 @@ __global__ void __launch_bounds__(256, LITE_MIN_CTAS) k_step_lite(DevSys s, Para
         vy = s.vy[i];
         vz = s.vz[i];
     }
-    if (do_j2) {
-        sv[0][threadIdx.x] = vx;
-        sv[1][threadIdx.x] = vy;
-        sv[2][threadIdx.x] = vz;
-        __syncthreads();
-        jump_phase_lite(s, p, cur, step - 1, BOUNCE_STREAM_J2, sact, nact, sv, nprop, nacc, near);
-        __syncthreads();
-        vx = sv[0][threadIdx.x];
-        vy = sv[1][threadIdx.x];
-        vz = sv[2][threadIdx.x];
-    }
+    // the jump half-steps, one thread per atom: most atoms settle M = 0 from
+    // their first draw (jump_thread), so no compaction or barrier pays off
+    if (do_j2 && live) jump_lite(s, p, cur, i, step - 1, BOUNCE_STREAM_J2, ahi, alo, vx, vy, vz, nprop, nacc, near);
     if (live) {
         const double c = hk * kick;
         vx -= c * (double)Gx;
@@ -1069,18 +1027,7 @@ __global__ void __launch_bounds__(256, LITE_MIN_CTAS) k_step_lite(DevSys s, Para
             vz -= co * (double)gz;
         }
     }
-    if (do_j1) {
-        __syncthreads();  // the J2 phase's reads of sv are done
-        sv[0][threadIdx.x] = vx;
-        sv[1][threadIdx.x] = vy;
-        sv[2][threadIdx.x] = vz;
-        __syncthreads();
-        jump_phase_lite(s, p, cur, step, BOUNCE_STREAM_J1, sact, nact, sv, nprop, nacc, near);
-        __syncthreads();
-        vx = sv[0][threadIdx.x];
-        vy = sv[1][threadIdx.x];
-        vz = sv[2][threadIdx.x];
-    }
+    if (do_j1 && live) jump_lite(s, p, cur, i, step, BOUNCE_STREAM_J1, ahi, alo, vx, vy, vz, nprop, nacc, near);
     if (live) {
         if (do_aoa) {
             const double h = 0.5 * p.dt;

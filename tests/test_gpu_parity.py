@@ -587,7 +587,7 @@ def test_full_size_box_first_step_sampled(coulomb_jumps):
     s = water_box(32, seed=0)
     rng = np.random.default_rng(8)
     q0 = s.q + rng.normal(scale=0.05, size=s.q.shape)
-    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=2.5, pair_skin=2.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
+    cfg = dict(r_on=7.5, r_off=8.5, r_cut=9.0, skin=2.5, pair_skin=3.0, ewald_beta=0.35, pme_grid=(96, 96, 96),
                pme_order=5, max_neighbors=2048, jump_coulomb=coulomb_jumps)
     ctx = bounce.from_system(s, seed=13, **cfg)
     ctx.set_state(q0, s.v, step=0)
