@@ -17,7 +17,9 @@
 //   convolve  multiply by the influence function B(m) C(m) (FP32 table made
 //             on the host in FP64) and accumulate the energy partials
 //             sum B C |F(Q)|^2 per CTA (FP64);
-//   fft x3    inverse transform (no 1/K normalisation);
+//   fft x3    inverse transform (no 1/K normalisation); without the energy,
+//             axis 0's forward and inverse transforms and the product are
+//             one pass over the grid;
 //   gather    per atom, q K/L sum dM M M conv (FP32) plus the removal of the
 //             same-molecule pairs, -k q_i q_j erf(beta r)/r, into an FP64
 //             gradient (SoA) that the step kernel kicks with.
@@ -462,6 +464,36 @@ __global__ void __launch_bounds__(256) k_pme_fft_w(DevPme m, int axis, float sig
     }
 }
 
+// The transforms of four lines of K = 32 M points held by one warp (lane n2
+// holds x[32 n1 + n2] of each line for n1 < M): M-point DFTs in registers,
+// twiddles W_K^(n2 k1) from tw, then the 32-point DFTs across the lanes by
+// shuffles.  On return lane l holds X[k1 + M rev(l)] of each line (rev: the
+// 5-bit reversal of l).
+template <int M>
+__device__ __forceinline__ void warp_fft4(float2 (&v)[4][M > 1 ? M : 2], const float2* tw, int lane, float sign) {
+    constexpr int K = 32 * M;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (M > 1) small_dft(v[q], M, sign);
+#pragma unroll
+        for (int k1 = 1; k1 < M; ++k1) v[q][k1] = cmul(v[q][k1], tw[(lane * k1) % K]);
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const bool low = (lane & sh) != 0;
+        const float2 w = tw[(lane & (sh - 1)) * (K / (2 * sh))];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) {
+                float2 b;
+                b.x = __shfl_xor_sync(0xffffffffu, v[q][k1].x, sh);
+                b.y = __shfl_xor_sync(0xffffffffu, v[q][k1].y, sh);
+                v[q][k1] = low ? cmul(csub(b, v[q][k1]), w) : cadd(v[q][k1], b);
+            }
+    }
+}
+
 // The same transform for four neighbouring lines of a strided axis (axis 0
 // or 1: lines l..l+3 are neighbours along the contiguous axis), one warp for
 // all four: each lane loads and stores 32 contiguous bytes (four complex
@@ -493,26 +525,68 @@ __global__ void __launch_bounds__(256) k_pme_fft_w4(DevPme m, int axis, float si
             v[2][n1] = make_float2(b.x, b.y);
             v[3][n1] = make_float2(b.z, b.w);
         }
+        warp_fft4<M>(v, tw, lane, sign);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (M > 1) small_dft(v[q], M, sign);
-#pragma unroll
-            for (int k1 = 1; k1 < M; ++k1) v[q][k1] = cmul(v[q][k1], tw[(lane * k1) % K]);
+        for (int k1 = 0; k1 < M; ++k1) {
+            float4* dst = reinterpret_cast<float4*>(m.cgrid + b0 + (size_t)(k1 + M * rev) * stride);
+            dst[0] = make_float4(v[0][k1].x, v[0][k1].y, v[1][k1].x, v[1][k1].y);
+            dst[1] = make_float4(v[2][k1].x, v[2][k1].y, v[3][k1].x, v[3][k1].y);
         }
+    }
+}
+
+// Axis 0 of the forward transform, the influence function and axis 0 of
+// the inverse transform in one pass (evaluations without the energy): each
+// warp transforms four neighbouring lines along axis 0 as k_pme_fft_w4,
+// multiplies every point by B C (k_pme_convolve's product, the same
+// rounding), brings the lines back to natural order through shared memory
+// and transforms them back, so that the grid is read and written once for
+// the three steps.
+template <int M>
+__global__ void __launch_bounds__(256) k_pme_conv_x4(DevPme m) {
+    constexpr int K = 32 * M;
+    __shared__ float2 twf[K], twi[K];
+    __shared__ float2 sl[8][4][K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)K, &sn, &cs);
+        twf[k] = make_float2(cs, -sn);
+        twi[k] = make_float2(cs, sn);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int ngroups = (int)((size_t)m.K[1] * m.K[2] / 4);
+    const size_t stride = (size_t)m.K[1] * m.K[2];
+    const int rev = (int)(__brev((unsigned)lane) >> 27);
+    for (int g = blockIdx.x * (blockDim.x >> 5) + wl; g < ngroups; g += gridDim.x * (blockDim.x >> 5)) {
+        const size_t b0 = 4 * (size_t)g;
+        float2 v[4][M > 1 ? M : 2];
 #pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) {
-            const bool low = (lane & sh) != 0;
-            const float2 w = tw[(lane & (sh - 1)) * (K / (2 * sh))];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int k1 = 0; k1 < M; ++k1) {
-                    float2 b;
-                    b.x = __shfl_xor_sync(0xffffffffu, v[q][k1].x, sh);
-                    b.y = __shfl_xor_sync(0xffffffffu, v[q][k1].y, sh);
-                    v[q][k1] = low ? cmul(csub(b, v[q][k1]), w) : cadd(v[q][k1], b);
-                }
+        for (int n1 = 0; n1 < M; ++n1) {
+            const float4* src = reinterpret_cast<const float4*>(m.cgrid + b0 + (size_t)(32 * n1 + lane) * stride);
+            const float4 a = src[0], b = src[1];
+            v[0][n1] = make_float2(a.x, a.y);
+            v[1][n1] = make_float2(a.z, a.w);
+            v[2][n1] = make_float2(b.x, b.y);
+            v[3][n1] = make_float2(b.z, b.w);
         }
+        warp_fft4<M>(v, twf, lane, -1.f);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) {
+            const int kx = k1 + M * rev;
+            const float4 bc = *reinterpret_cast<const float4*>(m.bc + b0 + (size_t)kx * stride);
+            sl[wl][0][kx] = make_float2(bc.x * v[0][k1].x, bc.x * v[0][k1].y);
+            sl[wl][1][kx] = make_float2(bc.y * v[1][k1].x, bc.y * v[1][k1].y);
+            sl[wl][2][kx] = make_float2(bc.z * v[2][k1].x, bc.z * v[2][k1].y);
+            sl[wl][3][kx] = make_float2(bc.w * v[3][k1].x, bc.w * v[3][k1].y);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int n1 = 0; n1 < M; ++n1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q][n1] = sl[wl][q][32 * n1 + lane];
+        warp_fft4<M>(v, twi, lane, 1.f);
 #pragma unroll
         for (int k1 = 0; k1 < M; ++k1) {
             float4* dst = reinterpret_cast<float4*>(m.cgrid + b0 + (size_t)(k1 + M * rev) * stride);
@@ -588,10 +662,27 @@ void launch_pme(const DevSys& s, const Params& p, const DevPme& m, int step_off,
             k_pme_dft<<<lines[axis], 128, 2 * m.K[axis] * sizeof(float2), st>>>(m, axis, sign);
         }
     };
-    for (int axis = 2; axis >= 0; --axis) transform(axis, -1.f);
-    if (energy) k_pme_convolve<true><<<PME_CONV_CTAS, 256, 0, st>>>(m);
-    else k_pme_convolve<false><<<PME_CONV_CTAS, 256, 0, st>>>(m);
-    for (int axis = 2; axis >= 0; --axis) transform(axis, 1.f);
+    // without the energy, axis 0's two transforms and the product in one
+    // pass when its lines are 32 M points that four-line warps take
+    const int M0 = m.K[0] / 32;
+    const bool fuse = !energy && m.K[0] % 32 == 0 && M0 >= 1 && M0 <= 5 && m.K[2] % 4 == 0;
+    if (fuse) {
+        transform(2, -1.f);
+        transform(1, -1.f);
+        const int wb = std::min((lines[0] / 4 + 7) / 8, 152 * 8);
+        if (M0 == 1) k_pme_conv_x4<1><<<wb, 256, 0, st>>>(m);
+        else if (M0 == 2) k_pme_conv_x4<2><<<wb, 256, 0, st>>>(m);
+        else if (M0 == 3) k_pme_conv_x4<3><<<wb, 256, 0, st>>>(m);
+        else if (M0 == 4) k_pme_conv_x4<4><<<wb, 256, 0, st>>>(m);
+        else k_pme_conv_x4<5><<<wb, 256, 0, st>>>(m);
+        transform(1, 1.f);
+        transform(2, 1.f);
+    } else {
+        for (int axis = 2; axis >= 0; --axis) transform(axis, -1.f);
+        if (energy) k_pme_convolve<true><<<PME_CONV_CTAS, 256, 0, st>>>(m);
+        else k_pme_convolve<false><<<PME_CONV_CTAS, 256, 0, st>>>(m);
+        for (int axis = 2; axis >= 0; --axis) transform(axis, 1.f);
+    }
     switch (m.order) {
         case 3: k_pme_gather<3><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
         case 4: k_pme_gather<4><<<nb, tb, 0, st>>>(s, p, m, step_off); break;
