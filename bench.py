@@ -26,10 +26,10 @@ Protocol (our arm):
   * per-kernel breakdown and the roofline of the pair kernel (the dominant
     kernel) from CUDA events around each group of launches
     (bounce_profile_breakdown) over 24 steps of the same trajectory;
-  * matched observables: eight independent runs per arm (own Philox seeds)
+  * matched observables: twelve independent runs per arm (own Philox seeds)
     from the relaxed box, 1.2 ps each to decorrelate, then 4.8 ps sampled every
     0.24 ps: potential energy per molecule, kinetic temperature, O-O g(r) and
-    O self-diffusion; standard errors from the spread of the eight runs; a
+    O self-diffusion; standard errors from the spread of the twelve runs; a
     second BAOAB arm with other seeds is the null control, BAOAB at 0.5 fs
     shows the comparator's own step-size error, and BOUNCE-RESPA without
     jumps (switch at the cutoff) separates the RESPA split from the jumps;
@@ -445,13 +445,12 @@ def compare_arms(cur, ref, alpha=0.05, g_min=0.1):
     return z
 
 
-def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=8, decor=1200, prod=4800, every=240):
-    """Eight independent runs per arm from the relaxed box (own Philox
-    seeds): `decor` steps, then `prod` steps sampled every `every` steps
-    (all multiples of every arm's outer step).  Eight runs, so that the
-    per-bin standard errors of g(r) taken from the spread of the runs are
-    themselves stable (with four runs a few bins get a small error estimate
-    by chance and dominate the chi^2 even between two BAOAB arms).
+def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=12, decor=1200, prod=4800, every=240):
+    """Twelve independent runs per arm from the relaxed box (own Philox
+    seeds, distinct between arms): `decor` steps, then `prod` steps sampled
+    every `every` steps (all multiples of every arm's outer step).  Twelve
+    runs, so that the standard errors taken from the spread of the runs are
+    themselves stable.
     Per run: mean potential energy per molecule, mean kinetic temperature,
     O-O pair-distance histogram (0-8 A, 0.1 A bins) as g(r), and the O
     self-diffusion D from the mean squared displacement over the production
@@ -466,13 +465,16 @@ def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=8, dec
     edges = np.arange(81) * 0.1
     shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
     # (name, integrator, extra config, outer period, seed base); dt from the config
-    arms = (("baoab", "BAOAB", {}, 1, 100),
-            ("baoab_control", "BAOAB", {}, 1, 200),
-            ("baoab_half_fs", "BAOAB", dict(dt=0.5), 1, 300),
-            ("bounce_respa", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2), 2, 100),
-            ("bounce_respa1", "BOUNCE_RESPA1", dict(LJ_JUMPS, respa_m=2, respa_m2=3), 6, 100),
-            ("bounce_respa_no_jumps", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2, r_on=R_CUT, r_off=R_CUT), 2, 100),
-            ("bounce_respa_coulomb_jumps", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2, 100))
+    # every arm draws its own Philox streams (seed bases 1,000 apart): arms
+    # that shared BAOAB's O-step noise would be correlated with it, and the
+    # unpaired comparison would then understate their differences
+    arms = (("baoab", "BAOAB", {}, 1, 1000),
+            ("baoab_control", "BAOAB", {}, 1, 2000),
+            ("baoab_half_fs", "BAOAB", dict(dt=0.5), 1, 3000),
+            ("bounce_respa", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2), 2, 4000),
+            ("bounce_respa1", "BOUNCE_RESPA1", dict(LJ_JUMPS, respa_m=2, respa_m2=3), 6, 5000),
+            ("bounce_respa_no_jumps", "BOUNCE_RESPA", dict(LJ_JUMPS, respa_m=2, r_on=R_CUT, r_off=R_CUT), 2, 6000),
+            ("bounce_respa_coulomb_jumps", "BOUNCE_RESPA", dict(JUMP_ROWS, respa_m=2), 2, 7000))
     raw = {}
     out = {"protocol": "%d runs per arm from the relaxed box, %d steps to decorrelate, then %d steps sampled every %d; "
                        "standard errors from the spread of the runs" % (runs, decor, prod, every)}
@@ -483,7 +485,7 @@ def matched_observables(bounce, s, q0, v0, device, stream, sh, rank, runs=8, dec
         per_run = {"pe": [], "T": [], "D": [], "g": []}
         ms, err = 0.0, None
         for r in range(runs):
-            ctx = bounce.from_system(s, seed=seed0 + 17 * r + 1000 * rank, **box_cfg(device, **extra))
+            ctx = bounce.from_system(s, seed=seed0 + 17 * r + 100000 * rank, **box_cfg(device, **extra))
             try:
                 ctx.set_state(q0, v0, step=0)
                 ctx.run(decor * k_dt, integ, stream=sh)
