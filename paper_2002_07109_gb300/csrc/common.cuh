@@ -34,7 +34,10 @@ constexpr double ACCEL_D = 4.184e-4;
 // sums both sides of every pair once (Newton's third law) into int64
 // fixed-point accumulators, one per slot and component.
 #define BOUNCE_CL 8
-#define BOUNCE_CL_EPW 256          // list entries per work item of the pair kernel
+#ifndef BOUNCE_CL_EPW
+#define BOUNCE_CL_EPW 512          // list entries per work item of the pair kernel (one item per
+                                   // cluster on the water box: fewer i-side reductions)
+#endif
 #define BOUNCE_CL_MAXCOL 1024      // atoms per column (one CTA sorts a column in shared memory)
 constexpr double CL_FIX = 4294967296.0;        // fixed-point scale 2^32 of the accumulators
 constexpr double CL_UNFIX = 2.3283064365386963e-10;  // 2^-32
