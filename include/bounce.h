@@ -94,7 +94,12 @@ typedef struct bounce_config {
     int32_t respa_m;       /* inner steps per BOUNCE-RESPA outer step, 1..8 (2)  */
     int32_t jump_coulomb;  /* 1: Coulomb is split by chi like LJ (Sec. V droplets);
                             * 0: Coulomb wholly in F_0, only LJ on jumps
-                            * (the first example of Sec. IV) (1)                 */
+                            * (the first example of Sec. IV); with one bound
+                            * per type the jump step's rows then keep only
+                            * the partners an atom has LJ with (Sec. V: the
+                            * partner is drawn among the particles it
+                            * interacts with), rebuilt on the displacement of
+                            * the types that propose or can be drawn (1)        */
     int32_t pair_bounds;   /* 1: one bound per type pair (Sec. V: L may depend on
                             * the types of both particles) with a two-stage
                             * partner choice: type b with probability
@@ -219,11 +224,15 @@ int bounce_jump_half(bounce_ctx* ctx, int64_t step, int32_t stream_id, int32_t* 
                      void* stream);
 
 /* Candidate rows at the current positions (rebuilt first if stale):
- * counts[n] and rows[n * capacity] (ascending atom indices). */
+ * counts[n] and rows[n * capacity] (ascending atom indices).  These are the
+ * full rows (every atom of another molecule within r_c + skin) even where a
+ * run's jump step reads rows restricted to the partners a jump can draw
+ * (LJ alone on the jumps with one bound per type: see jump_coulomb); reading
+ * them leaves the run's own rows and rebuild schedule unchanged. */
 int bounce_get_rows(bounce_ctx* ctx, int32_t* counts, int32_t* rows, int32_t capacity);
 
-/* Batch of independent replicas in one context (BASELINE's batched
- * droplets).  The topology holds all replicas back to back; replica r owns
+/* Batch of independent replicas in one context (for example many small
+ * droplets advanced together).  The topology holds all replicas back to back; replica r owns
  * atoms [atom_offsets[r], atom_offsets[r+1]) and draws every random number
  * with its own Philox key seeds[r] and its atoms' indices inside the
  * replica, so each replica follows exactly the trajectory it would follow
